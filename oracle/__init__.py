@@ -1,0 +1,241 @@
+"""ctypes front-end of the plain FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package. The CUDA library never does. ``build()`` compiles ``oracle.c`` with
+gcc, OpenMP and FP contraction off, so the results do not depend on the host's FMA units.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+HORIZON, ESCAPE, NMAX, NAN = 1, 2, 3, 4
+MODEL_ADAF, MODEL_GRID = 1, 2
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "oracle.c")
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fopenmp", "-fPIC", "-shared", "-o", _SO, src, "-lm"])
+    return _SO
+
+
+class Camera(C.Structure):
+    _fields_ = [("a", C.c_double), ("incl_deg", C.c_double), ("r_cam", C.c_double),
+                ("freq_hz", C.c_double), ("fov_M", C.c_double), ("nx", C.c_int), ("ny", C.c_int),
+                ("M_bh_g", C.c_double), ("dist_cm", C.c_double), ("eps", C.c_double),
+                ("nmax", C.c_int)]
+
+
+class Model(C.Structure):
+    _fields_ = [("kind", C.c_int),
+                ("n0", C.c_double), ("T0", C.c_double), ("beta", C.c_double), ("f_kep", C.c_double),
+                ("Ti_over_Te", C.c_double), ("r_out_emit", C.c_double),
+                ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int),
+                ("r_in", C.c_double), ("r_out", C.c_double), ("hslope", C.c_double),
+                ("poly_xt", C.c_double), ("poly_alpha", C.c_double), ("mks_smooth", C.c_double),
+                ("prims", C.POINTER(C.c_float)),
+                ("M_unit", C.c_double), ("R_high", C.c_double), ("R_low", C.c_double),
+                ("sigma_cut", C.c_double), ("gamma_ad", C.c_double),
+                ("edf", C.c_int), ("kappa", C.c_double)]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        L.ora_metric_ks.argtypes = [C.c_double, C.c_double, C.c_double, _D]
+        L.ora_invert4.argtypes = [_D, _D]
+        L.ora_metric_derivs.argtypes = [C.c_double, C.c_double, C.c_double, _D, _D]
+        L.ora_connection.argtypes = [C.c_double, C.c_double, C.c_double, _D]
+        L.ora_camera_ray.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, _D, _D]
+        L.ora_trace_geodesic.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, C.c_int, _D, _I]
+        L.ora_trace_geodesic.restype = C.c_int
+        L.ora_fmks_theta.argtypes = [C.POINTER(Model), C.c_double, C.c_double, _D, _D]
+        L.ora_fmks_theta.restype = C.c_double
+        L.ora_fmks_x2.argtypes = [C.POINTER(Model), C.c_double, C.c_double]
+        L.ora_fmks_x2.restype = C.c_double
+        L.ora_grid_interp.argtypes = [C.POINTER(Model), C.c_double, C.c_double, C.c_double, _D]
+        L.ora_plasma.argtypes = [C.POINTER(Camera), C.POINTER(Model), _D, _D]
+        L.ora_fluid_tetrad.argtypes = [C.c_double, _D, _D, _D, _D, _D]
+        L.ora_fluid_tetrad.restype = C.c_double
+        L.ora_bessel_k_scaled.argtypes = [C.c_int, C.c_double]
+        L.ora_bessel_k_scaled.restype = C.c_double
+        L.ora_thermal_coeffs.argtypes = [C.c_double] * 5 + [_D]
+        L.ora_substep.argtypes = [_D, C.c_double, _D, _D]
+        L.ora_render_pixels.argtypes = [C.POINTER(Camera), C.POINTER(Model), C.c_int, _I, _I, C.c_int,
+                                        _D, _I, _I, _D, C.c_int]
+        L.ora_render_pixels.restype = C.c_int
+        L.ora_image_stats.argtypes = [C.POINTER(Camera), _D, C.c_long, _D, _D, _D]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(_I)
+
+
+def camera(cam, eps: float = 0.05, nmax: int = 20000) -> Camera:
+    """Oracle camera from a ``synth.Camera`` (or any object with the same fields)."""
+    return Camera(cam.a, cam.incl_deg, cam.r_cam, cam.freq_hz, cam.fov_M, cam.nx, cam.ny,
+                  cam.M_bh_g, cam.dist_cm, eps, nmax)
+
+
+class ModelHandle:
+    """Keeps the primitive array alive for as long as the ctypes struct points at it."""
+
+    def __init__(self, st: Model, keep=None):
+        self.st = st
+        self.keep = keep
+
+
+def adaf_model(p) -> ModelHandle:
+    m = Model()
+    m.kind = MODEL_ADAF
+    m.n0, m.T0, m.beta, m.f_kep, m.Ti_over_Te, m.r_out_emit = p.n0, p.T0, p.beta, p.f_kep, p.Ti_over_Te, p.r_out
+    return ModelHandle(m)
+
+
+def grid_model(prims: np.ndarray, g) -> ModelHandle:
+    prims = np.ascontiguousarray(prims, dtype=np.float32)
+    m = Model()
+    m.kind = MODEL_GRID
+    m.n1, m.n2, m.n3 = prims.shape[0], prims.shape[1], prims.shape[2]
+    m.r_in, m.r_out, m.hslope, m.poly_xt = g.r_in, g.r_out, g.hslope, g.poly_xt
+    m.poly_alpha, m.mks_smooth = g.poly_alpha, g.mks_smooth
+    m.prims = prims.ctypes.data_as(C.POINTER(C.c_float))
+    m.M_unit, m.R_high, m.R_low, m.sigma_cut, m.gamma_ad = g.M_unit, g.R_high, g.R_low, g.sigma_cut, g.gamma_ad
+    return ModelHandle(m, prims)
+
+
+def render_pixels(cam: Camera, model: ModelHandle, ix, iy, pert: int = 0, nthreads: int = 0):
+    """Render the listed pixels; returns (iquv[n,4], nsteps[n], status[n], minpol[n])."""
+    L = lib()
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    n = ix.size
+    out = np.zeros((n, 4))
+    ns = np.zeros(n, dtype=np.int32)
+    stt = np.zeros(n, dtype=np.int32)
+    mp = np.zeros(n)
+    rc = L.ora_render_pixels(C.byref(cam), C.byref(model.st), n, _ip(ix), _ip(iy), pert, _dp(out), _ip(ns),
+                             _ip(stt), _dp(mp), nthreads)
+    if rc != 0:
+        raise MemoryError("oracle render failed")
+    return out, ns, stt, mp
+
+
+def render_image(cam: Camera, model: ModelHandle, pert: int = 0, nthreads: int = 0):
+    """Full image, row-major [ny][nx][4]."""
+    iy, ix = np.meshgrid(np.arange(cam.ny), np.arange(cam.nx), indexing="ij")
+    out, ns, stt, mp = render_pixels(cam, model, ix.ravel(), iy.ravel(), pert, nthreads)
+    return (out.reshape(cam.ny, cam.nx, 4), ns.reshape(cam.ny, cam.nx), stt.reshape(cam.ny, cam.nx),
+            mp.reshape(cam.ny, cam.nx))
+
+
+def trace_geodesic(cam: Camera, px: float, py: float):
+    L = lib()
+    maxst = cam.nmax + 2
+    st = np.zeros((maxst, 9))
+    stat = C.c_int(0)
+    n = L.ora_trace_geodesic(C.byref(cam), px, py, maxst, _dp(st), C.byref(stat))
+    return st[: n + 1].copy(), stat.value
+
+
+def metric(a, r, th):
+    g = np.zeros(16)
+    lib().ora_metric_ks(a, r, th, _dp(g))
+    return g.reshape(4, 4)
+
+
+def metric_derivs(a, r, th):
+    dr, dt = np.zeros(16), np.zeros(16)
+    lib().ora_metric_derivs(a, r, th, _dp(dr), _dp(dt))
+    return dr.reshape(4, 4), dt.reshape(4, 4)
+
+
+def connection(a, r, th):
+    G = np.zeros(64)
+    lib().ora_connection(a, r, th, _dp(G))
+    return G.reshape(4, 4, 4)
+
+
+def camera_ray(cam: Camera, px, py):
+    x, K = np.zeros(4), np.zeros(4)
+    lib().ora_camera_ray(C.byref(cam), px, py, _dp(x), _dp(K))
+    return x, K
+
+
+def plasma(cam: Camera, model: ModelHandle, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(12)
+    lib().ora_plasma(C.byref(cam), C.byref(model.st), _dp(x), _dp(out))
+    return out
+
+
+def fluid_tetrad(a, x, K, u, b):
+    e = np.zeros(16)
+    f = lambda v: np.ascontiguousarray(v, dtype=np.float64)
+    x, K, u, b = f(x), f(K), f(u), f(b)
+    thB = lib().ora_fluid_tetrad(a, _dp(x), _dp(K), _dp(u), _dp(b), _dp(e))
+    return e.reshape(4, 4), thB
+
+
+def fmks_theta(model: ModelHandle, X1, X2):
+    d1, d2 = C.c_double(0), C.c_double(0)
+    th = lib().ora_fmks_theta(C.byref(model.st), X1, X2, C.byref(d1), C.byref(d2))
+    return th, d1.value, d2.value
+
+
+def fmks_x2(model: ModelHandle, X1, th):
+    return lib().ora_fmks_x2(C.byref(model.st), X1, th)
+
+
+def grid_interp(model: ModelHandle, X1, X2, X3):
+    out = np.zeros(8)
+    lib().ora_grid_interp(C.byref(model.st), X1, X2, X3, _dp(out))
+    return out
+
+
+def bessel_k_scaled(n, z):
+    return lib().ora_bessel_k_scaled(n, z)
+
+
+def thermal_coeffs(ne, Te, B, nu, thB):
+    out = np.zeros(8)
+    lib().ora_thermal_coeffs(ne, Te, B, nu, thB, _dp(out))
+    return out
+
+
+def substep(coef11, ds, S0):
+    cf = np.ascontiguousarray(coef11, dtype=np.float64)
+    s0 = np.ascontiguousarray(S0, dtype=np.float64)
+    s1 = np.zeros(4)
+    lib().ora_substep(_dp(cf), ds, _dp(s0), _dp(s1))
+    return s1
+
+
+def image_stats(cam: Camera, iquv: np.ndarray):
+    iquv = np.ascontiguousarray(iquv, dtype=np.float64)
+    f, lp, cp = C.c_double(0), C.c_double(0), C.c_double(0)
+    lib().ora_image_stats(C.byref(cam), _dp(iquv), iquv.size // 4, C.byref(f), C.byref(lp), C.byref(cp))
+    return f.value, lp.value, cp.value
