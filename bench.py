@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the polarized ray-tracing hot path on GB300.
+
+Metric: Stokes-IQUV pixels/s for one 1024x1024 image of the GRMHD-shaped torus grid
+(FMKS 288x128x128 FP32 primitives, R_high = 40, i = 20 deg, 230 GHz) in the chosen form
+(RT_MIXED: FP64 geodesic, FP32 transfer), with the plain FP64 form timed beside it. One step
+is one rt_render of the whole image (backward geodesics, path arena, forward transfer)
+plus rt_image_stats, with inputs resident in HBM. The grid (151 MB) and the path arena
+(tens of GB) are both larger than L2, so nothing is flushed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank renders its own replica image (the method has no data
+exchange between images); value = pixels of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Stokes-IQUV pixels/s at 1024^2, chosen form (FP64 geodesic + FP32 transfer) vs plain FP64 form"
+# Algorithmic work per unit (derivation in the design notes): FP64 flops of one RK4 step of
+# the geodesic (4 right-hand sides of the contracted Kerr-Schild connection + stage algebra),
+# counting an FMA as 2 and sin, cos, a division or a square root as 1 each.
+GEO_FLOP_PER_STEP = 612
+XFER_FLOP_PER_POINT = {"fp64": 1450, "mixed": 1450}
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str | None):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.idx is not None:
+            cmd += ["-i", self.idx]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(size):
+    from paper_2302_02733_gb300 import synth
+
+    cam = synth.Camera(incl_deg=20.0, nx=size, ny=size)
+    prims, g = synth.fm_torus_grid(1)
+    return cam, prims, g
+
+
+def oracle_sample(cam, prims, g, npix, seed=0):
+    """Time the CPU oracle (as it stands, all host cores) on npix strided pixels."""
+    import numpy as np
+
+    import oracle
+
+    stride = max(1, int(round((cam.nx * cam.ny / npix) ** 0.5)))
+    iy, ix = np.meshgrid(np.arange(stride // 2, cam.ny, stride), np.arange(stride // 2, cam.nx, stride),
+                         indexing="ij")
+    ix, iy = ix.ravel()[:npix], iy.ravel()[:npix]
+    ocam, om = oracle.camera(cam), oracle.grid_model(prims, g)
+    t = time.perf_counter()
+    oracle.render_pixels(ocam, om, ix, iy)
+    dt = time.perf_counter() - t
+    return ix.size / dt, ix.size, stride, dt
+
+
+def run_reference(args):
+    """The reference arm: the plain FP64 CPU oracle on a bounded sample per step."""
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cam, prims, g = workload(args.size)
+    npix = 1024
+    for _ in range(args.warmup):
+        oracle_sample(cam, prims, g, npix)
+    rates, walls = [], []
+    for _ in range(args.steps):
+        r, n, stride, dt = oracle_sample(cam, prims, g, npix)
+        rates.append(r)
+        walls.append(dt)
+    value = args.steps * n / sum(walls)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded FM torus on an FMKS grid)",
+            "config": {"workload": f"grmhd-torus-{args.size}x{args.size}", "grid": "288x128x128x8 f32",
+                       "inclination_deg": 20, "freq_ghz": 230, "sample": f"{n} pixels, stride {stride}"},
+            "cpu_baseline": {"value": value, "unit": "pixels/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} strided pixels of the {args.size}^2 image per step"},
+            "e2e": {"value": value, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2302_02733_gb300 import build, polrt
+
+    build.build()
+    dev = f"cuda:{local}"
+    stream = torch.cuda.current_stream()
+    cam, prims, g = workload(args.size)
+    npix = cam.nx * cam.ny
+    form = polrt.RT_MIXED if args.form == "mixed" else polrt.RT_FP64
+    odt = torch.float32 if form == polrt.RT_MIXED else torch.float64
+    ctx = polrt.rt_create(local, stream.cuda_stream)
+    polrt.rt_set_camera(ctx, cam)
+    prims_dev = torch.from_numpy(prims).to(dev)
+    polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g))
+    out = torch.empty((cam.ny, cam.nx, 4), dtype=odt, device=dev)
+
+    def step(f=form, o=out):
+        polrt.rt_render(ctx, f, o)
+        polrt.rt_image_stats(ctx, o, f)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if ws == 1 else None
+    kt_geo, kt_xf, counters = [], [], None
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(gpu_index) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+            counters = polrt.rt_last_counters(ctx)
+            kt_geo.append(counters["ms_geodesic"])
+            kt_xf.append(counters["ms_transfer"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * npix / (ms_max / 1e3)
+
+    # per-kernel roofline of the dominant kernel (measured live with CUDA events in the library)
+    geo_ms, xf_ms = statistics.mean(kt_geo), statistics.mean(kt_xf)
+    steps_per_launch = counters["steps"]
+    pts_per_launch = counters["points"]
+    if geo_ms >= xf_ms:
+        achieved = steps_per_launch * GEO_FLOP_PER_STEP / (geo_ms / 1e3) / 1e12
+        dom = "geodesic_kernel (FP64 RK4)"
+    else:
+        achieved = pts_per_launch * XFER_FLOP_PER_POINT[args.form] / (xf_ms / 1e3) / 1e12
+        dom = f"transfer_kernel ({args.form})"
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+
+    extra = {"kernel_ms": {"geodesic": geo_ms, "transfer": xf_ms}, "steps_per_image": steps_per_launch,
+             "points_per_image": pts_per_launch, "mean_steps_per_ray": steps_per_launch / npix}
+
+    # the plain FP64 form on the same image
+    if not args.no_compare and form != polrt.RT_FP64:
+        o64 = torch.empty((cam.ny, cam.nx, 4), dtype=torch.float64, device=dev)
+        step(polrt.RT_FP64, o64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 2
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(reps):
+            step(polrt.RT_FP64, o64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / reps
+        c64 = polrt.rt_last_counters(ctx)
+        ref = o64.cpu().numpy()
+        mix = out.double().cpu().numpy()
+        scale = np.maximum(ref[..., 0], 1e-8 * ref[..., 0].max())
+        err = np.abs(mix - ref).max(axis=-1) / scale
+        extra["fp64_form"] = {"value": npix / (ms64 / 1e3), "unit": "pixels/s", "ms_per_step": ms64,
+                              "kernel_ms": {"geodesic": c64["ms_geodesic"], "transfer": c64["ms_transfer"]}}
+        extra["chosen_vs_fp64"] = {"speedup": ms64 / ms, "pixel_rel_err_p50": float(np.median(err)),
+                                   "pixel_rel_err_p99": float(np.percentile(err, 99)),
+                                   "pixel_rel_err_max": float(err.max()),
+                                   "flux_rel_err": float(abs(mix[..., 0].sum() / ref[..., 0].sum() - 1))}
+
+    # end to end through the C ABI with host buffers: prims H2D from pinned memory, image D2H
+    e2e = None
+    if not args.no_e2e:
+        host_prims = torch.from_numpy(prims).pin_memory()
+        host_out = torch.empty((cam.ny, cam.nx, 4), dtype=odt).pin_memory()
+        model_h = polrt.grid_model(host_prims, g)
+        polrt.rt_load_model(ctx, model_h)
+        polrt.rt_render(ctx, form, host_out)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            polrt.rt_load_model(ctx, model_h)
+            polrt.rt_render(ctx, form, host_out)
+            polrt.rt_image_stats(ctx, host_out, form)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * npix / dt, "unit": "pixels/s", "h2d_bytes_per_step": int(prims.nbytes),
+               "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()), "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+
+        oracle.build()
+        rate, n, stride, dt = oracle_sample(cam, prims, g, 8192)
+        cpu = {"value": rate, "unit": "pixels/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} pixels (stride {stride}) of the {cam.nx}^2 image, {dt:.1f} s"}
+
+    polrt.rt_destroy(ctx)
+    if rank == 0:
+        chunks = 1
+        line = {"metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 geodesic + f32 transfer" if form == polrt.RT_MIXED else "f64",
+                "data": "synthetic (seeded FM torus on an FMKS grid, log-normal perturbations)",
+                "config": {"workload": f"grmhd-torus-{cam.nx}x{cam.ny}", "grid": "288x128x128x8 f32",
+                           "inclination_deg": 20, "freq_ghz": 230, "form": args.form,
+                           "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (151 MB grid, multi-GB path arena); no flush"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": args.steps * (2 * chunks + 1), **extra}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * polrt: polarized general-relativistic ray tracing on one GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library. The method follows the paper's Section 2.1. One photon is
+ * launched per camera pixel, and its null geodesic in the Kerr metric is integrated
+ * backward in time and saved. The covariant, fully polarized transfer of Stokes I, Q, U, V
+ * (synchrotron emission, self-absorption, Faraday rotation and conversion; the coherency
+ * matrix is carried in the coordinate frame) is then integrated along the saved path
+ * toward the observer. Plasma comes from a semi-analytic ADAF or from gridded GRMHD
+ * primitives (Sections 2.1 and 3). Section 2.2 states that the CPU code saves the path. This
+ * library does the same in a device-memory arena, so the transfer follows exactly the
+ * states of the backward pass.
+ *
+ * Conventions for every call:
+ *   - Return RT_OK (0) on success or a negative RT_ERR_* code; rt_error_string names it.
+ *     Nothing throws across this boundary.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous, unless a call
+ *     says it synchronizes.
+ *   - Pointers marked "host or device" are classified with cudaPointerGetAttributes.
+ *   - The library never frees memory it did not allocate. The caller may hand it a
+ *     device workspace (rt_set_workspace). Otherwise it allocates one and frees it in
+ *     rt_destroy.
+ *   - Units: geometry in M = GM/c^2 (G = c = 1); intensities in cgs
+ *     (erg s^-1 cm^-2 Hz^-1 sr^-1); flux in Jy.
+ */
+#ifndef POLRT_H
+#define POLRT_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    RT_OK = 0,
+    RT_ERR_INVALID = -1,    /* a bad argument; nothing was enqueued */
+    RT_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+    RT_ERR_NOMEM = -3,      /* an allocation failed */
+    RT_ERR_NOT_READY = -4,  /* no model or no camera set */
+    RT_ERR_WORKSPACE = -5,  /* the path arena ran out; rays carry RT_RAY_OVERFLOW */
+    RT_ERR_SIZE = -6        /* a size beyond a fixed limit of the call */
+};
+
+enum { RT_MODEL_ADAF = 1, RT_MODEL_GRID = 2 };
+
+/* Forms of the hot path. */
+enum {
+    RT_FP64 = 0,  /* geodesic, plasma, coefficients and transfer all in FP64; output double */
+    RT_MIXED = 1  /* FP64 geodesic and path; FP32 plasma fetch, coefficients and transfer
+                     with compensated optical-depth and Faraday-phase sums; output float */
+};
+
+/* Per-pixel status codes written to the optional status buffer. */
+enum {
+    RT_RAY_HORIZON = 1,  /* reached r < 1.05 r_h */
+    RT_RAY_ESCAPE = 2,   /* left r > r_cam moving outward */
+    RT_RAY_NMAX = 3,     /* hit the step limit; the image keeps what was integrated */
+    RT_RAY_NAN = 4,      /* a non-finite state; the pixel is zero */
+    RT_RAY_OVERFLOW = 5  /* the path arena was full; the pixel is zero */
+};
+
+typedef struct rt_ctx rt_ctx;
+
+/* Semi-analytic ADAF: n_e = n0 r^-3/2 [cm^-3], T_e = T0/r [K], B^2/8pi = n_e k T_e
+ * (1 + Ti/Te)/beta, sub-Keplerian rotation f_kep l_K sin^2(theta) with infall from the
+ * normalisation, field direction along KS components (1, 0, 1/r); emission for r <= r_out. */
+typedef struct {
+    double n0, T0, beta, f_kep, Ti_over_Te, r_out;
+} rt_adaf_params;
+
+/* Gridded GRMHD primitives on a cell-centred FMKS grid (X1 = ln r in [ln r_in, ln r_out],
+ * X2 in [0, 1], X3 = phi in [0, 2 pi)). prims: n1*n2*n3*8 floats, layout
+ * [n1][n2][n3][8] = rho, u, U1, U2, U3, B1, B2, B3 (HARM conventions: U the velocity relative
+ * to the normal observer, B the field, both in FMKS components). The pointer may be host or
+ * device memory; it is copied during rt_load_model and the caller keeps ownership. */
+typedef struct {
+    int n1, n2, n3;
+    double r_in, r_out;
+    double hslope, poly_xt, poly_alpha, mks_smooth;
+    const float *prims;
+    double M_unit;       /* mass unit [g]: rho_unit = M_unit / L^3 */
+    double R_high, R_low;/* T_i/T_e = R_high b^2/(1+b^2) + R_low/(1+b^2), b = plasma beta */
+    double sigma_cut;    /* no emission where b^2/rho exceeds this */
+    double gamma_ad;     /* adiabatic index of the fluid */
+} rt_grid_params;
+
+typedef struct {
+    int kind; /* RT_MODEL_ADAF or RT_MODEL_GRID */
+    rt_adaf_params adaf;
+    rt_grid_params grid;
+} rt_model_params;
+
+/* Camera and image: a static observer at radius r_cam, inclination incl_deg, azimuth 0,
+ * looking at the hole through a pinhole image plane fov_M wide (square pixels). freq_hz is
+ * the observing frequency; M_bh_g and dist_cm set the length unit and the pixel solid angle. */
+typedef struct {
+    double a;         /* spin, |a| < 1 */
+    double incl_deg;  /* in (0, 180) */
+    double r_cam;
+    double freq_hz;
+    double fov_M;
+    int nx, ny;
+    double M_bh_g, dist_cm;
+} rt_camera;
+
+/* Counters of the last render, filled by rt_last_counters (which synchronizes). */
+typedef struct {
+    uint64_t rays, steps, points, emitting_points;
+    uint64_t arena_blocks_used, arena_blocks_total;
+    uint32_t n_horizon, n_escape, n_nmax, n_nan, n_overflow;
+    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events) */
+} rt_counters;
+
+/* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream). *out is owned by the caller and released with
+ * rt_destroy. */
+int rt_create(rt_ctx **out, int device, void *stream);
+int rt_destroy(rt_ctx *ctx);
+/* Change the stream later calls enqueue on. */
+int rt_set_stream(rt_ctx *ctx, void *stream);
+
+/* Load the plasma model (Section 2.1: semi-analytic prescription or GRMHD arrays).
+ * Grid primitives are copied to a context-owned device buffer. Synchronizes on the copy. */
+int rt_load_model(rt_ctx *ctx, const rt_model_params *p);
+
+/* Camera: spin, inclination, distance, frequency, field of view and resolution. */
+int rt_set_camera(rt_ctx *ctx, const rt_camera *cam);
+
+/* Geodesic step control: h = eps / (|K^r|/r + |K^th|/max(min(th, pi - th), 0.01) + |K^ph|),
+ * classic RK4, at most nmax steps per ray. Defaults: eps = 0.05, nmax = 20000. */
+int rt_set_integrator(rt_ctx *ctx, double eps, int nmax);
+
+/* Device workspace for the path arena and counters (bytes >= rt_workspace_min_bytes). The
+ * caller owns it; it must stay valid until the next rt_set_workspace or rt_destroy. Pass
+ * NULL to go back to a library-owned workspace. */
+int rt_set_workspace(rt_ctx *ctx, void *dev_ptr, size_t bytes);
+size_t rt_workspace_min_bytes(void);
+/* Workspace size the library would use for the current camera (a sizing hint). */
+int rt_workspace_hint(const rt_ctx *ctx, size_t *bytes);
+
+/* Render the IQUV image: out_iquv holds nx*ny*4 values, row-major [iy][ix][I,Q,U,V]
+ * (double for RT_FP64, float for RT_MIXED), host or device. Row iy = 0 is the bottom
+ * (image y = -FOV/2); x runs along +e_phi and y along -e_theta of the camera. Stokes Q is
+ * positive for E along x, and V > 0 for right-handed light in the IEEE/IAU sense. status:
+ * optional nx*ny uint8 per-pixel codes (host or device), or NULL. The rays are processed in
+ * chunks that fit the workspace. The call synchronizes the context's stream before it
+ * returns (it reads the ray counters). It returns RT_ERR_WORKSPACE if any ray overflowed the
+ * path arena; those pixels are zero with status RT_RAY_OVERFLOW. */
+int rt_render(rt_ctx *ctx, int form, void *out_iquv, uint8_t *status);
+
+/* Total flux [Jy] = sum(I) dOmega 1e23, dOmega = (fov_M L / (nx D))^2, and the net linear
+ * and circular polarization fractions sqrt(sum Q^2 + sum U^2)/sum I, sum V / sum I, from an
+ * image in `form` layout (host or device). A compensated device reduction; synchronizes. */
+int rt_image_stats(rt_ctx *ctx, const void *iquv, int form, double *flux_jy, double *lp_frac,
+                   double *cp_frac);
+
+/* Counters of the last rt_render (synchronizes). */
+int rt_last_counters(rt_ctx *ctx, rt_counters *out);
+
+const char *rt_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,442 @@
+// Host side of the C ABI (include/polrt.h): argument checks, buffers, chunking and launches.
+// All arithmetic of the method runs in the kernels. The host derives only constants of the
+// parameters (units, horizon radius, grid spacings).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "polrt.h"
+#include "rt_kernels.cuh"
+
+using namespace prt;
+
+namespace {
+constexpr size_t kAlign = 256;
+constexpr size_t kBlockBytes = sizeof(PathState) * kBlockStates + sizeof(int);
+constexpr int kBudgetBlocksPerRay = 20;  // 640 saved states per ray on average per chunk
+constexpr size_t kPerRayBytes = sizeof(RayRecord) + kBudgetBlocksPerRay * kBlockBytes;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+double r_isco(double a) {
+    double z1 = 1.0 + std::cbrt(1.0 - a * a) * (std::cbrt(1.0 + a) + std::cbrt(1.0 - a));
+    double z2 = std::sqrt(3.0 * a * a + z1 * z1);
+    return 3.0 + z2 - std::sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
+}
+}  // namespace
+
+struct rt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 1;
+    rt_camera cam{};
+    bool have_cam = false;
+    rt_model_params model{};
+    bool have_model = false;
+    float *d_prims = nullptr;
+    size_t prims_bytes = 0;
+    double *d_x2 = nullptr;
+    double eps = 0.05;
+    int nmax = 20000;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    void *d_stage = nullptr;
+    size_t stage_bytes = 0;
+    uint8_t *d_stage_status = nullptr;
+    size_t stage_status_bytes = 0;
+    double *d_stats = nullptr;
+    Counters *h_ctr = nullptr;  // pinned
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    long long last_rays = 0, last_blocks_total = 0;
+    int geo_bps = 1, fp64_bps = 1, mixed_bps = 1;
+};
+
+#define CK(x)                                 \
+    do {                                      \
+        if ((x) != cudaSuccess) {             \
+            cudaGetLastError();               \
+            return RT_ERR_CUDA;               \
+        }                                     \
+    } while (0)
+
+extern "C" {
+
+const char *rt_error_string(int code) {
+    switch (code) {
+        case RT_OK: return "ok";
+        case RT_ERR_INVALID: return "invalid argument";
+        case RT_ERR_CUDA: return "CUDA runtime error";
+        case RT_ERR_NOMEM: return "out of memory";
+        case RT_ERR_NOT_READY: return "model or camera not set";
+        case RT_ERR_WORKSPACE: return "path arena overflow: enlarge the workspace";
+        case RT_ERR_SIZE: return "size beyond the call's fixed limit";
+        default: return "unknown error";
+    }
+}
+
+size_t rt_workspace_min_bytes(void) { return align_up(sizeof(Counters)) + kPerRayBytes + kAlign; }
+
+int rt_create(rt_ctx **out, int device, void *stream) {
+    if (!out) return RT_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return RT_ERR_INVALID;
+    CK(cudaSetDevice(device));
+    rt_ctx *c = new (std::nothrow) rt_ctx();
+    if (!c) return RT_ERR_NOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return RT_ERR_CUDA;
+    }
+    c->nsm = prop.multiProcessorCount;
+    c->geo_bps = geodesic_blocks_per_sm();
+    c->fp64_bps = transfer_blocks_per_sm_fp64();
+    c->mixed_bps = transfer_blocks_per_sm_mixed();
+    bool ok = cudaMalloc(&c->d_stats, 8 * sizeof(double)) == cudaSuccess &&
+              cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; i++) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        rt_destroy(c);
+        return RT_ERR_CUDA;
+    }
+    memset(c->h_ctr, 0, sizeof(Counters));
+    *out = c;
+    return RT_OK;
+}
+
+int rt_destroy(rt_ctx *c) {
+    if (!c) return RT_ERR_INVALID;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_prims);
+    cudaFree(c->d_x2);
+    if (c->ws_owned) cudaFree(c->ws);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_stage_status);
+    cudaFree(c->d_stats);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    for (int i = 0; i < 3; i++)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    cudaGetLastError();
+    delete c;
+    return RT_OK;
+}
+
+int rt_set_stream(rt_ctx *c, void *stream) {
+    if (!c) return RT_ERR_INVALID;
+    c->stream = (cudaStream_t)stream;
+    return RT_OK;
+}
+
+int rt_set_integrator(rt_ctx *c, double eps, int nmax) {
+    if (!c || !(eps > 0.0) || !(eps < 1.0) || nmax < 1) return RT_ERR_INVALID;
+    c->eps = eps;
+    c->nmax = nmax;
+    return RT_OK;
+}
+
+int rt_set_camera(rt_ctx *c, const rt_camera *cam) {
+    if (!c || !cam) return RT_ERR_INVALID;
+    if (!(std::fabs(cam->a) < 1.0) || !(cam->incl_deg > 0.0 && cam->incl_deg < 180.0) || cam->nx < 1 ||
+        cam->ny < 1 || !(cam->freq_hz > 0.0) || !(cam->fov_M > 0.0) || !(cam->M_bh_g > 0.0) || !(cam->dist_cm > 0.0))
+        return RT_ERR_INVALID;
+    double rh = 1.0 + std::sqrt(1.0 - cam->a * cam->a);
+    if (!(cam->r_cam > 2.0 * rh)) return RT_ERR_INVALID;
+    if ((long long)cam->nx * cam->ny > (1ll << 31)) return RT_ERR_SIZE;
+    c->cam = *cam;
+    c->have_cam = true;
+    return RT_OK;
+}
+
+int rt_load_model(rt_ctx *c, const rt_model_params *p) {
+    if (!c || !p) return RT_ERR_INVALID;
+    CK(cudaSetDevice(c->device));
+    if (p->kind == RT_MODEL_ADAF) {
+        const rt_adaf_params &a = p->adaf;
+        if (!(a.n0 > 0) || !(a.T0 > 0) || !(a.beta > 0) || !(a.Ti_over_Te >= 0) || !(a.r_out > 0))
+            return RT_ERR_INVALID;
+    } else if (p->kind == RT_MODEL_GRID) {
+        const rt_grid_params &g = p->grid;
+        if (g.n1 < 2 || g.n2 < 2 || g.n3 < 1 || !g.prims || !(g.r_in > 0) || !(g.r_out > g.r_in) ||
+            !(g.M_unit > 0) || !(g.gamma_ad > 1.0) || !(g.poly_alpha > 0) || !(g.poly_xt > 0))
+            return RT_ERR_INVALID;
+        size_t bytes = (size_t)g.n1 * g.n2 * g.n3 * 8 * sizeof(float);
+        if (bytes != c->prims_bytes) {
+            cudaFree(c->d_prims);
+            c->d_prims = nullptr;
+            c->prims_bytes = 0;
+            if (cudaMalloc(&c->d_prims, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return RT_ERR_NOMEM;
+            }
+            c->prims_bytes = bytes;
+        }
+        cudaMemcpyKind kind = is_device_ptr(g.prims) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpyAsync(c->d_prims, g.prims, bytes, kind, c->stream));
+        if (!c->d_x2) {
+            if (cudaMalloc(&c->d_x2, sizeof(double) * kX2TabW * kX2TabT) != cudaSuccess) {
+                cudaGetLastError();
+                return RT_ERR_NOMEM;
+            }
+        }
+        GridModel gm{};
+        gm.hslope = g.hslope;
+        gm.poly_xt = g.poly_xt;
+        gm.poly_alpha = g.poly_alpha;
+        gm.mks_smooth = g.mks_smooth;
+        gm.poly_norm = 0.5 * kPi / (1.0 + 1.0 / ((g.poly_alpha + 1.0) * std::pow(g.poly_xt, g.poly_alpha)));
+        launch_x2_table(gm, c->d_x2, c->stream);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        return RT_ERR_INVALID;
+    }
+    c->model = *p;
+    c->model.grid.prims = nullptr;  // the device copy is used from here on
+    c->have_model = true;
+    return RT_OK;
+}
+
+int rt_set_workspace(rt_ctx *c, void *dev_ptr, size_t bytes) {
+    if (!c) return RT_ERR_INVALID;
+    if (dev_ptr && bytes < rt_workspace_min_bytes()) return RT_ERR_INVALID;
+    if (dev_ptr && ((uintptr_t)dev_ptr % kAlign) != 0) return RT_ERR_INVALID;
+    if (c->ws_owned) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->ws);
+    }
+    c->ws = dev_ptr;
+    c->ws_bytes = dev_ptr ? bytes : 0;
+    c->ws_owned = false;
+    return RT_OK;
+}
+
+int rt_workspace_hint(const rt_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return RT_ERR_INVALID;
+    if (!c->have_cam) return RT_ERR_NOT_READY;
+    long long nrays = (long long)c->cam.nx * c->cam.ny;
+    *bytes = align_up(sizeof(Counters)) + (size_t)nrays * kPerRayBytes + kAlign;
+    return RT_OK;
+}
+
+static int ensure_workspace(rt_ctx *c, long long nrays) {
+    if (c->ws && !c->ws_owned) return RT_OK;
+    size_t want = align_up(sizeof(Counters)) + (size_t)nrays * kPerRayBytes + kAlign;
+    size_t freeb = 0, total = 0;
+    CK(cudaMemGetInfo(&freeb, &total));
+    size_t avail = c->ws_bytes + (size_t)(0.6 * (double)freeb);
+    size_t bytes = std::min(want, avail);
+    if (bytes < rt_workspace_min_bytes()) return RT_ERR_NOMEM;
+    if (c->ws_owned && c->ws_bytes >= bytes) return RT_OK;
+    if (c->ws_owned) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_NOMEM;
+    }
+    c->ws_bytes = bytes;
+    c->ws_owned = true;
+    return RT_OK;
+}
+
+static int ensure_stage(void **buf, size_t *have, size_t need) {
+    if (*have >= need) return RT_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_NOMEM;
+    }
+    *have = need;
+    return RT_OK;
+}
+
+int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
+    if (!c || !out_iquv || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
+    if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    const rt_camera &rc = c->cam;
+    long long nrays = (long long)rc.nx * rc.ny;
+    int rv = ensure_workspace(c, nrays);
+    if (rv) return rv;
+
+    // camera and model in kernel form
+    Camera cam{};
+    cam.a = rc.a;
+    cam.r_cam = rc.r_cam;
+    cam.theta_o = rc.incl_deg * kPi / 180.0;
+    cam.nu_obs = rc.freq_hz;
+    cam.fov = rc.fov_M;
+    cam.L_unit = kG * rc.M_bh_g / (kC * kC);
+    cam.nx = rc.nx;
+    cam.ny = rc.ny;
+    cam.eps = c->eps;
+    cam.nmax = c->nmax;
+    cam.rh = 1.0 + std::sqrt(1.0 - rc.a * rc.a);
+    Model mod{};
+    mod.kind = c->model.kind;
+    if (mod.kind == RT_MODEL_ADAF) {
+        const rt_adaf_params &a = c->model.adaf;
+        mod.adaf = AdafModel{a.n0, a.T0, a.beta, a.f_kep, a.Ti_over_Te, a.r_out, r_isco(rc.a)};
+    } else {
+        const rt_grid_params &g = c->model.grid;
+        GridModel &gm = mod.grid;
+        gm.n1 = g.n1;
+        gm.n2 = g.n2;
+        gm.n3 = g.n3;
+        gm.r_in = g.r_in;
+        gm.r_out = g.r_out;
+        gm.x1in = std::log(g.r_in);
+        gm.dx1 = (std::log(g.r_out) - gm.x1in) / g.n1;
+        gm.dx2 = 1.0 / g.n2;
+        gm.dx3 = 2.0 * kPi / g.n3;
+        gm.hslope = g.hslope;
+        gm.poly_xt = g.poly_xt;
+        gm.poly_alpha = g.poly_alpha;
+        gm.mks_smooth = g.mks_smooth;
+        gm.poly_norm = 0.5 * kPi / (1.0 + 1.0 / ((g.poly_alpha + 1.0) * std::pow(g.poly_xt, g.poly_alpha)));
+        gm.prims = reinterpret_cast<const float4 *>(c->d_prims);
+        gm.x2_table = c->d_x2;
+        double L = cam.L_unit;
+        gm.rho_unit = g.M_unit / (L * L * L);
+        gm.b_unit = kC * std::sqrt(4.0 * kPi * gm.rho_unit);
+        gm.ne_unit = gm.rho_unit / (kMp + kMe);
+        gm.R_high = g.R_high;
+        gm.R_low = g.R_low;
+        gm.sigma_cut = g.sigma_cut;
+        gm.gamma_ad = g.gamma_ad;
+    }
+
+    // workspace carving
+    char *base = (char *)c->ws;
+    Counters *ctr = (Counters *)base;
+    size_t off = align_up(sizeof(Counters));
+    size_t room = c->ws_bytes - off - kAlign;
+    long long chunk = std::min<long long>(nrays, (long long)(room / kPerRayBytes));
+    if (chunk < 1) return RT_ERR_NOMEM;
+    RayRecord *rec = (RayRecord *)(base + off);
+    off = align_up(off + sizeof(RayRecord) * chunk);
+    long long nblocks = (long long)((c->ws_bytes - off - kAlign) / kBlockBytes);
+    Arena ar;
+    ar.states = (PathState *)(base + off);
+    ar.prev = (int *)(base + off + (size_t)nblocks * sizeof(PathState) * kBlockStates);
+    ar.nblocks = nblocks;
+
+    // outputs: device directly, or staged
+    size_t esz = form == RT_FP64 ? sizeof(double) : sizeof(float);
+    bool out_dev = is_device_ptr(out_iquv);
+    bool st_dev = status ? is_device_ptr(status) : true;
+    void *d_out = out_iquv;
+    uint8_t *d_status = status;
+    if (!out_dev) {
+        rv = ensure_stage(&c->d_stage, &c->stage_bytes, (size_t)nrays * 4 * esz);
+        if (rv) return rv;
+        d_out = c->d_stage;
+    }
+    if (status && !st_dev) {
+        rv = ensure_stage((void **)&c->d_stage_status, &c->stage_status_bytes, (size_t)nrays);
+        if (rv) return rv;
+        d_status = c->d_stage_status;
+    }
+
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
+    int geo_grid = c->nsm * c->geo_bps;
+    int xf_grid = c->nsm * (form == RT_FP64 ? c->fp64_bps : c->mixed_bps);
+    for (long long o = 0; o < nrays; o += chunk) {
+        long long n = std::min(chunk, nrays - o);
+        CK(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), c->stream));  // queues + arena
+        GeoArgs ga{cam, ar, rec, ctr, n, o};
+        XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status};
+        if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
+        launch_geodesic(ga, geo_grid, c->stream);
+        if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
+        if (form == RT_FP64)
+            launch_transfer_fp64(xa, xf_grid, c->stream);
+        else
+            launch_transfer_mixed(xa, xf_grid, c->stream);
+        CK(cudaGetLastError());
+    }
+    CK(cudaEventRecord(c->ev[2], c->stream));
+    if (!out_dev) CK(cudaMemcpyAsync(out_iquv, d_out, (size_t)nrays * 4 * esz, cudaMemcpyDeviceToHost, c->stream));
+    if (status && !st_dev)
+        CK(cudaMemcpyAsync(status, d_status, (size_t)nrays, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->last_rays = nrays;
+    c->last_blocks_total = nblocks;
+    if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
+    return RT_OK;
+}
+
+int rt_image_stats(rt_ctx *c, const void *iquv, int form, double *flux_jy, double *lp_frac, double *cp_frac) {
+    if (!c || !iquv || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
+    if (!c->have_cam) return RT_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    long long npix = (long long)c->cam.nx * c->cam.ny;
+    size_t esz = form == RT_FP64 ? sizeof(double) : sizeof(float);
+    const void *d_img = iquv;
+    if (!is_device_ptr(iquv)) {
+        int rv = ensure_stage(&c->d_stage, &c->stage_bytes, (size_t)npix * 4 * esz);
+        if (rv) return rv;
+        CK(cudaMemcpyAsync(c->d_stage, iquv, (size_t)npix * 4 * esz, cudaMemcpyHostToDevice, c->stream));
+        d_img = c->d_stage;
+    }
+    double L = kG * c->cam.M_bh_g / (kC * kC);
+    double pix = c->cam.fov_M * L / (c->cam.nx * c->cam.dist_cm);
+    launch_image_sums(d_img, form == RT_FP64 ? 0 : 1, npix, pix * pix, c->d_stats, c->stream);
+    CK(cudaGetLastError());
+    double h[8];
+    CK(cudaMemcpyAsync(h, c->d_stats, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (flux_jy) *flux_jy = h[4];
+    if (lp_frac) *lp_frac = h[5];
+    if (cp_frac) *cp_frac = h[6];
+    return RT_OK;
+}
+
+int rt_last_counters(rt_ctx *c, rt_counters *out) {
+    if (!c || !out) return RT_ERR_INVALID;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    const Counters &k = *c->h_ctr;
+    memset(out, 0, sizeof(*out));
+    out->rays = (uint64_t)c->last_rays;
+    out->steps = k.steps;
+    out->points = k.points;
+    out->emitting_points = k.emitting;
+    out->arena_blocks_used = k.arena_next;
+    out->arena_blocks_total = (uint64_t)c->last_blocks_total;
+    out->n_horizon = k.n_status[kHorizon];
+    out->n_escape = k.n_status[kEscape];
+    out->n_nmax = k.n_status[kNmax];
+    out->n_nan = k.n_status[kNan];
+    out->n_overflow = k.n_status[kOverflow];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out->ms_geodesic = ms;
+    if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) out->ms_transfer = ms;
+    cudaGetLastError();
+    return RT_OK;
+}
+
+}  // extern "C"

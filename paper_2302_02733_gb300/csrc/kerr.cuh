@@ -1,0 +1,176 @@
+// Kerr geometry in spherical Kerr-Schild coordinates (t, r, theta, phi), G = c = M = 1.
+//
+// With Sigma = r^2 + a^2 cos^2, q = 2r/Sigma and the Kerr-Schild null form
+// l_mu = (1, 1, 0, -a sin^2), the metric is g = (oblate flat part) + q l l:
+//   g_tt = -1 + q, g_tr = q, g_tphi = -a s^2 q, g_rr = 1 + q, g_rphi = -a s^2 (1 + q),
+//   g_thth = Sigma, g_phiphi = s^2 (Sigma + a^2 s^2 (1 + q)),
+// and the inverse is g^tt = -(1 + q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
+// g^thth = 1/Sigma, g^phiphi = 1/(Sigma s^2).
+//
+// Only r and theta enter, so every connection contraction is built from the two partial
+// derivatives of g. The geodesic acceleration -Gamma^mu_ab K^a K^b = -g^{mu nu}(A_nu - B_nu),
+// with A_nu = (K^a d_a g_{nu b}) K^b and B_nu = 1/2 d_nu g_ab K^a K^b, is evaluated
+// directly, without forming the 40 connection coefficients.
+#pragma once
+#include "rt_common.cuh"
+
+namespace prt {
+
+template <typename R>
+struct Fn;
+template <>
+struct Fn<double> {
+    static __device__ __forceinline__ void sc(double x, double *s, double *c) { sincos(x, s, c); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+};
+template <>
+struct Fn<float> {
+    static __device__ __forceinline__ void sc(float x, float *s, float *c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rcp(float x) { return 1.0f / x; }
+};
+
+// Metric, inverse and the two derivative sets at (r, theta).
+template <typename R>
+struct KS {
+    R a, r, s, c, s2, sc, sig, isig, iss, q, op, dqr, dqt;
+    R tt, tr, tp, rr, rp, hh, pp;  // g_{mu nu}
+    R Itt, Itr, Irr, Irp, Ihh, Ipp;  // g^{mu nu}
+
+    __device__ __forceinline__ void eval(R a_, R r_, R th) {
+        a = a_;
+        r = r_;
+        Fn<R>::sc(th, &s, &c);
+        s2 = s * s;
+        sc = s * c;
+        R a2 = a * a;
+        sig = r * r + a2 * c * c;
+        iss = Fn<R>::rcp(sig * s2);
+        isig = iss * s2;
+        q = R(2) * r * isig;
+        op = R(1) + q;
+        dqr = R(2) * isig - q * q;
+        dqt = R(2) * a2 * sc * q * isig;
+        tt = q - R(1);
+        tr = q;
+        tp = -a * s2 * q;
+        rr = op;
+        rp = -a * s2 * op;
+        hh = sig;
+        pp = s2 * (sig + a2 * s2 * op);
+        Itt = -op;
+        Itr = q;
+        Irr = (r * r - R(2) * r + a2) * isig;
+        Irp = a * isig;
+        Ihh = isig;
+        Ipp = iss;
+    }
+    __device__ __forceinline__ R dot(const R u[4], const R v[4]) const {
+        return tt * u[0] * v[0] + tr * (u[0] * v[1] + u[1] * v[0]) + tp * (u[0] * v[3] + u[3] * v[0]) +
+               rr * u[1] * v[1] + rp * (u[1] * v[3] + u[3] * v[1]) + hh * u[2] * v[2] + pp * u[3] * v[3];
+    }
+    __device__ __forceinline__ void lower(const R u[4], R l[4]) const {
+        l[0] = tt * u[0] + tr * u[1] + tp * u[3];
+        l[1] = tr * u[0] + rr * u[1] + rp * u[3];
+        l[2] = hh * u[2];
+        l[3] = tp * u[0] + rp * u[1] + pp * u[3];
+    }
+    __device__ __forceinline__ void raise(const R l[4], R u[4]) const {
+        u[0] = Itt * l[0] + Itr * l[1];
+        u[1] = Itr * l[0] + Irr * l[1] + Irp * l[3];
+        u[2] = Ihh * l[2];
+        u[3] = Irp * l[1] + Ipp * l[3];
+    }
+    __device__ __forceinline__ R sqrt_mg() const { return sig * s; }  // sqrt(-g) = Sigma sin
+};
+
+// Contractions of the metric derivatives with a vector K:
+//   D_{nu b} = K^r d_r g_{nu b} + K^th d_th g_{nu b}   (7 unique entries)
+//   P_nu = d_r g_{nu a} K^a,  Q_nu = d_th g_{nu a} K^a.
+template <typename R>
+struct DK {
+    R d1, dtp, drp, dhh, dpp;  // D_tt = D_tr = D_rr = d1
+    R P[4], Qv[4];
+    __device__ __forceinline__ void eval(const KS<R> &m, const R K[4]) {
+        R a = m.a, a2 = a * a;
+        R W = K[0] + K[1];
+        R V = W - a * m.s2 * K[3];
+        d1 = K[1] * m.dqr + K[2] * m.dqt;
+        R two_sc = R(2) * m.sc;
+        dtp = -a * (m.s2 * d1 + two_sc * m.q * K[2]);
+        drp = -a * (m.s2 * d1 + two_sc * m.op * K[2]);
+        dhh = R(2) * m.r * K[1] - R(2) * a2 * m.sc * K[2];
+        R bigp = m.sig + a2 * m.s2 * (R(1) + R(2) * m.q);
+        dpp = R(2) * m.r * m.s2 * K[1] + a2 * m.s2 * m.s2 * d1 + two_sc * bigp * K[2];
+        P[0] = m.dqr * V;
+        P[1] = P[0];
+        P[2] = R(2) * m.r * K[2];
+        P[3] = -a * m.s2 * m.dqr * V + R(2) * m.r * m.s2 * K[3];
+        Qv[0] = m.dqt * V - two_sc * a * m.q * K[3];
+        Qv[1] = m.dqt * V - two_sc * a * m.op * K[3];
+        Qv[2] = -R(2) * a2 * m.sc * K[2];
+        Qv[3] = -a * m.s2 * m.dqt * V - two_sc * a * (m.q * K[0] + m.op * K[1]) + two_sc * bigp * K[3];
+    }
+    // D_{nu b} as a full symmetric 4x4 accessor
+    __device__ __forceinline__ R D(int n, int b) const {
+        if (n > b) { int t = n; n = b; b = t; }
+        if (n == 2 || b == 2) return (n == 2 && b == 2) ? dhh : R(0);
+        if (b == 3) return n == 0 ? dtp : (n == 1 ? drp : dpp);
+        return d1;  // (0,0), (0,1), (1,1)
+    }
+};
+
+// Geodesic acceleration dK/dl = -Gamma K K (FP64 path).
+__device__ __forceinline__ void geo_accel(double a, double r, double th, const double K[4], double acc[4]) {
+    KS<double> m;
+    m.eval(a, r, th);
+    DK<double> d;
+    d.eval(m, K);
+    double W = K[0] + K[1];
+    double At = d.d1 * W + d.dtp * K[3];
+    double Ar = d.d1 * W + d.drp * K[3];
+    double Ah = d.dhh * K[2];
+    double Ap = d.dtp * K[0] + d.drp * K[1] + d.dpp * K[3];
+    // B_nu = 1/2 d_nu g_ab K^a K^b = 1/2 K.P (nu = r), 1/2 K.Q (nu = theta)
+    double Br = 0.5 * (d.P[0] * K[0] + d.P[1] * K[1] + d.P[2] * K[2] + d.P[3] * K[3]);
+    double Bh = 0.5 * (d.Qv[0] * K[0] + d.Qv[1] * K[1] + d.Qv[2] * K[2] + d.Qv[3] * K[3]);
+    double F[4] = {At, Ar - Br, Ah - Bh, Ap};
+    double u[4];
+    m.raise(F, u);
+    acc[0] = -u[0];
+    acc[1] = -u[1];
+    acc[2] = -u[2];
+    acc[3] = -u[3];
+}
+
+// T^mu_b = Gamma^mu_{a b} K^a = 1/2 g^{mu nu} (D_{nu b} + [b=r] P_nu + [b=th] Q_nu
+//                                              - [nu=r] P_b - [nu=th] Q_b).
+template <typename R>
+__device__ __forceinline__ void connection_T(const KS<R> &m, const R K[4], R T[4][4]) {
+    DK<R> d;
+    d.eval(m, K);
+    R M[4][4];
+#pragma unroll
+    for (int n = 0; n < 4; n++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            R v = d.D(n, b);
+            if (b == 1) v += d.P[n];
+            if (b == 2) v += d.Qv[n];
+            if (n == 1) v -= d.P[b];
+            if (n == 2) v -= d.Qv[b];
+            M[n][b] = v;
+        }
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        R col[4] = {M[0][b], M[1][b], M[2][b], M[3][b]}, up[4];
+        m.raise(col, up);
+        T[0][b] = R(0.5) * up[0];
+        T[1][b] = R(0.5) * up[1];
+        T[2][b] = R(0.5) * up[2];
+        T[3][b] = R(0.5) * up[3];
+    }
+}
+
+}  // namespace prt

@@ -1,0 +1,109 @@
+// Device-side shared definitions of the polrt CUDA library (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace prt {
+
+// cgs constants (CODATA 2018)
+constexpr double kG = 6.67430e-8;
+constexpr double kC = 2.99792458e10;
+constexpr double kMe = 9.1093837015e-28;
+constexpr double kMp = 1.67262192369e-24;
+constexpr double kQe = 4.80320471257e-10;
+constexpr double kKb = 1.380649e-16;
+constexpr double kH = 6.62607015e-27;
+constexpr double kPi = 3.14159265358979323846;
+
+enum RayStatus : uint8_t { kHorizon = 1, kEscape = 2, kNmax = 3, kNan = 4, kOverflow = 5 };
+
+// One saved geodesic state: r, theta, phi, K^t, K^r, K^theta, K^phi and the step h taken
+// from it (negative when that step was reflected through the polar axis). 64 bytes.
+struct __align__(16) PathState {
+    double r, th, ph, kt, kr, kth, kph, h;
+};
+
+// The path arena: fixed-size blocks of kBlockStates states, handed out by a bump counter.
+// Each block records the block that precedes it on the same ray, so the transfer can walk
+// a ray's states backward.
+constexpr int kBlockStates = 32;
+
+struct Camera {
+    double a, r_cam, theta_o, nu_obs, fov, L_unit;
+    int nx, ny;
+    double eps;
+    int nmax;
+    double rh;             // outer horizon radius
+};
+
+struct AdafModel {
+    double n0, T0, beta, f_kep, ti_te, r_out, r_isco;
+};
+
+struct GridModel {
+    int n1, n2, n3;
+    double r_in, r_out, x1in, dx1, dx2, dx3;
+    double hslope, poly_xt, poly_alpha, mks_smooth, poly_norm;
+    const float4 *prims;   // [n1][n2][n3] cells of two float4: (rho,u,U1,U2),(U3,B1,B2,B3)
+    const double *x2_table;  // inverse FMKS guess table [kX2TabW][kX2TabT]
+    double rho_unit, b_unit, ne_unit, R_high, R_low, sigma_cut, gamma_ad;
+};
+constexpr int kX2TabW = 64;     // blend weight w = exp(s (X1_in - X1)) in [0, 1]
+constexpr int kX2TabT = 1024;   // theta in [0, pi]
+
+struct Model {
+    int kind;  // 1 ADAF, 2 grid
+    AdafModel adaf;
+    GridModel grid;
+};
+
+struct Counters {
+    unsigned long long geo_next, xfer_next;   // work-queue heads
+    unsigned long long arena_next;            // next free arena block
+    unsigned long long steps, points, emitting;
+    unsigned int n_status[8];
+};
+
+struct RayRecord {
+    int last_block;  // arena block holding the last state, -1 if none
+    int nstates;     // saved states (steps + 1); 0 if the ray has no usable path
+    int status;      // RayStatus
+    int pad;
+};
+
+struct Arena {
+    PathState *states;   // nblocks * kBlockStates
+    int *prev;           // nblocks: previous block of the same ray, -1 for the first
+    long long nblocks;
+};
+
+// --------------------------------------------------------------------------------------
+// Warp-aggregated pop of `want` lanes from a global queue: returns each requesting lane's
+// ticket (>= limit means empty).
+__device__ __forceinline__ unsigned long long warp_pop(unsigned long long *head, bool want) {
+    unsigned mask = __ballot_sync(0xffffffffu, want);
+    unsigned long long base = 0;
+    int leader = __ffs(mask) - 1;
+    int lane = threadIdx.x & 31;
+    if (mask) {
+        if (lane == leader) base = atomicAdd(head, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+    }
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// Pixel of ray `id`: rays are numbered in 8x4 tiles so that a warp's rays are neighbours.
+__device__ __forceinline__ void ray_pixel(long long id, int nx, int ny, int &ix, int &iy) {
+    if ((nx & 7) == 0 && (ny & 3) == 0) {
+        long long tile = id >> 5;
+        int l = (int)(id & 31);
+        int tx = (int)(tile % (nx >> 3)), ty = (int)(tile / (nx >> 3));
+        ix = tx * 8 + (l & 7);
+        iy = ty * 4 + (l >> 3);
+    } else {
+        ix = (int)(id % nx);
+        iy = (int)(id / nx);
+    }
+}
+
+}  // namespace prt

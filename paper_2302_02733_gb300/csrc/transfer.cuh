@@ -1,0 +1,608 @@
+// Forward polarized transfer along the saved geodesic (the paper's Section 2.1: the covariant,
+// fully polarized transfer equations are integrated toward the observer; plasma quantities are
+// interpolated or computed at every point; the coherency matrix lives in the coordinate frame).
+//
+// Representation. The coherency tensor after each radiative step is rank two in the screen
+// of the fluid frame: N^{mu nu} = sum_ab n^{ab} E_a^mu E_b^nu with the 2x2 coherency n built
+// from the Stokes vector S and the screen legs (E_1, E_2). Parallel transport of N by the
+// Heun propagator P (each index as a vector) therefore equals transporting E_1 and E_2 by
+// Heun and keeping S. Projecting onto the next fluid screen (e_1', e_2') is the 2x2 congruence
+// n' = C n C^T with C_{a'a} = e_a' . E_a, which keeps n positive semi-definite (I >= |P|).
+//
+// Templated on the transfer precision R: double for the FP64 form, float for the mixed form
+// (the path itself is always the FP64 geodesic).
+#pragma once
+#include "camera.cuh"
+#include "rt_kernels.cuh"
+
+namespace prt {
+
+// ------------------------------------------------------------------------------------------
+// precision-dispatched math
+template <typename R>
+struct Mth;
+template <>
+struct Mth<double> {
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+    static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+    static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
+    static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
+    static __device__ __forceinline__ double sin_(double x) { return sin(x); }
+    static __device__ __forceinline__ double cos_(double x) { return cos(x); }
+    static __device__ __forceinline__ double sinh_(double x) { return sinh(x); }
+    static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+    static __device__ __forceinline__ double fmod_(double x, double y) { return fmod(x, y); }
+    static constexpr double jflush = 1e-250;  // emissivity below this carries no precision
+    static constexpr int taylor_max = 24;
+    static constexpr double taylor_tol = 1e-17;
+    static constexpr double degen_D = 1e-9, degen_tp = 1e-3;
+};
+template <>
+struct Mth<float> {
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+    static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float tanh_(float x) { return tanhf(x); }
+    static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
+    static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
+    static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
+    static __device__ __forceinline__ float sinh_(float x) { return sinhf(x); }
+    static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+    static __device__ __forceinline__ float fmod_(float x, float y) { return fmodf(x, y); }
+    static constexpr float jflush = 1e-35f;
+    static constexpr int taylor_max = 14;
+    static constexpr float taylor_tol = 3e-8f;
+    static constexpr float degen_D = 1e-4f, degen_tp = 1e-2f;
+};
+
+// ------------------------------------------------------------------------------------------
+// e^z K_n(z), n = 0, 1, 2.
+//   z < 2: ascending series (Abramowitz & Stegun 9.6.11, 9.6.13),
+//     K0 = -(ln(z/2) + gamma) I0 + sum H_k t^k/(k!)^2,
+//     K1 = 1/z + (ln(z/2) + gamma) I1 - (z/4) sum (H_k + H_{k+1}) t^k/(k!(k+1)!),  t = z^2/4;
+//   z >= 2: with u = sqrt(2z) sinh(s/2) in K_n = int_0^inf e^{-z cosh s} cosh(ns) ds,
+//     e^z K_n(z) = sqrt(2/z) int_0^inf e^{-u^2} c_n(u) / sqrt(1 + u^2/(2z)) du,
+//     c_0 = 1, c_1 = 1 + u^2/z, c_2 = 2 c_1^2 - 1, by the trapezoid rule on fixed nodes u_k = k h
+//     (the integrand is analytic in |Im u| < sqrt(2z), so the rule converges geometrically).
+//   K2 = K0 + (2/z) K1 for the series branch.
+template <typename R>
+struct BesselCfg;
+template <>
+struct BesselCfg<double> {
+    static constexpr int nser = 14, nq = 27;
+    static constexpr double h = 0.25;
+};
+template <>
+struct BesselCfg<float> {
+    static constexpr int nser = 8, nq = 10;
+    static constexpr float h = 0.5f;
+};
+
+// gw[k] = exp(-(k h)^2), halved at k = 0 (trapezoid end weight); kept in shared memory.
+template <typename R>
+__device__ __forceinline__ void bessel_k012_scaled(R z, const R *gw, R &k0, R &k1, R &k2) {
+    typedef Mth<R> F;
+    typedef BesselCfg<R> B;
+    R iz = R(1) / z;
+    if (z < R(2)) {
+        R hz = R(0.5) * z, t = hz * hz;
+        R lg = F::log_(hz) + R(0.57721566490153286061);
+        R i0 = 0, s0 = 0, i1s = 0, s1 = 0, term0 = 1, term1 = 1, H = 0;
+#pragma unroll
+        for (int k = 0; k < B::nser; k++) {
+            R ik1 = R(1) / R(k + 1);
+            i0 += term0;
+            s0 += H * term0;
+            i1s += term1;
+            s1 += (R(2) * H + ik1) * term1;
+            H += ik1;
+            term0 *= t * ik1 * ik1;
+            term1 *= t * ik1 / R(k + 2);
+        }
+        R e = F::exp_(z);
+        R K0 = -lg * i0 + s0;
+        R K1 = iz + lg * (hz * i1s) - R(0.25) * z * s1;
+        k0 = K0 * e;
+        k1 = K1 * e;
+        k2 = k0 + R(2) * iz * k1;
+    } else {
+        R i2z = R(0.5) * iz;
+        R a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int k = 0; k < B::nq; k++) {
+            R u = R(k) * B::h, u2 = u * u;
+            R w = gw[k];
+            R rr = w * F::rsqrt_(R(1) + u2 * i2z);
+            R c1 = R(1) + u2 * iz;
+            a0 += rr;
+            a1 += rr * c1;
+            a2 += rr * (R(2) * c1 * c1 - R(1));
+        }
+        R sc = F::sqrt_(R(2) * iz) * B::h;
+        k0 = sc * a0;
+        k1 = sc * a1;
+        k2 = sc * a2;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Thermal synchrotron coefficients in the fluid frame (cgs).
+// Emission: the Dexter (2016) fits with nu_c = (3/2) nu_B sin(th) Theta^2, x = nu/nu_c:
+//   j_I = n e^2 nu/(2 sqrt3 c Theta^2) 2.5651 (1 + 1.92 x^-1/3 + 0.9977 x^-2/3) e^{-1.8899 x^1/3},
+//   j_Q = same with (1 + 0.93193 x^-1/3 + 0.499873 x^-2/3),
+//   j_V = 2 n e^2 nu cot(th)/(3 sqrt3 c Theta^3) (1.81348/x + 3.42319 x^-2/3 + 0.0292545 x^-1/2
+//         + 2.03773 x^-1/3) e^{-1.8899 x^1/3};
+// absorption from Kirchhoff's law a_S = j_S / B_nu(T_e); rotativities from the Shcherbakov
+// (2008) fits with X = Theta sqrt(sqrt2 sin(th) 1e3 nu_B/nu):
+//   rho_V = 2 n e^2 nu_B cos(th)/(m c nu^2) K0/K2 (1 - 0.11 ln(1 + 0.035 X)),
+//   rho_Q = n e^2 nu_B^2 sin^2(th)/(m c nu^3) f_m(X) (K1/K2 + 6 Theta).
+// Stokes Q is positive across the projected field, so j_U = a_U = rho_U = 0. Emissivities
+// below a flush level are zeroed with their absorption, and (j_Q, j_V) are scaled back inside
+// the light cone |j_P| <= j_I where the fits are used out of range.
+// out: jI jQ jV aI aQ aV rQ rV
+template <typename R>
+__device__ __forceinline__ void thermal_coeffs(R ne, R Te, R B, R nu, R sth, R cth, const R *gw, R out[8]) {
+    typedef Mth<R> F;
+#pragma unroll
+    for (int i = 0; i < 8; i++) out[i] = R(0);
+    if (!(ne > R(0)) || !(Te > R(0)) || !(B > R(0))) return;
+    const R cB = R(kQe / (2.0 * kPi * kMe * kC));        // nu_B / B
+    const R cQ2 = R(kQe * kQe / (kMe * kC));             // e^2 / (m c)
+    const R cJ = R(kQe * kQe / (2.0 * 1.7320508075688772 * kC));
+    const R cJV = R(2.0 * kQe * kQe / (3.0 * 1.7320508075688772 * kC));
+    const R cT = R(kH / (kMe * kC * kC));                // h nu / (m c^2 Theta) = cT nu / Theta
+    const R c2h = R(2.0 * kH);
+    const R ic = R(1.0 / kC);
+    R nuB = cB * B;
+    R rb = nuB / nu;
+    R X = Te * F::sqrt_(R(1.4142135623730951) * sth * R(1e3) * rb);
+    R k0, k1, k2;
+    bessel_k012_scaled<R>(R(1) / Te, gw, k0, k1, k2);
+    R f = R(2.011) * F::exp_(-F::pow_(X, R(1.035)) / R(4.7)) -
+          F::cos_(R(0.5) * X) * F::exp_(-F::pow_(X, R(1.2)) / R(2.73)) - R(0.011) * F::exp_(-X / R(47.2));
+    if (X > R(1))
+        f += (R(0.011) * F::exp_(-X / R(47.2)) -
+              R(0.7937005259840998 / 67.40655678327585 * 1.0e4 * kPi) * F::pow_(X, R(-8.0 / 3.0))) *
+             R(0.5) * (R(1) + F::tanh_(R(10) * F::log_(X / R(120))));
+    R gX = R(1) - R(0.11) * F::log1p_(R(0.035) * X);
+    out[6] = cQ2 * ne * rb * rb / nu * sth * sth * f * (k1 / k2 + R(6) * Te);
+    out[7] = R(2) * cQ2 * ne * rb / nu * cth * (k0 / k2) * gX;
+    if (sth < R(1e-12)) return;
+    R nuc = R(1.5) * nuB * sth * Te * Te;
+    R x = nu / nuc;
+    R x13 = F::cbrt_(x), ix13 = R(1) / x13, ix23 = ix13 * ix13;
+    R ex = F::exp_(R(-1.8899) * x13);
+    R pre = cJ * ne * nu / (Te * Te);
+    R jI = pre * R(2.5651) * (R(1) + R(1.92) * ix13 + R(0.9977) * ix23) * ex;
+    if (!(jI > F::jflush)) return;
+    R jQ = pre * R(2.5651) * (R(1) + R(0.93193) * ix13 + R(0.499873) * ix23) * ex;
+    R jV = cJV * ne * nu * (cth / sth) / (Te * Te * Te) *
+           (R(1.81348) / x + R(3.42319) * ix23 + R(0.0292545) * F::rsqrt_(x) + R(2.03773) * ix13) * ex;
+    R rq = jQ / jI, rv = jV / jI;
+    R pj = F::sqrt_(rq * rq + rv * rv);
+    if (pj > R(1)) {
+        jQ /= pj;
+        jV /= pj;
+    }
+    R nuic = nu * ic;
+    R Bnu = c2h * nu * nuic * nuic / F::expm1_(cT * nu / Te);
+    R iB = R(1) / Bnu;
+    out[0] = jI;
+    out[1] = jQ;
+    out[2] = jV;
+    out[3] = jI * iB;
+    out[4] = jQ * iB;
+    out[5] = jV * iB;
+}
+
+// ------------------------------------------------------------------------------------------
+// Exact constant-coefficient step of dS/ds = J - M S over ds (M as in the transfer matrix
+// with j_U = a_U = r_U = 0): S <- exp(-M ds) S + (int_0^ds exp(-M v) dv) J.
+// Small steps (||M ds|| <= 1/2): Taylor series of the augmented system applied to the vector.
+// Otherwise M ds = tau 1 + B with B a Lorentz generator whose eigenvalues are +-P, +-iQ:
+//   exp(-B) = C0 + C1 B + C2 B^2 + C3 B^3,
+//   C0 = (Q^2 cosh P + P^2 cos Q)/D, C2 = (cosh P - cos Q)/D,
+//   C1 = -(P^2 sinc Q + Q^2 sinhc P)/D, C3 = (sinc Q - sinhc P)/D,   D = P^2 + Q^2,
+// and int_0^1 e^{-(tau + B) v} dv = f0 + f1 B + f2 B^2 + f3 B^3 with the same combinations of
+//   Ec = int e^{-tau v} cosh(Pv), Es = int e^{-tau v} sinh(Pv)/P,
+//   EC = int e^{-tau v} cos(Qv),  ES = int e^{-tau v} sin(Qv)/Q   (v from 0 to 1),
+// each evaluated in a form free of cancellation (exponentials folded with e^{-tau}).
+template <typename R>
+__device__ __forceinline__ R phi1(R x) {  // (1 - e^-x)/x
+    typedef Mth<R> F;
+    if (x == R(0)) return R(1);
+    return -F::expm1_(-x) / x;
+}
+template <typename R>
+__device__ __forceinline__ R gamma2(R t) {  // 1 - (1 + t) e^-t
+    typedef Mth<R> F;
+    if (t < R(0.5)) {
+        R s = 0, p = t * t, f = R(0.5);
+#pragma unroll
+        for (int k = 2; k < 18; k++) {
+            s += f * p;
+            p *= -t;
+            f *= R(k) / (R(k - 1) * R(k + 1));  // (k)/((k+1)!) from (k-1)/k!
+        }
+        return s;
+    }
+    return R(1) - (R(1) + t) * F::exp_(-t);
+}
+
+template <typename R>
+__device__ __forceinline__ void bmul(R aQ, R aV, R rQ, R rV, const R v[4], R o[4]) {
+    o[0] = aQ * v[1] + aV * v[3];
+    o[1] = aQ * v[0] + rV * v[2];
+    o[2] = -rV * v[1] + rQ * v[3];
+    o[3] = aV * v[0] - rQ * v[2];
+}
+
+template <typename R>
+__device__ __forceinline__ void taylor_step(R tau, R aQ, R aV, R rQ, R rV, const R J[4], R S[4]) {
+    typedef Mth<R> F;
+    R t[4], acc[4], b[4];
+    bmul(aQ, aV, rQ, rV, S, b);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        t[i] = J[i] - tau * S[i] - b[i];
+        acc[i] = t[i];
+    }
+    for (int k = 2; k <= F::taylor_max; k++) {
+        bmul(aQ, aV, rQ, rV, t, b);
+        R ik = R(1) / R(k);
+        R m = 0, sz = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            t[i] = -(tau * t[i] + b[i]) * ik;
+            acc[i] += t[i];
+            m = fmax(m, fabs(t[i]));
+            sz = fmax(sz, fabs(acc[i]) + fabs(S[i]));
+        }
+        if (m <= F::taylor_tol * sz) break;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) S[i] += acc[i];
+}
+
+template <typename R>
+__device__ void substep(const R cf[8], R ds, R S[4]) {
+    typedef Mth<R> F;
+    R tau = cf[3] * ds, aQ = cf[4] * ds, aV = cf[5] * ds, rQ = cf[6] * ds, rV = cf[7] * ds;
+    R J[4] = {cf[0] * ds, cf[1] * ds, R(0), cf[2] * ds};
+    R nrm = tau + fabs(aQ) + fabs(aV) + fabs(rQ) + fabs(rV);
+    if (!(nrm > R(0.5))) {
+        taylor_step(tau, aQ, aV, rQ, rV, J, S);
+        return;
+    }
+    R a2 = aQ * aQ + aV * aV, r2 = rQ * rQ + rV * rV, ar = aQ * rQ + aV * rV;
+    if (a2 + r2 == R(0)) {  // isotropic absorption and emission only
+        R e = F::exp_(-tau), p = phi1(tau);
+#pragma unroll
+        for (int i = 0; i < 4; i++) S[i] = e * S[i] + p * J[i];
+        return;
+    }
+    // eigenvalue magnitudes: P^2 - Q^2 = a^2 - r^2, P^2 Q^2 = (a.r)^2; the larger root from the
+    // sum, the smaller from the product (no cancellation when one of a, r dominates)
+    R hd = R(0.5) * (a2 - r2);
+    R disc = F::sqrt_(hd * hd + ar * ar);
+    R P2r, Q2r;
+    if (hd >= R(0)) {
+        P2r = disc + hd;
+        Q2r = P2r > R(0) ? ar * ar / P2r : R(0);
+    } else {
+        Q2r = disc - hd;
+        P2r = Q2r > R(0) ? ar * ar / Q2r : R(0);
+    }
+    R P = F::sqrt_(P2r), Q = F::sqrt_(Q2r);
+    R D = R(2) * disc;
+    if (D < F::degen_D * (a2 + r2) || (tau - P) < F::degen_tp * tau) {
+        // near-degenerate generator or maximal dichroism: sub-stepped Taylor series
+        int m = (int)fmin(ceil(nrm / R(0.5)), R(8192));
+        R inv = R(1) / R(m);
+        R Js[4] = {J[0] * inv, J[1] * inv, J[2] * inv, J[3] * inv};
+        for (int k = 0; k < m; k++) taylor_step(tau * inv, aQ * inv, aV * inv, rQ * inv, rV * inv, Js, S);
+        return;
+    }
+    R iD = R(1) / D, P2 = P * P, Q2 = Q * Q;
+    R e = F::exp_(-tau);
+    R sQ, cQ;
+    F::sincos_(Q, &sQ, &cQ);
+    R scQ = (Q < R(1e-4)) ? R(1) - Q2 / R(6) : sQ / Q;
+    R omscQ;  // 1 - sinc Q
+    if (Q < R(0.1)) {
+        R q2 = Q2;
+        omscQ = q2 * (R(1) / R(6) - q2 * (R(1) / R(120) - q2 * (R(1) / R(5040) - q2 / R(362880))));
+    } else {
+        omscQ = R(1) - scQ;
+    }
+    R sh2 = F::sin_(R(0.5) * Q);
+    sh2 = R(2) * sh2 * sh2;  // 1 - cos Q
+    R ech, esh, esh_m_e, ech_m_e;  // e^-tau cosh P, e^-tau sinh(P)/P, and minus e^-tau
+    if (P < R(1)) {
+        R p2 = P2, shcm1;
+        if (P < R(0.1))
+            shcm1 = p2 * (R(1) / R(6) + p2 * (R(1) / R(120) + p2 * (R(1) / R(5040) + p2 / R(362880))));
+        else
+            shcm1 = F::sinh_(P) / P - R(1);
+        R hs = F::sinh_(R(0.5) * P);
+        R chm1 = R(2) * hs * hs;  // cosh P - 1
+        ech = e * (R(1) + chm1);
+        esh = e * (R(1) + shcm1);
+        esh_m_e = e * shcm1;
+        ech_m_e = e * chm1;
+    } else {
+        R em = F::exp_(-(tau - P)), ep = F::exp_(-(tau + P));
+        ech = R(0.5) * (em + ep);
+        esh = R(0.5) * (em - ep) / P;
+        esh_m_e = esh - e;
+        ech_m_e = ech - e;
+    }
+    // homogeneous part
+    R eC0 = (Q2 * ech + P2 * e * cQ) * iD;
+    R eC2 = (ech - e * cQ) * iD;
+    R eC1 = -(P2 * e * scQ + Q2 * esh) * iD;
+    R eC3 = (e * scQ - esh) * iD;
+    // emission integrals
+    R g2 = gamma2(tau);
+    R Ec = R(0.5) * (phi1(tau - P) + phi1(tau + P));
+    R Es = (g2 - tau * esh_m_e - ech_m_e) / ((tau - P) * (tau + P));
+    R tq = tau * tau + Q2;
+    R Aa = -F::expm1_(-tau) + e * sh2;
+    R EC = (Aa * tau + e * sQ * Q) / tq;
+    R ES = (g2 + e * sh2 + tau * e * omscQ) / tq;
+    R f0 = (Q2 * Ec + P2 * EC) * iD;
+    R f2 = (Ec - EC) * iD;
+    R f1 = -(P2 * ES + Q2 * Es) * iD;
+    R f3 = (ES - Es) * iD;
+    R b1[4], b2[4], b3[4], j1[4], j2[4], j3[4];
+    bmul(aQ, aV, rQ, rV, S, b1);
+    bmul(aQ, aV, rQ, rV, b1, b2);
+    bmul(aQ, aV, rQ, rV, b2, b3);
+    bmul(aQ, aV, rQ, rV, J, j1);
+    bmul(aQ, aV, rQ, rV, j1, j2);
+    bmul(aQ, aV, rQ, rV, j2, j3);
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        S[i] = eC0 * S[i] + eC1 * b1[i] + eC2 * b2[i] + eC3 * b3[i] + f0 * J[i] + f1 * j1[i] + f2 * j2[i] +
+               f3 * j3[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// Plasma models. out: valid flag; ne, Theta_e, B [G]; u^mu, b^mu (direction) in KS.
+template <typename R>
+struct Plasma {
+    bool valid;
+    R ne, Te, B;
+    R u[4], b[4];
+};
+
+template <typename R>
+__device__ __forceinline__ void adaf_plasma(const AdafModel &p, R a, const KS<R> &m, R r, Plasma<R> &o) {
+    typedef Mth<R> F;
+    o.valid = false;
+    if (r > R(p.r_out)) return;
+    R ir = R(1) / r;
+    R r15 = ir * F::rsqrt_(r);
+    o.ne = R(p.n0) * r15;
+    o.Te = R(p.T0 * kKb / (kMe * kC * kC)) * ir;
+    o.B = R(sqrt(8.0 * kPi * p.n0 * kKb * p.T0 * (1.0 + p.ti_te) / p.beta)) * F::sqrt_(r15 * ir);
+    // Boyer-Lindquist inverse metric pieces
+    R a2 = a * a, s2 = m.s2;
+    R del = r * r - R(2) * r + a2;
+    R rr2 = r * r + a2;
+    R A = rr2 * rr2 - a2 * del * s2;
+    R isd = R(1) / (m.sig * del);
+    R gtt = -A * isd, gtp = -R(2) * a * r * isd, gpp = (del - a2 * s2) * isd / s2, grr = del * m.isig;
+    R rk = fmax(r, R(p.r_isco));
+    R sq = F::sqrt_(rk);
+    R lK = (rk * rk - R(2) * a * sq + a2) / (rk * sq - R(2) * sq + a);
+    R l = R(p.f_kep) * lK * s2;
+    R rhs = -R(1) - gtt + R(2) * gtp * l - gpp * l * l;
+    R ur_low = -F::sqrt_(fmax(rhs, R(0)) / grr);
+    R u[4];
+    u[1] = grr * ur_low;
+    u[0] = -gtt + gtp * l + R(2) * r / del * u[1];
+    u[2] = R(0);
+    u[3] = -gtp + gpp * l + a / del * u[1];
+    R nrm = F::rsqrt_(-m.dot(u, u));
+#pragma unroll
+    for (int i = 0; i < 4; i++) o.u[i] = u[i] * nrm;
+    R ul[4];
+    m.lower(o.u, ul);
+    R bt = ul[1] + ul[3] * ir;
+    R iut = R(1) / o.u[0];
+    o.b[0] = bt;
+    o.b[1] = (R(1) + bt * o.u[1]) * iut;
+    o.b[2] = bt * o.u[2] * iut;
+    o.b[3] = (ir + bt * o.u[3]) * iut;
+    o.valid = true;
+}
+
+// FMKS polar angle theta(X2) at blend weight w = exp(s (X1_in - X1)), and d/dX2.
+template <typename R>
+__device__ __forceinline__ R fmks_theta_w(const GridModel &g, R w, R x2, R *dth2, R *thj_m_thg) {
+    typedef Mth<R> F;
+    R s2p, c2p;
+    F::sincos_(R(2 * kPi) * x2, &s2p, &c2p);
+    R omh = R(1) - R(g.hslope);
+    R thg = R(kPi) * x2 + R(0.5) * omh * s2p;
+    R dthg = R(kPi) * (R(1) + omh * c2p);
+    R y = R(2) * x2 - R(1);
+    R yx = y / R(g.poly_xt);
+    R ya = F::pow_(fabs(yx), R(g.poly_alpha));
+    R N = R(g.poly_norm);
+    R thj = N * y * (R(1) + ya / R(g.poly_alpha + 1.0)) + R(0.5 * kPi);
+    R dthj = R(2) * N * (R(1) + ya);
+    if (dth2) *dth2 = dthg + w * (dthj - dthg);
+    if (thj_m_thg) *thj_m_thg = thj - thg;
+    return thg + w * (thj - thg);
+}
+
+template <typename R>
+__device__ __forceinline__ R fmks_x2(const GridModel &g, R w, R th) {
+    // table guess in (w, theta), then Newton
+    R fw = w * R(kX2TabW - 1);
+    int iw = min(max((int)fw, 0), kX2TabW - 2);
+    R tw = fw - R(iw);
+    R ft = th * R((kX2TabT - 1) / kPi);
+    int it = min(max((int)ft, 0), kX2TabT - 2);
+    R tt = ft - R(it);
+    const double *T = g.x2_table;
+    R x00 = R(T[iw * kX2TabT + it]), x01 = R(T[iw * kX2TabT + it + 1]);
+    R x10 = R(T[(iw + 1) * kX2TabT + it]), x11 = R(T[(iw + 1) * kX2TabT + it + 1]);
+    R x2 = (R(1) - tw) * ((R(1) - tt) * x00 + tt * x01) + tw * ((R(1) - tt) * x10 + tt * x11);
+    const int iters = sizeof(R) == 8 ? 3 : 2;
+#pragma unroll
+    for (int k = 0; k < iters; k++) {
+        R d;
+        R f = fmks_theta_w(g, w, x2, &d, (R *)nullptr) - th;
+        x2 -= f / d;
+    }
+    return fmin(fmax(x2, R(0)), R(1));
+}
+
+template <typename R>
+__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, R r, R th, double ph,
+                                            Plasma<R> &o) {
+    typedef Mth<R> F;
+    o.valid = false;
+    if (r < R(g.r_in) || r > R(g.r_out)) return;
+    R X1 = F::log_(r);
+    R w = F::exp_(R(g.mks_smooth) * (R(g.x1in) - X1));
+    R X2 = fmks_x2(g, w, th);
+    double X3 = fmod(ph, 2.0 * kPi);
+    if (X3 < 0.0) X3 += 2.0 * kPi;
+    R fi = (X1 - R(g.x1in)) / R(g.dx1) - R(0.5);
+    R fj = X2 / R(g.dx2) - R(0.5);
+    R fk = R(X3 / g.dx3 - 0.5);
+    fi = fmin(fmax(fi, R(0)), R(g.n1 - 1));
+    fj = fmin(fmax(fj, R(0)), R(g.n2 - 1));
+    int i0 = min((int)fi, g.n1 - 2), j0 = min((int)fj, g.n2 - 2);
+    R w1 = fi - R(i0), w2 = fj - R(j0);
+    R kf = F::floor_(fk);
+    R w3 = fk - kf;
+    int k0 = (int)kf;
+    k0 = ((k0 % g.n3) + g.n3) % g.n3;
+    int k1 = k0 + 1 == g.n3 ? 0 : k0 + 1;
+    R P[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int di = 0; di < 2; di++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++) {
+            long long row = ((long long)(i0 + di) * g.n2 + (j0 + dj)) * g.n3;
+            R wij = (di ? w1 : R(1) - w1) * (dj ? w2 : R(1) - w2);
+#pragma unroll
+            for (int dk = 0; dk < 2; dk++) {
+                long long cell = row + (dk ? k1 : k0);
+                R wt = wij * (dk ? w3 : R(1) - w3);
+                float4 lo = __ldg(g.prims + 2 * cell), hi = __ldg(g.prims + 2 * cell + 1);
+                P[0] += wt * R(lo.x);
+                P[1] += wt * R(lo.y);
+                P[2] += wt * R(lo.z);
+                P[3] += wt * R(lo.w);
+                P[4] += wt * R(hi.x);
+                P[5] += wt * R(hi.y);
+                P[6] += wt * R(hi.z);
+                P[7] += wt * R(hi.w);
+            }
+        }
+    R rho = P[0], uu = P[1];
+    if (!(rho > R(0))) return;
+    R dth2, dd;
+    fmks_theta_w(g, w, X2, &dth2, &dd);
+    R dth1 = -R(g.mks_smooth) * w * dd;
+    R Ut[4] = {R(0), r * P[2], dth1 * P[2] + dth2 * P[3], P[4]};
+    R Bi[4] = {R(0), r * P[5], dth1 * P[5] + dth2 * P[6], P[7]};
+    // KS lapse 1/sqrt(1+q), shift beta^r = q/(1+q)
+    R Ul[4];
+    m.lower(Ut, Ul);
+    R gam = F::sqrt_(R(1) + Ul[1] * Ut[1] + Ul[2] * Ut[2] + Ul[3] * Ut[3]);
+    R sop = F::sqrt_(m.op);
+    o.u[0] = gam * sop;
+    o.u[1] = Ut[1] - gam * m.q / sop;
+    o.u[2] = Ut[2];
+    o.u[3] = Ut[3];
+    R ul[4];
+    m.lower(o.u, ul);
+    R bt = Bi[1] * ul[1] + Bi[2] * ul[2] + Bi[3] * ul[3];
+    R iut = R(1) / o.u[0];
+    o.b[0] = bt;
+    o.b[1] = (Bi[1] + bt * o.u[1]) * iut;
+    o.b[2] = (Bi[2] + bt * o.u[2]) * iut;
+    o.b[3] = (Bi[3] + bt * o.u[3]) * iut;
+    R bsq = m.dot(o.b, o.b);
+    if (bsq > R(g.sigma_cut) * rho) return;
+    R ga = R(g.gamma_ad);
+    R Rt;
+    if (bsq > R(0)) {
+        R bp = R(2) * (ga - R(1)) * uu / bsq;
+        R bp2 = bp * bp, i1 = R(1) / (R(1) + bp2);
+        Rt = R(g.R_high) * bp2 * i1 + R(g.R_low) * i1;
+    } else {
+        Rt = R(g.R_high);
+    }
+    o.ne = rho * R(g.ne_unit);
+    o.Te = R(kMp / kMe) * (ga - R(1)) * uu / (rho * (R(1) + Rt));
+    o.B = F::sqrt_(fmax(bsq, R(0))) * R(g.b_unit);
+    o.valid = true;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fluid tetrad: e3 the unit projection of k = -K normal to u; e2 the unit part of b normal to
+// (u, e3) (d_theta if b is along k); e1 = Levi-Civita(e0, e2, e3) so (e1, e2, e3) is right
+// handed. Returns w = -k.u = nu/nu_obs, sin and cos of the field angle.
+template <typename R>
+__device__ __forceinline__ void fluid_tetrad(const KS<R> &m, const R K[4], const R u[4], const R b[4], R e1[4],
+                                             R e2[4], R &w, R &sth, R &cth) {
+    typedef Mth<R> F;
+    w = m.dot(K, u);
+    R e3[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) e3[i] = -K[i] - w * u[i];
+    R n3 = F::rsqrt_(m.dot(e3, e3));
+#pragma unroll
+    for (int i = 0; i < 4; i++) e3[i] *= n3;
+    R bb = m.dot(b, b), be3 = m.dot(b, e3);
+#pragma unroll
+    for (int i = 0; i < 4; i++) e2[i] = b[i] - be3 * e3[i];
+    R n2sq = fmax(m.dot(e2, e2), R(0));
+    R n2 = F::sqrt_(n2sq);
+    R ib = F::rsqrt_(bb);
+    if (!(n2 > R(1e-10) * F::sqrt_(bb))) {
+        R v[4] = {R(0), R(0), R(1), R(0)};
+        R vu = m.dot(v, u), ve = m.dot(v, e3);
+#pragma unroll
+        for (int i = 0; i < 4; i++) e2[i] = v[i] + vu * u[i] - ve * e3[i];
+        R nn = F::rsqrt_(m.dot(e2, e2));
+#pragma unroll
+        for (int i = 0; i < 4; i++) e2[i] *= nn;
+    } else {
+        R in2 = R(1) / n2;
+#pragma unroll
+        for (int i = 0; i < 4; i++) e2[i] *= in2;
+    }
+    sth = n2 * ib;
+    cth = be3 * ib;
+    // e1_mu = -sqrt(-g) eps[mu nu rho sigma] u^nu e2^rho e3^sigma (generalized cross product)
+    const R *A = u, *Bv = e2, *Cv = e3;
+    auto det3 = [&](int i, int j, int k) {
+        return A[i] * (Bv[j] * Cv[k] - Bv[k] * Cv[j]) - A[j] * (Bv[i] * Cv[k] - Bv[k] * Cv[i]) +
+               A[k] * (Bv[i] * Cv[j] - Bv[j] * Cv[i]);
+    };
+    R sg = m.sqrt_mg();
+    R low[4] = {-sg * det3(1, 2, 3), sg * det3(0, 2, 3), -sg * det3(0, 1, 3), sg * det3(0, 1, 2)};
+    m.raise(low, e1);
+}
+
+}  // namespace prt

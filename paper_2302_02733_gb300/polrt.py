@@ -1,0 +1,197 @@
+"""Thin Python binding of the polrt C ABI (include/polrt.h): argument marshalling only.
+
+Every function keeps the C name. Buffers may be torch tensors (on the GPU or the host) or
+numpy arrays; their data pointers are passed through unchanged. The CUDA library must have
+been built in-tree (``paper_2302_02733_gb300.build.build()``). Without it this module raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_NOMEM, RT_ERR_NOT_READY, RT_ERR_WORKSPACE, RT_ERR_SIZE = 0, -1, -2, -3, -4, -5, -6
+RT_MODEL_ADAF, RT_MODEL_GRID = 1, 2
+RT_FP64, RT_MIXED = 0, 1
+RT_RAY_HORIZON, RT_RAY_ESCAPE, RT_RAY_NMAX, RT_RAY_NAN, RT_RAY_OVERFLOW = 1, 2, 3, 4, 5
+
+
+class rt_adaf_params(C.Structure):
+    _fields_ = [("n0", C.c_double), ("T0", C.c_double), ("beta", C.c_double), ("f_kep", C.c_double),
+                ("Ti_over_Te", C.c_double), ("r_out", C.c_double)]
+
+
+class rt_grid_params(C.Structure):
+    _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("hslope", C.c_double), ("poly_xt", C.c_double), ("poly_alpha", C.c_double),
+                ("mks_smooth", C.c_double), ("prims", C.c_void_p), ("M_unit", C.c_double), ("R_high", C.c_double),
+                ("R_low", C.c_double), ("sigma_cut", C.c_double), ("gamma_ad", C.c_double)]
+
+
+class rt_model_params(C.Structure):
+    _fields_ = [("kind", C.c_int), ("adaf", rt_adaf_params), ("grid", rt_grid_params)]
+
+
+class rt_camera(C.Structure):
+    _fields_ = [("a", C.c_double), ("incl_deg", C.c_double), ("r_cam", C.c_double), ("freq_hz", C.c_double),
+                ("fov_M", C.c_double), ("nx", C.c_int), ("ny", C.c_int), ("M_bh_g", C.c_double),
+                ("dist_cm", C.c_double)]
+
+
+class rt_counters(C.Structure):
+    _fields_ = [("rays", C.c_uint64), ("steps", C.c_uint64), ("points", C.c_uint64),
+                ("emitting_points", C.c_uint64), ("arena_blocks_used", C.c_uint64),
+                ("arena_blocks_total", C.c_uint64), ("n_horizon", C.c_uint32), ("n_escape", C.c_uint32),
+                ("n_nmax", C.c_uint32), ("n_nan", C.c_uint32), ("n_overflow", C.c_uint32),
+                ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float)]
+
+
+_lib = None
+_VP = C.c_void_p
+
+
+def lib():
+    """Load libpolrt.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"polrt CUDA library missing at {_build.LIB}: run build() first")
+        L = C.CDLL(_build.LIB)
+        L.rt_create.argtypes = [C.POINTER(_VP), C.c_int, _VP]
+        L.rt_destroy.argtypes = [_VP]
+        L.rt_set_stream.argtypes = [_VP, _VP]
+        L.rt_load_model.argtypes = [_VP, C.POINTER(rt_model_params)]
+        L.rt_set_camera.argtypes = [_VP, C.POINTER(rt_camera)]
+        L.rt_set_integrator.argtypes = [_VP, C.c_double, C.c_int]
+        L.rt_set_workspace.argtypes = [_VP, _VP, C.c_size_t]
+        L.rt_workspace_min_bytes.restype = C.c_size_t
+        L.rt_workspace_hint.argtypes = [_VP, C.POINTER(C.c_size_t)]
+        L.rt_render.argtypes = [_VP, C.c_int, _VP, _VP]
+        L.rt_image_stats.argtypes = [_VP, _VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]
+        L.rt_last_counters.argtypes = [_VP, C.POINTER(rt_counters)]
+        L.rt_error_string.argtypes = [C.c_int]
+        L.rt_error_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class PolrtError(RuntimeError):
+    def __init__(self, code: int, call: str):
+        super().__init__(f"{call}: {lib().rt_error_string(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code: int, call: str):
+    if code != RT_OK:
+        raise PolrtError(code, call)
+
+
+def _ptr(buf):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def rt_create(device: int = 0, stream=None) -> int:
+    h = _VP()
+    _check(lib().rt_create(C.byref(h), device, stream), "rt_create")
+    return h.value
+
+
+def rt_destroy(ctx):
+    _check(lib().rt_destroy(ctx), "rt_destroy")
+
+
+def rt_set_stream(ctx, stream):
+    _check(lib().rt_set_stream(ctx, stream), "rt_set_stream")
+
+
+def rt_set_camera(ctx, cam):
+    """cam: an rt_camera, or any object with the same field names (e.g. synth.Camera)."""
+    if not isinstance(cam, rt_camera):
+        cam = rt_camera(cam.a, cam.incl_deg, cam.r_cam, cam.freq_hz, cam.fov_M, cam.nx, cam.ny, cam.M_bh_g,
+                        cam.dist_cm)
+    _check(lib().rt_set_camera(ctx, C.byref(cam)), "rt_set_camera")
+
+
+def rt_set_integrator(ctx, eps: float = 0.05, nmax: int = 20000):
+    _check(lib().rt_set_integrator(ctx, eps, nmax), "rt_set_integrator")
+
+
+def rt_load_model(ctx, params: rt_model_params, keepalive=None):
+    _check(lib().rt_load_model(ctx, C.byref(params)), "rt_load_model")
+
+
+def adaf_model(p) -> rt_model_params:
+    m = rt_model_params()
+    m.kind = RT_MODEL_ADAF
+    m.adaf = rt_adaf_params(p.n0, p.T0, p.beta, p.f_kep, p.Ti_over_Te, p.r_out)
+    return m
+
+
+def grid_model(prims, g) -> rt_model_params:
+    """prims: float32 [n1][n2][n3][8] (torch tensor on any device, or numpy)."""
+    shape = tuple(prims.shape)
+    if len(shape) != 4 or shape[3] != 8:
+        raise ValueError("prims must be [n1][n2][n3][8]")
+    m = rt_model_params()
+    m.kind = RT_MODEL_GRID
+    m.grid = rt_grid_params(shape[0], shape[1], shape[2], g.r_in, g.r_out, g.hslope, g.poly_xt, g.poly_alpha,
+                            g.mks_smooth, _ptr(prims), g.M_unit, g.R_high, g.R_low, g.sigma_cut, g.gamma_ad)
+    return m
+
+
+def rt_set_workspace(ctx, buf, nbytes: int | None = None):
+    if buf is None:
+        _check(lib().rt_set_workspace(ctx, None, 0), "rt_set_workspace")
+        return
+    if nbytes is None:
+        nbytes = buf.numel() * buf.element_size() if hasattr(buf, "numel") else buf.nbytes
+    _check(lib().rt_set_workspace(ctx, _ptr(buf), nbytes), "rt_set_workspace")
+
+
+def rt_workspace_min_bytes() -> int:
+    return lib().rt_workspace_min_bytes()
+
+
+def rt_workspace_hint(ctx) -> int:
+    b = C.c_size_t(0)
+    _check(lib().rt_workspace_hint(ctx, C.byref(b)), "rt_workspace_hint")
+    return b.value
+
+
+def rt_render(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
+    rc = lib().rt_render(ctx, form, _ptr(out_iquv), _ptr(status))
+    if check:
+        _check(rc, "rt_render")
+    return rc
+
+
+def rt_image_stats(ctx, iquv, form: int):
+    f, lp, cp = C.c_double(0), C.c_double(0), C.c_double(0)
+    _check(lib().rt_image_stats(ctx, _ptr(iquv), form, C.byref(f), C.byref(lp), C.byref(cp)), "rt_image_stats")
+    return f.value, lp.value, cp.value
+
+
+def rt_last_counters(ctx) -> dict:
+    c = rt_counters()
+    _check(lib().rt_last_counters(ctx, C.byref(c)), "rt_last_counters")
+    return {k: getattr(c, k) for k, _ in rt_counters._fields_}
+
+
+def rt_error_string(code: int) -> str:
+    return lib().rt_error_string(code).decode()

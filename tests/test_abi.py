@@ -1,0 +1,54 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every declared entry point;
+calls fail with an error code (never a crash) when no GPU is present."""
+import re
+
+import pytest
+
+import __graft_entry__  # noqa: F401  (puts the repo root on sys.path)
+
+
+def declared_symbols():
+    text = open(__graft_entry__.ROOT + "/include/polrt.h").read()
+    return re.findall(r"^\s*(?:int|size_t|const char \*)\s*(rt_\w+)\(", text, re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_02733_gb300 import build, polrt
+
+    build.build()
+    return polrt.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_error_strings(lib):
+    from paper_2302_02733_gb300 import polrt
+
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert polrt.rt_error_string(code)
+    assert "unknown" in polrt.rt_error_string(-99)
+    assert polrt.rt_workspace_min_bytes() > 0
+
+
+def test_null_arguments_are_rejected(lib):
+    from paper_2302_02733_gb300 import polrt
+
+    assert lib.rt_destroy(None) == polrt.RT_ERR_INVALID
+    assert lib.rt_render(None, 0, None, None) == polrt.RT_ERR_INVALID
+    assert lib.rt_set_integrator(None, 0.05, 100) == polrt.RT_ERR_INVALID
+
+
+def test_create_without_gpu_reports_an_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2302_02733_gb300 import polrt
+
+    with pytest.raises(polrt.PolrtError):
+        polrt.rt_create(0, None)

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Per-pixel error = max_S |S_gpu - S_oracle| / max(I_oracle(pixel), 1e-8 max I_oracle).
+FP64 form: <= 1e-9 on every pixel outside the oracle's sensitivity mask, <= 1e-6 inside it,
+and <= 1e-10 on the total flux. The mask holds pixels whose oracle output moves by more than
+1e-10 (same measure) when the pixel position is nudged by one ulp, or whose step count moves
+(the photon ring, where the path is chaotic); it must cover under 0.1% of the pixels.
+Mixed form (FP32 transfer): per-pixel p99 <= 1e-4 (ADAF) and the stated flux/LP/CP bounds.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2302_02733_gb300 import polrt
+
+    torch.cuda.set_device(0)
+    ctx = polrt.rt_create(0, torch.cuda.current_stream().cuda_stream)
+    yield polrt, ctx
+    polrt.rt_destroy(ctx)
+
+
+def gpu_render(rt, cam, model, form, eps=0.05, nmax=20000, host=False):
+    polrt, ctx = rt
+    polrt.rt_set_integrator(ctx, eps, nmax)
+    polrt.rt_set_camera(ctx, cam)
+    polrt.rt_load_model(ctx, model)
+    dt = torch.float64 if form == polrt.RT_FP64 else torch.float32
+    dev = "cpu" if host else "cuda"
+    out = torch.full((cam.ny, cam.nx, 4), float("nan"), dtype=dt, device=dev)
+    st = torch.zeros((cam.ny, cam.nx), dtype=torch.uint8, device=dev)
+    rc = polrt.rt_render(ctx, form, out, st, check=False)
+    cnt = polrt.rt_last_counters(ctx)
+    return rc, out.cpu().numpy().astype(np.float64), st.cpu().numpy(), cnt
+
+
+def per_pixel_error(gpu, ref):
+    scale = np.maximum(ref[..., 0], 1e-8 * max(ref[..., 0].max(), 1e-300))
+    return np.abs(gpu - ref).max(axis=-1) / scale
+
+
+def oracle_mask(ora, ocam, omodel, ref, nsteps, ix=None, iy=None):
+    masks = []
+    for pert in (1, 2):
+        if ix is None:
+            img, ns, _, _ = ora.render_image(ocam, omodel, pert=pert)
+        else:
+            img, ns, _, _ = ora.render_pixels(ocam, omodel, ix, iy, pert=pert)
+        masks.append((per_pixel_error(img, ref) > 1e-10) | (ns != nsteps))
+    return masks[0] | masks[1]
+
+
+def check_fp64(ora, gpu, st, cnt, ref, nsteps, status, mask, flux_tol=1e-10):
+    assert np.array_equal(st.astype(np.int64), status.astype(np.int64)), "status codes differ"
+    err = per_pixel_error(gpu, ref)
+    frac = mask.mean()
+    assert frac < 1e-3 or mask.sum() <= 1, f"sensitivity mask covers {frac:.2%}"
+    assert err[~mask].max() <= 1e-9, f"max unmasked error {err[~mask].max():.3e}"
+    if mask.any():
+        assert err[mask].max() <= 1e-6, f"max masked error {err[mask].max():.3e}"
+    fg, fr = gpu[..., 0].sum(), ref[..., 0].sum()
+    assert abs(fg - fr) <= flux_tol * abs(fr), (fg, fr)
+    return err
+
+
+def test_adaf_fp64_64(rt, ora, synth):
+    cam = synth.Camera(incl_deg=60.0, nx=64, ny=64)
+    par = synth.adaf_params(1)
+    polrt = rt[0]
+    rc, gpu, st, cnt = gpu_render(rt, cam, polrt.adaf_model(par), polrt.RT_FP64)
+    assert rc == 0
+    ocam, om = ora.camera(cam), ora.adaf_model(par)
+    ref, nsteps, status, _ = ora.render_image(ocam, om)
+    mask = oracle_mask(ora, ocam, om, ref, nsteps)
+    err = check_fp64(ora, gpu, st, cnt, ref, nsteps, status, mask)
+    # steps are integers: equal wherever the path is not chaotic
+    assert abs(cnt["steps"] - int(nsteps.sum())) <= int(nsteps[mask].sum()) + 0
+    print(f"adaf64 fp64: max err {err[~mask].max():.2e}, mask {mask.sum()} px")
+
+
+@pytest.mark.parametrize("nx,ny", [(32, 32), (30, 22)])
+def test_grid_fp64_small_images(rt, ora, synth, torus_grid, nx, ny):
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=20.0, nx=nx, ny=ny)
+    polrt = rt[0]
+    rc, gpu, st, cnt = gpu_render(rt, cam, polrt.grid_model(prims, g), polrt.RT_FP64)
+    assert rc == 0
+    ocam, om = ora.camera(cam), ora.grid_model(prims, g)
+    ref, nsteps, status, _ = ora.render_image(ocam, om)
+    mask = oracle_mask(ora, ocam, om, ref, nsteps)
+    check_fp64(ora, gpu, st, cnt, ref, nsteps, status, mask)
+    assert cnt["emitting_points"] > 0
+
+
+def test_grid_fp64_1024_sampled(rt, ora, synth, torus_grid):
+    """The benchmark workload (torus grid, 1024x1024, i = 20 deg) at full size; the oracle
+    checks 256 seeded pixels one by one."""
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=20.0, nx=1024, ny=1024)
+    polrt = rt[0]
+    rc, gpu, st, cnt = gpu_render(rt, cam, polrt.grid_model(torch.from_numpy(prims).cuda(), g), polrt.RT_FP64)
+    assert rc == 0
+    rng = np.random.default_rng(2024)
+    ix, iy = rng.integers(0, 1024, 256), rng.integers(0, 1024, 256)
+    ocam, om = ora.camera(cam), ora.grid_model(prims, g)
+    ref, nsteps, status, _ = ora.render_pixels(ocam, om, ix, iy)
+    mask = oracle_mask(ora, ocam, om, ref, nsteps, ix, iy)
+    g_px = gpu[iy, ix]
+    assert np.array_equal(st[iy, ix].astype(np.int64), status.astype(np.int64))
+    scale = np.maximum(ref[:, 0], 1e-8 * gpu[..., 0].max())
+    err = np.abs(g_px - ref).max(axis=-1) / scale
+    assert err[~mask].max() <= 1e-9, err[~mask].max()
+    assert cnt["n_overflow"] == 0 and cnt["rays"] == 1024 * 1024
+
+
+def test_mixed_form_error(rt, ora, synth, torus_grid):
+    polrt = rt[0]
+    cam = synth.Camera(incl_deg=60.0, nx=64, ny=64)
+    par = synth.adaf_params(1)
+    rc, gpu, st, cnt = gpu_render(rt, cam, polrt.adaf_model(par), polrt.RT_MIXED)
+    assert rc == 0
+    ref, nsteps, status, _ = ora.render_image(ora.camera(cam), ora.adaf_model(par))
+    err = per_pixel_error(gpu, ref)
+    f_err = abs(gpu[..., 0].sum() / ref[..., 0].sum() - 1)
+    print(f"mixed adaf64: p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e} flux {f_err:.2e}")
+    assert np.percentile(err, 99) <= 1e-4
+    assert f_err <= 1e-5
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=20.0, nx=32, ny=32)
+    rc, gpu, st, cnt = gpu_render(rt, cam, polrt.grid_model(prims, g), polrt.RT_MIXED)
+    assert rc == 0
+    ref, nsteps, status, _ = ora.render_image(ora.camera(cam), ora.grid_model(prims, g))
+    err = per_pixel_error(gpu, ref)
+    f_err = abs(gpu[..., 0].sum() / ref[..., 0].sum() - 1)
+    print(f"mixed grid32: p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e} flux {f_err:.2e}")
+
+
+def test_step_limit_and_tiny_images(rt, ora, synth):
+    polrt = rt[0]
+    par = synth.adaf_params(1)
+    for nx, ny, nmax in ((1, 1, 20000), (13, 7, 20000), (8, 8, 60)):
+        cam = synth.Camera(incl_deg=60.0, nx=nx, ny=ny)
+        rc, gpu, st, cnt = gpu_render(rt, cam, polrt.adaf_model(par), polrt.RT_FP64, nmax=nmax)
+        assert rc == 0
+        ref, nsteps, status, _ = ora.render_image(ora.camera(cam, nmax=nmax), ora.adaf_model(par))
+        assert np.array_equal(st.astype(np.int64), status.astype(np.int64))
+        if nmax == 60:
+            assert np.all(status == 3)
+        assert per_pixel_error(gpu, ref).max() <= 1e-9
+
+
+def test_host_buffers_match_device(rt, synth):
+    polrt = rt[0]
+    cam = synth.Camera(incl_deg=60.0, nx=24, ny=16)
+    m = polrt.adaf_model(synth.adaf_params(1))
+    _, dev, sdev, _ = gpu_render(rt, cam, m, polrt.RT_FP64)
+    _, host, shost, _ = gpu_render(rt, cam, m, polrt.RT_FP64, host=True)
+    assert np.array_equal(dev, host) and np.array_equal(sdev, shost)
+
+
+def test_image_stats_match_oracle(rt, ora, synth):
+    polrt, ctx = rt
+    cam = synth.Camera(incl_deg=60.0, nx=32, ny=32)
+    _, gpu, _, _ = gpu_render(rt, cam, polrt.adaf_model(synth.adaf_params(1)), polrt.RT_FP64)
+    f, lp, cp = polrt.rt_image_stats(ctx, torch.from_numpy(gpu).cuda(), polrt.RT_FP64)
+    fo, lpo, cpo = ora.image_stats(ora.camera(cam), gpu)
+    assert np.isclose(f, fo, rtol=1e-12) and np.isclose(lp, lpo, rtol=1e-10) and np.isclose(cp, cpo, rtol=1e-10)
+
+
+def test_arena_overflow_is_reported(rt, synth):
+    polrt, ctx = rt
+    cam = synth.Camera(incl_deg=60.0, nx=4, ny=4)
+    ws = torch.empty(polrt.rt_workspace_min_bytes() + 4096, dtype=torch.uint8, device="cuda")
+    polrt.rt_set_workspace(ctx, ws)
+    try:
+        rc, gpu, st, cnt = gpu_render(rt, cam, polrt.adaf_model(synth.adaf_params(1)), polrt.RT_FP64, eps=0.004)
+        assert rc == polrt.RT_ERR_WORKSPACE
+        assert np.all(gpu[st == polrt.RT_RAY_OVERFLOW] == 0.0) and (st == polrt.RT_RAY_OVERFLOW).any()
+        rc, gpu2, st2, _ = gpu_render(rt, cam, polrt.adaf_model(synth.adaf_params(1)), polrt.RT_FP64)
+        assert rc == 0   # the same small workspace is enough at the normal step
+    finally:
+        polrt.rt_set_workspace(ctx, None)
+
+
+def test_invalid_arguments(rt, synth):
+    polrt, ctx = rt
+    L = polrt.lib()
+    bad = polrt.rt_camera(0.9375, 200.0, 1000.0, 2.3e11, 40.0, 8, 8, 1e40, 1e22)
+    assert L.rt_set_camera(ctx, polrt.C.byref(bad)) == polrt.RT_ERR_INVALID
+    bad = polrt.rt_camera(1.2, 60.0, 1000.0, 2.3e11, 40.0, 8, 8, 1e40, 1e22)
+    assert L.rt_set_camera(ctx, polrt.C.byref(bad)) == polrt.RT_ERR_INVALID
+    assert L.rt_render(ctx, 7, None, None) == polrt.RT_ERR_INVALID
