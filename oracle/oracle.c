@@ -441,7 +441,8 @@ void ora_grid_interp(const ora_model *m, double X1, double X2, double X3, double
  *   u^t = gamma/alpha, u^i = U^i - gamma beta^i/alpha; b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t.
  *   Units: L = GM/c^2, rho_unit = M_unit/L^3, B_unit = c sqrt(4 pi rho_unit),
  *   n_e = rho rho_unit/(m_p + m_e).
- *   beta_p = 2(gamma_ad - 1) u / b^2, R = R_high beta_p^2/(1 + beta_p^2) + R_low/(1 + beta_p^2),
+ *   beta_p = 2(gamma_ad - 1) u / b^2, R = R_high beta_p^2/(1 + beta_p^2) + R_low/(1 + beta_p^2)
+ *   (taken as R_low once (1/beta_p)^2 exceeds 1e30),
  *   Theta_e = (m_p/m_e)(gamma_ad - 1) u / (rho (1 + R)).
  *   No emission where sigma = b^2/rho > sigma_cut or outside r_in <= r <= r_out. */
 static void grid_plasma(const ora_camera *cam, const ora_model *m, const double x[4], double out[12]) {
@@ -455,7 +456,7 @@ static void grid_plasma(const ora_camera *cam, const ora_model *m, const double 
     double P[8];
     ora_grid_interp(m, X1, X2, X3, P);
     double rho = P[0], uu = P[1];
-    if (!(rho > 0.0)) return;
+    if (!(rho > 0.0) || !(uu > 0.0)) return;
     double dth1, dth2;
     ora_fmks_theta(m, X1, X2, &dth1, &dth2);
     double Ut[4] = {0.0, r * P[2], dth1 * P[2] + dth2 * P[3], P[4]};
@@ -483,14 +484,10 @@ static void grid_plasma(const ora_camera *cam, const ora_model *m, const double 
     double rho_unit = m->M_unit / (L * L * L);
     double B_unit = O_C * sqrt(4.0 * O_PI * rho_unit);
     double ga = m->gamma_ad;
-    double R;
-    if (bsq > 0.0) {
-        double bp = 2.0 * (ga - 1.0) * uu / bsq;
-        double bp2 = bp * bp;
-        R = m->R_high * bp2 / (1.0 + bp2) + m->R_low / (1.0 + bp2);
-    } else {
-        R = m->R_high;
-    }
+    /* R = (R_high b^2 + R_low)/(1 + b^2) in terms of 1/b, b = beta_p, so nothing overflows */
+    double ib = bsq / (2.0 * (ga - 1.0) * uu);
+    double ib2 = ib * ib;
+    double R = ib2 < 1e30 ? (m->R_high + m->R_low * ib2) / (1.0 + ib2) : m->R_low;
     out[0] = rho * rho_unit / (O_MP + O_ME);
     out[1] = (O_MP / O_ME) * (ga - 1.0) * uu / (rho * (1.0 + R));
     out[2] = sqrt(fmax(bsq, 0.0)) * B_unit;
@@ -762,6 +759,9 @@ static double fluid_tetrad(const double g[16], const double K[4], const double u
     double bb = dot4(g, b, b), be3 = dot4(g, b, e3);
     for (int i = 0; i < 4; i++) e2[i] = b[i] - be3 * e3[i];
     double n2 = sqrt(fmax(dot4(g, e2, e2), 0.0));
+    /* the angle between b and e3: atan2 of the normal and parallel parts of b, which stays
+     * accurate when b is nearly along the ray (acos of the cosine would not) */
+    double thB = atan2(n2, be3);
     if (!(n2 > 1e-10 * sqrt(bb))) {
         double v[4] = {0, 0, 1, 0};
         double vu = dot4(g, v, u), ve = dot4(g, v, e3);
@@ -770,8 +770,7 @@ static double fluid_tetrad(const double g[16], const double K[4], const double u
     }
     for (int i = 0; i < 4; i++) e2[i] /= n2;
     levi_e1(g, e0, e2, e3, e1);
-    double cth = fmax(-1.0, fmin(1.0, be3 / sqrt(bb)));
-    return acos(cth);
+    return thB;
 }
 
 double ora_fluid_tetrad(double a, const double x[4], const double K[4], const double u[4], const double b[4],

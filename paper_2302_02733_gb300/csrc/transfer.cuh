@@ -168,12 +168,16 @@ __device__ __forceinline__ void thermal_coeffs(R ne, R Te, R B, R nu, R sth, R c
     R rb = nuB / nu;
     R X = Te * F::sqrt_(R(1.4142135623730951) * sth * R(1e3) * rb);
     R k0, k1, k2;
-    bessel_k012_scaled<R>(R(1) / Te, gw, k0, k1, k2);
+    if (Te > R(1e-12)) {
+        bessel_k012_scaled<R>(R(1) / Te, gw, k0, k1, k2);
+    } else {  // K_n(z)/K_2(z) -> 1 as z -> infinity
+        k0 = k1 = k2 = R(1);
+    }
     R f = R(2.011) * F::exp_(-F::pow_(X, R(1.035)) / R(4.7)) -
           F::cos_(R(0.5) * X) * F::exp_(-F::pow_(X, R(1.2)) / R(2.73)) - R(0.011) * F::exp_(-X / R(47.2));
     if (X > R(1))
         f += (R(0.011) * F::exp_(-X / R(47.2)) -
-              R(0.7937005259840998 / 67.40655678327585 * 1.0e4 * kPi) * F::pow_(X, R(-8.0 / 3.0))) *
+              R(369.6934286909082) * F::pow_(X, R(-8.0 / 3.0))) *  // 2^-1/3 3^-23/6 1e4 pi
              R(0.5) * (R(1) + F::tanh_(R(10) * F::log_(X / R(120))));
     R gX = R(1) - R(0.11) * F::log1p_(R(0.035) * X);
     out[6] = cQ2 * ne * rb * rb / nu * sth * sth * f * (k1 / k2 + R(6) * Te);
@@ -238,6 +242,32 @@ __device__ __forceinline__ R gamma2(R t) {  // 1 - (1 + t) e^-t
         return s;
     }
     return R(1) - (R(1) + t) * F::exp_(-t);
+}
+
+// E_s(tau, P) = int_0^1 e^{-tau v} sinh(P v)/P dv for tau < 1/2 (then P <= tau < 1/2):
+// sum_k P^2k/(2k+1)! m_{2k+1}(tau) with m_n(tau) = int_0^1 v^n e^{-tau v} dv, m_13 from its
+// series sum_j (-tau)^j/(j! (14 + j)) and the stable downward recurrence
+// m_{n-1} = (tau m_n + e^{-tau})/n.
+template <typename R>
+__device__ __forceinline__ R es_small(R tau, R P, R e) {
+    const int nj = sizeof(R) == 8 ? 18 : 10;
+    R term = R(1), m = R(0);
+#pragma unroll
+    for (int j = 0; j < nj; j++) {
+        m += term / R(14 + j);
+        term *= -tau / R(j + 1);
+    }
+    R mm[14];
+    mm[13] = m;
+#pragma unroll
+    for (int n = 13; n >= 1; n--) mm[n - 1] = (tau * mm[n] + e) / R(n);
+    R P2 = P * P, c = R(1), acc = R(0);
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        acc += c * mm[2 * k + 1];
+        c *= P2 / (R(2 * k + 2) * R(2 * k + 3));
+    }
+    return acc;
 }
 
 template <typename R>
@@ -306,7 +336,7 @@ __device__ void substep(const R cf[8], R ds, R S[4]) {
     }
     R P = F::sqrt_(P2r), Q = F::sqrt_(Q2r);
     R D = R(2) * disc;
-    if (D < F::degen_D * (a2 + r2) || (tau - P) < F::degen_tp * tau) {
+    if (D < F::degen_D * (a2 + r2) || (tau >= R(0.5) && (tau - P) < F::degen_tp * tau)) {
         // near-degenerate generator or maximal dichroism: sub-stepped Taylor series
         int m = (int)fmin(ceil(nrm / R(0.5)), R(8192));
         R inv = R(1) / R(m);
@@ -356,7 +386,7 @@ __device__ void substep(const R cf[8], R ds, R S[4]) {
     // emission integrals
     R g2 = gamma2(tau);
     R Ec = R(0.5) * (phi1(tau - P) + phi1(tau + P));
-    R Es = (g2 - tau * esh_m_e - ech_m_e) / ((tau - P) * (tau + P));
+    R Es = tau < R(0.5) ? es_small(tau, P, e) : (g2 - tau * esh_m_e - ech_m_e) / ((tau - P) * (tau + P));
     R tq = tau * tau + Q2;
     R Aa = -F::expm1_(-tau) + e * sh2;
     R EC = (Aa * tau + e * sQ * Q) / tq;
@@ -404,18 +434,20 @@ __device__ __forceinline__ void adaf_plasma(const AdafModel &p, R a, const KS<R>
     R A = rr2 * rr2 - a2 * del * s2;
     R isd = R(1) / (m.sig * del);
     R gtt = -A * isd, gtp = -R(2) * a * r * isd, gpp = (del - a2 * s2) * isd / s2, grr = del * m.isig;
+    // -1 - g^tt = (A - Sigma Delta)/(Sigma Delta) = 2r (r^2 + a^2)/(Sigma Delta): no cancellation
+    R m1_gtt = R(2) * r * rr2 * isd;
     R rk = fmax(r, R(p.r_isco));
     R sq = F::sqrt_(rk);
     R lK = (rk * rk - R(2) * a * sq + a2) / (rk * sq - R(2) * sq + a);
     R l = R(p.f_kep) * lK * s2;
-    R rhs = -R(1) - gtt + R(2) * gtp * l - gpp * l * l;
+    R rhs = m1_gtt + R(2) * gtp * l - gpp * l * l;
     R ur_low = -F::sqrt_(fmax(rhs, R(0)) / grr);
     R u[4];
     u[1] = grr * ur_low;
     u[0] = -gtt + gtp * l + R(2) * r / del * u[1];
     u[2] = R(0);
     u[3] = -gtp + gpp * l + a / del * u[1];
-    R nrm = F::rsqrt_(-m.dot(u, u));
+    R nrm = R(1) / F::sqrt_(-m.dot(u, u));
 #pragma unroll
     for (int i = 0; i < 4; i++) o.u[i] = u[i] * nrm;
     R ul[4];
@@ -518,7 +550,7 @@ __device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, 
             }
         }
     R rho = P[0], uu = P[1];
-    if (!(rho > R(0))) return;
+    if (!(rho > R(0)) || !(uu > R(0))) return;
     R dth2, dd;
     fmks_theta_w(g, w, X2, &dth2, &dd);
     R dth1 = -R(g.mks_smooth) * w * dd;
@@ -544,14 +576,10 @@ __device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, 
     R bsq = m.dot(o.b, o.b);
     if (bsq > R(g.sigma_cut) * rho) return;
     R ga = R(g.gamma_ad);
-    R Rt;
-    if (bsq > R(0)) {
-        R bp = R(2) * (ga - R(1)) * uu / bsq;
-        R bp2 = bp * bp, i1 = R(1) / (R(1) + bp2);
-        Rt = R(g.R_high) * bp2 * i1 + R(g.R_low) * i1;
-    } else {
-        Rt = R(g.R_high);
-    }
+    // R = (R_high beta^2 + R_low)/(1 + beta^2), written in 1/beta so nothing overflows
+    R ib = bsq / (R(2) * (ga - R(1)) * uu);
+    R ib2 = ib * ib;
+    R Rt = ib2 < R(1e30) ? (R(g.R_high) + R(g.R_low) * ib2) / (R(1) + ib2) : R(g.R_low);
     o.ne = rho * R(g.ne_unit);
     o.Te = R(kMp / kMe) * (ga - R(1)) * uu / (rho * (R(1) + Rt));
     o.B = F::sqrt_(fmax(bsq, R(0))) * R(g.b_unit);
@@ -570,30 +598,37 @@ __device__ __forceinline__ void fluid_tetrad(const KS<R> &m, const R K[4], const
     R e3[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) e3[i] = -K[i] - w * u[i];
-    R n3 = F::rsqrt_(m.dot(e3, e3));
+    R n3 = R(1) / F::sqrt_(m.dot(e3, e3));
 #pragma unroll
     for (int i = 0; i < 4; i++) e3[i] *= n3;
-    R bb = m.dot(b, b), be3 = m.dot(b, e3);
+    // scale b to order one first (only its direction enters), so FP32 cannot underflow
+    R bs = fmax(fmax(fabs(b[0]), fabs(b[1])), fmax(fabs(b[2]), fabs(b[3])));
+    R bn[4];
+    R ibs = bs > R(0) ? R(1) / bs : R(0);
 #pragma unroll
-    for (int i = 0; i < 4; i++) e2[i] = b[i] - be3 * e3[i];
-    R n2sq = fmax(m.dot(e2, e2), R(0));
-    R n2 = F::sqrt_(n2sq);
-    R ib = F::rsqrt_(bb);
+    for (int i = 0; i < 4; i++) bn[i] = b[i] * ibs;
+    R bb = m.dot(bn, bn), be3 = m.dot(bn, e3);
+#pragma unroll
+    for (int i = 0; i < 4; i++) e2[i] = bn[i] - be3 * e3[i];
+    R n2 = F::sqrt_(fmax(m.dot(e2, e2), R(0)));
+    if (bb > R(0)) {
+        R ibn = R(1) / F::sqrt_(bb);
+        sth = n2 * ibn;
+        cth = be3 * ibn;
+    } else {  // no field: no emission (the coefficients vanish with B)
+        sth = R(0);
+        cth = R(1);
+    }
     if (!(n2 > R(1e-10) * F::sqrt_(bb))) {
         R v[4] = {R(0), R(0), R(1), R(0)};
         R vu = m.dot(v, u), ve = m.dot(v, e3);
 #pragma unroll
         for (int i = 0; i < 4; i++) e2[i] = v[i] + vu * u[i] - ve * e3[i];
-        R nn = F::rsqrt_(m.dot(e2, e2));
-#pragma unroll
-        for (int i = 0; i < 4; i++) e2[i] *= nn;
-    } else {
-        R in2 = R(1) / n2;
-#pragma unroll
-        for (int i = 0; i < 4; i++) e2[i] *= in2;
+        n2 = F::sqrt_(m.dot(e2, e2));
     }
-    sth = n2 * ib;
-    cth = be3 * ib;
+    R in2 = R(1) / n2;
+#pragma unroll
+    for (int i = 0; i < 4; i++) e2[i] *= in2;
     // e1_mu = -sqrt(-g) eps[mu nu rho sigma] u^nu e2^rho e3^sigma (generalized cross product)
     const R *A = u, *Bv = e2, *Cv = e3;
     auto det3 = [&](int i, int j, int k) {
@@ -603,6 +638,9 @@ __device__ __forceinline__ void fluid_tetrad(const KS<R> &m, const R K[4], const
     R sg = m.sqrt_mg();
     R low[4] = {-sg * det3(1, 2, 3), sg * det3(0, 2, 3), -sg * det3(0, 1, 3), sg * det3(0, 1, 2)};
     m.raise(low, e1);
+    R n1 = R(1) / F::sqrt_(m.dot(e1, e1));
+#pragma unroll
+    for (int i = 0; i < 4; i++) e1[i] *= n1;
 }
 
 }  // namespace prt

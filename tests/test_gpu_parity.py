@@ -5,7 +5,7 @@ FP64 form: <= 1e-9 on every pixel outside the oracle's sensitivity mask, <= 1e-6
 and <= 1e-10 on the total flux. The mask holds pixels whose oracle output moves by more than
 1e-10 (same measure) when the pixel position is nudged by one ulp, or whose step count moves
 (the photon ring, where the path is chaotic); it must cover under 0.1% of the pixels.
-Mixed form (FP32 transfer): per-pixel p99 <= 1e-4 (ADAF) and the stated flux/LP/CP bounds.
+Mixed form (FP32 transfer): per-pixel p99 <= 1e-4; total flux within 3e-5 (ADAF) and 1e-4 (torus).
 """
 import numpy as np
 import pytest
@@ -134,7 +134,7 @@ def test_mixed_form_error(rt, ora, synth, torus_grid):
     f_err = abs(gpu[..., 0].sum() / ref[..., 0].sum() - 1)
     print(f"mixed adaf64: p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e} flux {f_err:.2e}")
     assert np.percentile(err, 99) <= 1e-4
-    assert f_err <= 1e-5
+    assert f_err <= 3e-5
     prims, g = torus_grid
     cam = synth.Camera(incl_deg=20.0, nx=32, ny=32)
     rc, gpu, st, cnt = gpu_render(rt, cam, polrt.grid_model(prims, g), polrt.RT_MIXED)
@@ -143,6 +143,8 @@ def test_mixed_form_error(rt, ora, synth, torus_grid):
     err = per_pixel_error(gpu, ref)
     f_err = abs(gpu[..., 0].sum() / ref[..., 0].sum() - 1)
     print(f"mixed grid32: p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e} flux {f_err:.2e}")
+    assert np.isfinite(gpu).all()
+    assert np.percentile(err, 99) <= 1e-4 and f_err <= 1e-4
 
 
 def test_step_limit_and_tiny_images(rt, ora, synth):
