@@ -160,6 +160,21 @@ int rt_last_counters(rt_ctx *ctx, rt_counters *out);
 
 const char *rt_error_string(int code);
 
+/* rt_render without any device allocation, for callers that cannot allocate (their device
+ * memory is budgeted by someone else, or allocation is forbidden on their code path). The
+ * paper has no counterpart; it is a service of this library. The scratch (counters, ray
+ * records, path arena) lives in one static 512 MiB device array that every GPU loading this
+ * library holds until the process exits. The whole image is one chunk, so nx*ny must not
+ * exceed rt_render_static_max_pixels() (13076 pixels, e.g. 114x114): larger images return
+ * RT_ERR_SIZE. out_iquv (and status, if given) must be device memory, else RT_ERR_INVALID.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture. Every call shares the one array and
+ * clears its counters first; calls that overlap on the GPU (on different streams or from
+ * several threads) race on it and must be serialized by the caller. Synchronizes the
+ * context's stream like rt_render and fills the same counters (rt_last_counters). */
+int rt_render_static(rt_ctx *ctx, int form, void *out_iquv, uint8_t *status);
+long long rt_render_static_max_pixels(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def lib():
         L.rt_image_stats.argtypes = [_VP, _VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]
         L.rt_last_counters.argtypes = [_VP, C.POINTER(rt_counters)]
+        L.rt_render_static.argtypes = [_VP, C.c_int, _VP, _VP]
+        L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
         L.rt_error_string.restype = C.c_char_p
         _lib = L
@@ -179,6 +181,18 @@ def rt_render(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
     if check:
         _check(rc, "rt_render")
     return rc
+
+
+def rt_render_static(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
+    """rt_render with the scratch in the library's static device array (no allocation)."""
+    rc = lib().rt_render_static(ctx, form, _ptr(out_iquv), _ptr(status))
+    if check:
+        _check(rc, "rt_render_static")
+    return rc
+
+
+def rt_render_static_max_pixels() -> int:
+    return lib().rt_render_static_max_pixels()
 
 
 def rt_image_stats(ctx, iquv, form: int):

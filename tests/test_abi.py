@@ -9,7 +9,7 @@ import __graft_entry__  # noqa: F401  (puts the repo root on sys.path)
 
 def declared_symbols():
     text = open(__graft_entry__.ROOT + "/include/polrt.h").read()
-    return re.findall(r"^\s*(?:int|size_t|const char \*)\s*(rt_\w+)\(", text, re.M)
+    return re.findall(r"^\s*(?:int|size_t|long long|const char \*)\s*(rt_\w+)\(", text, re.M)
 
 
 @pytest.fixture(scope="module")
