@@ -82,6 +82,7 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     c->fp64_bps = transfer_blocks_per_sm_fp64();
     c->mixed_bps = transfer_blocks_per_sm_mixed();
     bool ok = cudaMalloc(&c->d_stats, 8 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->d_sctab, kSinTabBytes) == cudaSuccess &&
               cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess;
     for (int i = 0; i < 3 && ok; i++) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
     if (!ok) {
@@ -90,6 +91,12 @@ int rt_create(rt_ctx **out, int device, void *stream) {
         return RT_ERR_CUDA;
     }
     memset(c->h_ctr, 0, sizeof(Counters));
+    launch_sincos_table(c->d_sctab, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rt_destroy(c);
+        return RT_ERR_CUDA;
+    }
     *out = c;
     return RT_OK;
 }
@@ -104,6 +111,7 @@ int rt_destroy(rt_ctx *c) {
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
     cudaFree(c->d_stats);
+    cudaFree(c->d_sctab);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     for (int i = 0; i < 3; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -340,7 +348,7 @@ int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     for (long long o = 0; o < nrays; o += chunk) {
         long long n = std::min(chunk, nrays - o);
         CK(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), c->stream));  // queues + arena
-        GeoArgs ga{cam, ar, rec, ctr, n, o};
+        GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
         XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status};
         if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
         launch_geodesic(ga, geo_grid, c->stream);

@@ -16,14 +16,15 @@ __device__ __forceinline__ double step_size(double eps, const double y[7]) {
 }
 
 // y = (r, theta, phi, K^t, K^r, K^theta, K^phi); t is never needed (stationary metric).
-__device__ __forceinline__ void rk4_step(double a, double h, const double y[7], double out[7]) {
+__device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double a, double h, const double y[7],
+                                         double out[7]) {
     double k1[7], k2[7], k3[7], k4[7], t[7];
     auto rhs = [&](const double *z, double *dz) {
         dz[0] = z[4];
         dz[1] = z[5];
         dz[2] = z[6];
         double acc[4];
-        geo_accel(a, z[0], z[1], z + 3, acc);
+        geo_accel(tab, a, z[0], z[1], z + 3, acc);
         dz[3] = acc[0];
         dz[4] = acc[1];
         dz[5] = acc[2];
@@ -44,7 +45,7 @@ __device__ __forceinline__ void rk4_step(double a, double h, const double y[7], 
     for (int i = 0; i < 7; i++) out[i] = y[i] + h6 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
-__global__ void __launch_bounds__(kGeoThreads) geodesic_kernel(GeoArgs p) {
+__global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
     const Camera &c = p.cam;
     double y[7];
     long long ray = -1;
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kGeoThreads) geodesic_kernel(GeoArgs p) {
 
         double h = step_size(c.eps, y);
         double yn[7];
-        rk4_step(c.a, h, y, yn);
+        rk4_step(p.sctab, c.a, h, y, yn);
         bool refl = false;
         if (yn[1] < 0.0) {
             yn[1] = -yn[1];
@@ -146,6 +147,21 @@ __global__ void __launch_bounds__(kGeoThreads) geodesic_kernel(GeoArgs p) {
     }
     // one counter update per lane
     if (my_steps) atomicAdd(&p.ctr->steps, my_steps);
+}
+
+__global__ void sincos_table_kernel(double *tab) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kSinTab) return;
+    double th = kSinLo + k * kSinH;
+    double s, c;
+    sincos(th, &s, &c);
+    tab[3 * k] = th;
+    tab[3 * k + 1] = s;
+    tab[3 * k + 2] = c;
+}
+
+void launch_sincos_table(double *tab, cudaStream_t s) {
+    sincos_table_kernel<<<(kSinTab + 255) / 256, 256, 0, s>>>(tab);
 }
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s) {

@@ -39,9 +39,15 @@ struct KS {
     R Itt, Itr, Irr, Irp, Ihh, Ipp;  // g^{mu nu}
 
     __device__ __forceinline__ void eval(R a_, R r_, R th) {
+        R s_, c_;
+        Fn<R>::sc(th, &s_, &c_);
+        eval_sc(a_, r_, s_, c_);
+    }
+    __device__ __forceinline__ void eval_sc(R a_, R r_, R s_, R c_) {
         a = a_;
         r = r_;
-        Fn<R>::sc(th, &s, &c);
+        s = s_;
+        c = c_;
         s2 = s * s;
         sc = s * c;
         R a2 = a * a;
@@ -121,10 +127,40 @@ struct DK {
     }
 };
 
+// sin and cos of theta for the FP64 geodesic by table-driven angle addition: theta_k from a
+// table of (theta_k, sin theta_k, cos theta_k) at spacing h = 1.5 pi / 2048 over
+// [-pi/4, 5 pi/4], delta = theta - theta_k (|delta| <= h/2 < 1.2e-3), then
+// sin(theta_k + delta) = s_k cos(delta) + c_k sin(delta) with the Taylor polynomials
+// sin d = d - d^3/6 + d^5/120 and cos d = 1 - d^2/2 + d^4/24 - d^6/720 (remainders below
+// 1e-20 relative). Outside the table range it falls back to sincos().
+constexpr int kSinTab = 2048;
+constexpr double kSinLo = -0.25 * kPi;
+constexpr double kSinH = 1.5 * kPi / (kSinTab - 1);
+
+__device__ __forceinline__ void sincos_tab(const double *__restrict__ tab, double th, double *s, double *c) {
+    double t = (th - kSinLo) * (1.0 / kSinH);
+    if (!(t > 1.0 && t < kSinTab - 2.0)) {
+        sincos(th, s, c);
+        return;
+    }
+    int k = __double2int_rn(t);
+    const double *e = tab + 3 * k;
+    double d = th - __ldg(e);
+    double sk = __ldg(e + 1), ck = __ldg(e + 2);
+    double d2 = d * d;
+    double sd = fma(d * d2, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);
+    double cd = fma(d2, fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    *s = fma(sk, cd, ck * sd);
+    *c = fma(ck, cd, -sk * sd);
+}
+
 // Geodesic acceleration dK/dl = -Gamma K K (FP64 path).
-__device__ __forceinline__ void geo_accel(double a, double r, double th, const double K[4], double acc[4]) {
+__device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, double a, double r, double th,
+                                          const double K[4], double acc[4]) {
     KS<double> m;
-    m.eval(a, r, th);
+    double s_, c_;
+    sincos_tab(sctab, th, &s_, &c_);
+    m.eval_sc(a, r, s_, c_);
     DK<double> d;
     d.eval(m, K);
     double W = K[0] + K[1];

@@ -140,7 +140,7 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
         cudaGetLastError();
         return RT_ERR_CUDA;
     }
-    GeoArgs ga{cam, ar, rec, ctr, nrays, 0};
+    GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, nrays, 0};
     XferArgs xa{cam, mod, ar, rec, ctr, nrays, 0, out_iquv, status};
     cudaEventRecord(c->ev[0], c->stream);
     launch_geodesic(ga, c->nsm * c->geo_bps, c->stream);

@@ -24,6 +24,7 @@ struct rt_ctx {
     uint8_t *d_stage_status = nullptr;
     size_t stage_status_bytes = 0;
     double *d_stats = nullptr;
+    double *d_sctab = nullptr;  // sin/cos table of the FP64 geodesic
     prt::Counters *h_ctr = nullptr;  // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     long long last_rays = 0, last_blocks_total = 0;

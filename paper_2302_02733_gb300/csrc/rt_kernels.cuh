@@ -9,6 +9,7 @@ constexpr int kXferThreads = 128;
 
 struct GeoArgs {
     Camera cam;
+    const double *sctab;  // (theta, sin, cos) table of the FP64 geodesic, 2048 entries
     Arena arena;
     RayRecord *rec;       // per ray of this chunk
     Counters *ctr;
@@ -28,6 +29,8 @@ struct XferArgs {
 };
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
+void launch_sincos_table(double *tab, cudaStream_t s);
+constexpr size_t kSinTabBytes = 2048 * 3 * sizeof(double);
 void launch_transfer_fp64(const XferArgs &a, int grid, cudaStream_t s);
 void launch_transfer_mixed(const XferArgs &a, int grid, cudaStream_t s);
 void launch_x2_table(const GridModel &g, double *table, cudaStream_t s);

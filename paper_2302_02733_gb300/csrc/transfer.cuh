@@ -505,19 +505,18 @@ __device__ __forceinline__ R fmks_x2(const GridModel &g, R w, R th) {
 }
 
 template <typename R>
-__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, R r, R th, double ph,
-                                            Plasma<R> &o) {
+__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, R r, R th, R ph, Plasma<R> &o) {
     typedef Mth<R> F;
     o.valid = false;
     if (r < R(g.r_in) || r > R(g.r_out)) return;
     R X1 = F::log_(r);
     R w = F::exp_(R(g.mks_smooth) * (R(g.x1in) - X1));
     R X2 = fmks_x2(g, w, th);
-    double X3 = fmod(ph, 2.0 * kPi);
-    if (X3 < 0.0) X3 += 2.0 * kPi;
+    R X3 = F::fmod_(ph, R(2.0 * kPi));
+    if (X3 < R(0)) X3 += R(2.0 * kPi);
     R fi = (X1 - R(g.x1in)) / R(g.dx1) - R(0.5);
     R fj = X2 / R(g.dx2) - R(0.5);
-    R fk = R(X3 / g.dx3 - 0.5);
+    R fk = X3 / R(g.dx3) - R(0.5);
     fi = fmin(fmax(fi, R(0)), R(g.n1 - 1));
     fj = fmin(fmax(fj, R(0)), R(g.n2 - 1));
     int i0 = min((int)fi, g.n1 - 2), j0 = min((int)fj, g.n2 - 2);

@@ -8,6 +8,34 @@
 
 namespace prt {
 
+// double -> float rounded to nearest even with integer operations only, so the FP32 form
+// reads the FP64 path without using the FP64 pipe. Magnitudes below the float normal range
+// become signed zero; above it, infinity.
+__device__ __forceinline__ float d2f_int(double d) {
+    unsigned long long x = (unsigned long long)__double_as_longlong(d);
+    unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
+    unsigned sign = hi & 0x80000000u;
+    int fe = (int)((hi >> 20) & 0x7ffu) - 896;
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+    unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned rem = lo & 0x1fffffffu;
+    unsigned f = sign | ((unsigned)fe << 23) | mant;
+    f += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (mant & 1u));
+    return __uint_as_float(f);
+}
+
+template <typename R>
+__device__ __forceinline__ R to_real(double d);
+template <>
+__device__ __forceinline__ double to_real<double>(double d) {
+    return d;
+}
+template <>
+__device__ __forceinline__ float to_real<float>(double d) {
+    return d2f_int(d);
+}
+
 template <typename R>
 __device__ __forceinline__ void heun_transport(R E[4], const R T1[4][4], const R T0[4][4], R h) {
     R a[4], v[4];
@@ -96,13 +124,14 @@ __global__ void __launch_bounds__(kXferThreads) transfer_kernel(XferArgs p) {
         n--;
         const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
         double4_32a q0 = src[0], q1 = src[1];
-        R r = R(q0.x), th = R(q0.y);
-        R K[4] = {R(q0.w), R(q1.x), R(q1.y), R(q1.z)};
-        R h = R(fabs(q1.w));
+        R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
+        R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
+        R hs = to_real<R>(q1.w);
+        R h = fabs(hs);
         KS<R> m;
         m.eval(a, r, th);
         if (basis) {
-            if (q1.w < 0.0) {  // that step crossed the polar axis: bring n+1 into this chart
+            if (hs < R(0)) {  // that step crossed the polar axis: bring n+1 into this chart
                 E1[2] = -E1[2];
                 E2[2] = -E2[2];
 #pragma unroll
@@ -124,7 +153,7 @@ __global__ void __launch_bounds__(kXferThreads) transfer_kernel(XferArgs p) {
         if (p.model.kind == 1)
             adaf_plasma(p.model.adaf, a, m, r, pl);
         else
-            grid_plasma(p.model.grid, m, r, th, q0.z, pl);
+            grid_plasma(p.model.grid, m, r, th, ph, pl);
         if (pl.valid) {
             R e1[4], e2[4], w, sth, cth;
             fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
