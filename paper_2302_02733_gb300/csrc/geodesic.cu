@@ -10,9 +10,13 @@
 
 namespace prt {
 
+// h = eps / (|K^r|/r + |K^th|/tt + |K^ph| + 1e-40), tt = max(min(th, pi - th), 0.01), taken
+// with one division: h = eps r tt / (|K^r| tt + |K^th| r + (|K^ph| + 1e-40) r tt).
 __device__ __forceinline__ double step_size(double eps, const double y[7]) {
     double tt = fmax(fmin(y[1], kPi - y[1]), 1e-2);
-    return eps / (fabs(y[4]) / y[0] + fabs(y[5]) / tt + fabs(y[6]) + 1e-40);
+    double rt = y[0] * tt;
+    double den = fma(fabs(y[6]) + 1e-40, rt, fma(fabs(y[4]), tt, fabs(y[5]) * y[0]));
+    return eps * rt / den;
 }
 
 // y = (r, theta, phi, K^t, K^r, K^theta, K^phi); t is never needed (stationary metric).
@@ -30,19 +34,19 @@ __device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double 
         dz[5] = acc[2];
         dz[6] = acc[3];
     };
+    const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
     rhs(y, k1);
 #pragma unroll
-    for (int i = 0; i < 7; i++) t[i] = y[i] + 0.5 * h * k1[i];
+    for (int i = 0; i < 7; i++) t[i] = fma(h2, k1[i], y[i]);
     rhs(t, k2);
 #pragma unroll
-    for (int i = 0; i < 7; i++) t[i] = y[i] + 0.5 * h * k2[i];
+    for (int i = 0; i < 7; i++) t[i] = fma(h2, k2[i], y[i]);
     rhs(t, k3);
 #pragma unroll
-    for (int i = 0; i < 7; i++) t[i] = y[i] + h * k3[i];
+    for (int i = 0; i < 7; i++) t[i] = fma(h, k3[i], y[i]);
     rhs(t, k4);
-    const double h6 = h / 6.0;
 #pragma unroll
-    for (int i = 0; i < 7; i++) out[i] = y[i] + h6 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+    for (int i = 0; i < 7; i++) out[i] = fma(h6, k4[i], fma(h3, k3[i], fma(h3, k2[i], fma(h6, k1[i], y[i]))));
 }
 
 __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {

@@ -154,30 +154,67 @@ __device__ __forceinline__ void sincos_tab(const double *__restrict__ tab, doubl
     *c = fma(ck, cd, -sk * sd);
 }
 
-// Geodesic acceleration dK/dl = -Gamma K K (FP64 path).
+// Geodesic acceleration dK/dl = -Gamma K K (FP64 path), arranged for the FP64 pipe: every
+// product that can be folded into a fused multiply-add is, and products shared by the
+// D, P and Q contractions are formed once. Same quantities as DK::eval / connection_T:
+//   A_nu = D_{nu b} K^b, B_r = K.P/2, B_th = K.Q/2, acc = -g^{-1} (A - B).
 __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, double a, double r, double th,
                                           const double K[4], double acc[4]) {
-    KS<double> m;
-    double s_, c_;
-    sincos_tab(sctab, th, &s_, &c_);
-    m.eval_sc(a, r, s_, c_);
-    DK<double> d;
-    d.eval(m, K);
-    double W = K[0] + K[1];
-    double At = d.d1 * W + d.dtp * K[3];
-    double Ar = d.d1 * W + d.drp * K[3];
-    double Ah = d.dhh * K[2];
-    double Ap = d.dtp * K[0] + d.drp * K[1] + d.dpp * K[3];
-    // B_nu = 1/2 d_nu g_ab K^a K^b = 1/2 K.P (nu = r), 1/2 K.Q (nu = theta)
-    double Br = 0.5 * (d.P[0] * K[0] + d.P[1] * K[1] + d.P[2] * K[2] + d.P[3] * K[3]);
-    double Bh = 0.5 * (d.Qv[0] * K[0] + d.Qv[1] * K[1] + d.Qv[2] * K[2] + d.Qv[3] * K[3]);
-    double F[4] = {At, Ar - Br, Ah - Bh, Ap};
-    double u[4];
-    m.raise(F, u);
-    acc[0] = -u[0];
-    acc[1] = -u[1];
-    acc[2] = -u[2];
-    acc[3] = -u[3];
+    const double a2 = a * a;
+    double s, c;
+    sincos_tab(sctab, th, &s, &c);
+    const double Kt = K[0], Kr = K[1], Kh = K[2], Kp = K[3];
+    // metric pieces
+    double s2 = s * s, sc = s * c;
+    double r2 = r * r;
+    double sig = fma(a2 * c, c, r2);
+    double iss = 1.0 / (sig * s2);  // 1/(Sigma sin^2)
+    double isig = iss * s2;         // 1/Sigma
+    double tr = r + r;
+    double q = tr * isig;           // 2r/Sigma
+    double op = 1.0 + q;
+    double dqr = fma(-q, q, isig + isig);      // d q/dr
+    double two_sc = sc + sc;
+    double dqt = (a2 * two_sc) * (q * isig);   // d q/dtheta
+    // contractions with K
+    double W = Kt + Kr;
+    double as2 = a * s2;
+    double V = fma(-as2, Kp, W);               // l_mu K^mu
+    double d1 = fma(Kr, dqr, Kh * dqt);        // D_tt = D_tr = D_rr
+    double scK = two_sc * Kh;
+    double aq = a * q;
+    double ndtp = fma(as2, d1, aq * scK);      // -D_tphi
+    double ndrp = fma(a, scK, ndtp);           // -D_rphi
+    double a2scK = a2 * scK;
+    double dhh = fma(tr, Kr, -a2scK);          // D_thth
+    double a2s2 = a2 * s2;
+    double bigp = fma(a2s2, q + q, sig + a2s2);
+    double dpp = fma(s2, fma(tr, Kr, a2s2 * d1), bigp * scK);  // D_phiphi
+    double P0 = dqr * V;                       // P_t = P_r
+    double P2 = tr * Kh;
+    double P3 = fma(-as2, P0, (tr * s2) * Kp);
+    double sca = two_sc * a;
+    double scaK = sca * Kp;
+    double dqtV = dqt * V;
+    double Q0 = fma(-scaK, q, dqtV);
+    double Q1 = Q0 - scaK;
+    double Q3 = fma(two_sc * bigp, Kp, -fma(sca, fma(q, Kt, op * Kr), as2 * dqtV));
+    // A_nu, B_nu and F = A - B
+    double d1W = d1 * W;
+    double At = fma(-ndtp, Kp, d1W);
+    double Ar = fma(-ndrp, Kp, d1W);
+    double Ap = fma(dpp, Kp, -fma(ndtp, Kt, ndrp * Kr));
+    double sumP = fma(P3, Kp, fma(P2, Kh, P0 * W));
+    double sumQ = fma(Q3, Kp, fma(-a2scK, Kh, fma(Q1, Kr, Q0 * Kt)));
+    double Fr = fma(-0.5, sumP, Ar);
+    double Fh = fma(-0.5, sumQ, dhh * Kh);
+    // acc = -g^{-1} F with g^tt = -(1+q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
+    // g^thth = 1/Sigma, g^phiphi = 1/(Sigma sin^2)
+    double del = (r2 - tr) + a2;
+    acc[0] = fma(op, At, -q * Fr);
+    acc[1] = -fma(isig, fma(del, Fr, a * Ap), q * At);
+    acc[2] = -isig * Fh;
+    acc[3] = -fma(iss, Ap, (a * isig) * Fr);
 }
 
 // T^mu_b = Gamma^mu_{a b} K^a = 1/2 g^{mu nu} (D_{nu b} + [b=r] P_nu + [b=th] Q_nu

@@ -69,7 +69,7 @@ __device__ __forceinline__ void reproject(const R f1[4], const R f2[4], const R 
 }
 
 template <typename R, typename OutT>
-__global__ void __launch_bounds__(kXferThreads) transfer_kernel(XferArgs p) {
+__global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer_kernel(XferArgs p) {
     typedef Mth<R> F;
     __shared__ R sgw[32];
     if (threadIdx.x < BesselCfg<R>::nq) {
