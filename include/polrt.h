@@ -47,8 +47,11 @@ enum { RT_MODEL_ADAF = 1, RT_MODEL_GRID = 2 };
 /* Forms of the hot path. */
 enum {
     RT_FP64 = 0,  /* geodesic, plasma, coefficients and transfer all in FP64; output double */
-    RT_MIXED = 1  /* FP64 geodesic and path; FP32 plasma fetch, coefficients and transfer
-                     with compensated optical-depth and Faraday-phase sums; output float */
+    RT_MIXED = 1  /* FP64 geodesic and path; FP32 plasma fetch, coefficients and transfer.
+                     The Stokes vector is carried as a compensated pair (value + error term):
+                     every step forms its change (screen re-projection, radiative step) as an
+                     increment and adds it by an error-free sum, and the optical and Faraday
+                     depths are Kahan sums. Output float. */
 };
 
 /* Per-pixel status codes written to the optional status buffer. */
@@ -148,6 +151,14 @@ int rt_workspace_hint(const rt_ctx *ctx, size_t *bytes);
  * returns (it reads the ray counters). It returns RT_ERR_WORKSPACE if any ray overflowed the
  * path arena; those pixels are zero with status RT_RAY_OVERFLOW. */
 int rt_render(rt_ctx *ctx, int form, void *out_iquv, uint8_t *status);
+
+/* rt_render that also writes, per pixel, the optical depth tau = sum alpha_I ds and the
+ * Faraday depth phi = sum rho_V ds accumulated along the ray over its emitting points (the
+ * exponents of the isotropic absorption and of the Faraday rotation that the constant-
+ * coefficient steps of Section 2.1's transfer apply; alpha and rho in the fluid frame, ds the
+ * fluid-frame path length). out_depth: nx*ny*2 values [iy][ix][tau, phi] of the form's type,
+ * host or device; it must not be NULL. Both sums are compensated (Kahan) in either form. */
+int rt_render_depths(rt_ctx *ctx, int form, void *out_iquv, uint8_t *status, void *out_depth);
 
 /* Total flux [Jy] = sum(I) dOmega 1e23, dOmega = (fov_M L / (nx D))^2, and the net linear
  * and circular polarization fractions sqrt(sum Q^2 + sum U^2)/sum I, sum V / sum I, from an

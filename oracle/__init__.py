@@ -79,7 +79,7 @@ def lib():
         L.ora_thermal_coeffs.argtypes = [C.c_double] * 5 + [_D]
         L.ora_substep.argtypes = [_D, C.c_double, _D, _D]
         L.ora_render_pixels.argtypes = [C.POINTER(Camera), C.POINTER(Model), C.c_int, _I, _I, C.c_int,
-                                        _D, _I, _I, _D, C.c_int]
+                                        _D, _I, _I, _D, _D, C.c_int]
         L.ora_render_pixels.restype = C.c_int
         L.ora_image_stats.argtypes = [C.POINTER(Camera), _D, C.c_long, _D, _D, _D]
         _lib = L
@@ -127,8 +127,10 @@ def grid_model(prims: np.ndarray, g) -> ModelHandle:
     return ModelHandle(m, prims)
 
 
-def render_pixels(cam: Camera, model: ModelHandle, ix, iy, pert: int = 0, nthreads: int = 0):
-    """Render the listed pixels; returns (iquv[n,4], nsteps[n], status[n], minpol[n])."""
+def render_pixels(cam: Camera, model: ModelHandle, ix, iy, pert: int = 0, nthreads: int = 0,
+                  depth: bool = False):
+    """Render the listed pixels; returns (iquv[n,4], nsteps[n], status[n], minpol[n]), and
+    with depth=True also depth[n,2] = (tau = sum alpha_I ds, phi = sum rho_V ds)."""
     L = lib()
     ix = np.ascontiguousarray(ix, dtype=np.int32)
     iy = np.ascontiguousarray(iy, dtype=np.int32)
@@ -137,19 +139,25 @@ def render_pixels(cam: Camera, model: ModelHandle, ix, iy, pert: int = 0, nthrea
     ns = np.zeros(n, dtype=np.int32)
     stt = np.zeros(n, dtype=np.int32)
     mp = np.zeros(n)
+    dep = np.zeros((n, 2))
     rc = L.ora_render_pixels(C.byref(cam), C.byref(model.st), n, _ip(ix), _ip(iy), pert, _dp(out), _ip(ns),
-                             _ip(stt), _dp(mp), nthreads)
+                             _ip(stt), _dp(mp), _dp(dep) if depth else None, nthreads)
     if rc != 0:
         raise MemoryError("oracle render failed")
+    if depth:
+        return out, ns, stt, mp, dep
     return out, ns, stt, mp
 
 
-def render_image(cam: Camera, model: ModelHandle, pert: int = 0, nthreads: int = 0):
-    """Full image, row-major [ny][nx][4]."""
+def render_image(cam: Camera, model: ModelHandle, pert: int = 0, nthreads: int = 0, depth: bool = False):
+    """Full image, row-major [ny][nx][4] (and [ny][nx][2] depths with depth=True)."""
     iy, ix = np.meshgrid(np.arange(cam.ny), np.arange(cam.nx), indexing="ij")
-    out, ns, stt, mp = render_pixels(cam, model, ix.ravel(), iy.ravel(), pert, nthreads)
-    return (out.reshape(cam.ny, cam.nx, 4), ns.reshape(cam.ny, cam.nx), stt.reshape(cam.ny, cam.nx),
-            mp.reshape(cam.ny, cam.nx))
+    r = render_pixels(cam, model, ix.ravel(), iy.ravel(), pert, nthreads, depth)
+    out = (r[0].reshape(cam.ny, cam.nx, 4), r[1].reshape(cam.ny, cam.nx), r[2].reshape(cam.ny, cam.nx),
+           r[3].reshape(cam.ny, cam.nx))
+    if depth:
+        out = out + (r[4].reshape(cam.ny, cam.nx, 2),)
+    return out
 
 
 def trace_geodesic(cam: Camera, px: float, py: float):

@@ -808,6 +808,7 @@ static void N_from_stokes(const double e1[4], const double e2[4], const double S
 
 typedef struct {
     double st[4], minpol;
+    double tau, phi; /* optical depth sum alpha_I ds and Faraday depth sum rho_V ds */
 } pix_out;
 
 static pix_out transfer(const ora_camera *cam, const ora_model *m, const double *st, int M, double px,
@@ -817,7 +818,7 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
     double L = O_G * cam->M_bh_g / (O_C * O_C);
     cplx N[4][4];
     memset(N, 0, sizeof(N));
-    double minpol = 1.0;
+    double minpol = 1.0, tau = 0.0, phi = 0.0;
     for (int n = M - 1; n >= 0; n--) {
         const double *sn = st + n * 9, *s1 = st + (n + 1) * 9;
         double h = fabs(sn[8]);
@@ -853,6 +854,10 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
         ora_thermal_coeffs(pl[0], pl[1], pl[2], nu, thB, c8);
         double cf[11] = {c8[0], c8[1], 0.0, c8[2], c8[3], c8[4], 0.0, c8[5], c8[6], 0.0, c8[7]};
         double ds = w * h * L;
+        /* depths: the exponents of the isotropic absorption and the Faraday rotation that
+         * this segment's constant-coefficient step applies, summed along the ray */
+        tau += c8[3] * ds;
+        phi += c8[7] * ds;
         double w3 = w * w * w;
         double Sf[4], Sf1[4];
         for (int i = 0; i < 4; i++) Sf[i] = S[i] * w3;
@@ -885,12 +890,13 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
     double g[16], S[4];
     ora_metric_ks(a, st[1], st[2], g);
     stokes_from_N(g, X, Y, N, S);
-    pix_out o = {{S[0], S[1], S[2], S[3]}, minpol};
+    pix_out o = {{S[0], S[1], S[2], S[3]}, minpol, tau, phi};
     return o;
 }
 
 int ora_render_pixels(const ora_camera *cam, const ora_model *m, int npix, const int *ix, const int *iy,
-                      int pert, double *iquv, int *nsteps, int *status, double *minpol, int nthreads) {
+                      int pert, double *iquv, int *nsteps, int *status, double *minpol, double *depth,
+                      int nthreads) {
     int err = 0;
 #ifdef _OPENMP
     int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
@@ -918,6 +924,10 @@ int ora_render_pixels(const ora_camera *cam, const ora_model *m, int npix, const
                 if (nsteps) nsteps[p] = M;
                 if (status) status[p] = stat;
                 if (minpol) minpol[p] = o.minpol;
+                if (depth) {
+                    depth[2 * p] = o.tau;
+                    depth[2 * p + 1] = o.phi;
+                }
             }
             free(st);
         }

@@ -81,10 +81,12 @@ void ora_thermal_coeffs(double ne, double Thetae, double B, double nu, double th
 /* coef: jI jQ jU jV aI aQ aU aV rQ rU rV ; exact constant-coefficient solution over ds */
 void ora_substep(const double coef[11], double ds, const double S0[4], double S1[4]);
 
-/* full pixels: image-plane pixel (ix, iy) of the camera grid; pert 0 none, 1 px+ulp, 2 py+ulp */
+/* full pixels: image-plane pixel (ix, iy) of the camera grid; pert 0 none, 1 px+ulp, 2 py+ulp.
+ * depth (optional, 2 per pixel): tau = sum alpha_I ds and phi = sum rho_V ds over the emitting
+ * points, the exponents of the isotropic absorption and of the Faraday rotation along the ray. */
 int ora_render_pixels(const ora_camera *cam, const ora_model *m, int npix, const int *ix,
                       const int *iy, int pert, double *iquv, int *nsteps, int *status,
-                      double *minpol, int nthreads);
+                      double *minpol, double *depth, int nthreads);
 void ora_image_stats(const ora_camera *cam, const double *iquv, long npix, double *flux_jy,
                      double *lp, double *cp);
 

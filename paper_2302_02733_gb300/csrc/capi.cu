@@ -110,6 +110,7 @@ int rt_destroy(rt_ctx *c) {
     if (c->ws_owned) cudaFree(c->ws);
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
+    cudaFree(c->d_stage_depth);
     cudaFree(c->d_stats);
     cudaFree(c->d_sctab);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
@@ -254,7 +255,7 @@ static int ensure_stage(void **buf, size_t *have, size_t need) {
     return RT_OK;
 }
 
-int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
+static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *depth) {
     if (!c || !out_iquv || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
     if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
     CK(cudaSetDevice(c->device));
@@ -341,6 +342,13 @@ int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
         if (rv) return rv;
         d_status = c->d_stage_status;
     }
+    bool dep_dev = depth ? is_device_ptr(depth) : true;
+    void *d_depth = depth;
+    if (depth && !dep_dev) {
+        rv = ensure_stage(&c->d_stage_depth, &c->stage_depth_bytes, (size_t)nrays * 2 * esz);
+        if (rv) return rv;
+        d_depth = c->d_stage_depth;
+    }
 
     CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
     int geo_grid = c->nsm * c->geo_bps;
@@ -349,7 +357,7 @@ int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
         long long n = std::min(chunk, nrays - o);
         CK(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), c->stream));  // queues + arena
         GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
-        XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status};
+        XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
         if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
         launch_geodesic(ga, geo_grid, c->stream);
         if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
@@ -363,12 +371,23 @@ int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     if (!out_dev) CK(cudaMemcpyAsync(out_iquv, d_out, (size_t)nrays * 4 * esz, cudaMemcpyDeviceToHost, c->stream));
     if (status && !st_dev)
         CK(cudaMemcpyAsync(status, d_status, (size_t)nrays, cudaMemcpyDeviceToHost, c->stream));
+    if (depth && !dep_dev)
+        CK(cudaMemcpyAsync(depth, d_depth, (size_t)nrays * 2 * esz, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->last_rays = nrays;
     c->last_blocks_total = nblocks;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     return RT_OK;
+}
+
+int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
+    return render_impl(c, form, out_iquv, status, nullptr);
+}
+
+int rt_render_depths(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *out_depth) {
+    if (!out_depth) return RT_ERR_INVALID;
+    return render_impl(c, form, out_iquv, status, out_depth);
 }
 
 int rt_image_stats(rt_ctx *c, const void *iquv, int form, double *flux_jy, double *lp_frac, double *cp_frac) {

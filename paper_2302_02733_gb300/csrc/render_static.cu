@@ -141,7 +141,7 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
         return RT_ERR_CUDA;
     }
     GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, nrays, 0};
-    XferArgs xa{cam, mod, ar, rec, ctr, nrays, 0, out_iquv, status};
+    XferArgs xa{cam, mod, ar, rec, ctr, nrays, 0, out_iquv, status, nullptr};
     cudaEventRecord(c->ev[0], c->stream);
     launch_geodesic(ga, c->nsm * c->geo_bps, c->stream);
     cudaEventRecord(c->ev[1], c->stream);

@@ -23,6 +23,8 @@ struct rt_ctx {
     size_t stage_bytes = 0;
     uint8_t *d_stage_status = nullptr;
     size_t stage_status_bytes = 0;
+    void *d_stage_depth = nullptr;
+    size_t stage_depth_bytes = 0;
     double *d_stats = nullptr;
     double *d_sctab = nullptr;  // sin/cos table of the FP64 geodesic
     prt::Counters *h_ctr = nullptr;  // pinned

@@ -26,6 +26,7 @@ struct XferArgs {
     long long nrays, ray_offset;
     void *out;            // image [ny][nx][4] of double (FP64 form) or float (mixed form)
     uint8_t *status;      // optional per-pixel status
+    void *depth;          // optional [ny][nx][2] optical and Faraday depths, same type as out
 };
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);

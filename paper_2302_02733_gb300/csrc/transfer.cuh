@@ -222,6 +222,26 @@ __device__ __forceinline__ void thermal_coeffs(R ne, R Te, R B, R nu, R sth, R c
 //   Ec = int e^{-tau v} cosh(Pv), Es = int e^{-tau v} sinh(Pv)/P,
 //   EC = int e^{-tau v} cos(Qv),  ES = int e^{-tau v} sin(Qv)/Q   (v from 0 to 1),
 // each evaluated in a form free of cancellation (exponentials folded with e^{-tau}).
+// Error-free transformation of a sum (Knuth's TwoSum): hi + d = s + err exactly; s becomes the
+// value and err joins the compensation lo. Six additions, no assumption on |hi| vs |d|.
+template <typename R>
+__device__ __forceinline__ void two_sum_add(R &hi, R &lo, R d) {
+    R s = hi + d;
+    R bb = s - hi;
+    R err = (hi - (s - bb)) + (d - bb);
+    hi = s;
+    lo += err;
+}
+
+// Kahan's compensated summation: s + (-c) carries the running sum.
+template <typename R>
+__device__ __forceinline__ void kahan_add(R &s, R &c, R x) {
+    R y = x - c;
+    R t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 template <typename R>
 __device__ __forceinline__ R phi1(R x) {  // (1 - e^-x)/x
     typedef Mth<R> F;
@@ -278,10 +298,12 @@ __device__ __forceinline__ void bmul(R aQ, R aV, R rQ, R rV, const R v[4], R o[4
     o[3] = aV * v[0] - rQ * v[2];
 }
 
+// Increment of one constant-coefficient step by the Taylor series of the exponential applied
+// to the vector: acc = sum_k t_k, t_1 = J - M S, t_k = -M t_{k-1} / k.
 template <typename R>
-__device__ __forceinline__ void taylor_step(R tau, R aQ, R aV, R rQ, R rV, const R J[4], R S[4]) {
+__device__ __forceinline__ void taylor_inc(R tau, R aQ, R aV, R rQ, R rV, const R J[4], const R S[4], R acc[4]) {
     typedef Mth<R> F;
-    R t[4], acc[4], b[4];
+    R t[4], b[4];
     bmul(aQ, aV, rQ, rV, S, b);
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -301,21 +323,32 @@ __device__ __forceinline__ void taylor_step(R tau, R aQ, R aV, R rQ, R rV, const
         }
         if (m <= F::taylor_tol * sz) break;
     }
-#pragma unroll
-    for (int i = 0; i < 4; i++) S[i] += acc[i];
 }
 
+// One exact constant-coefficient step of dS/ds = J js - M S over ds on the compensated value
+// S + Slo (js scales the emissivities: 1/w^3 for the invariant form). Thin steps (the common
+// case) form the increment by the Taylor series and add it without rounding loss; thick steps
+// fold Slo in and apply the closed form.
 template <typename R>
-__device__ void substep(const R cf[8], R ds, R S[4]) {
+__device__ void substep(const R cf[8], R ds, R js, R S[4], R Slo[4]) {
     typedef Mth<R> F;
     R tau = cf[3] * ds, aQ = cf[4] * ds, aV = cf[5] * ds, rQ = cf[6] * ds, rV = cf[7] * ds;
-    R J[4] = {cf[0] * ds, cf[1] * ds, R(0), cf[2] * ds};
+    R jds = js * ds;
+    R J[4] = {cf[0] * jds, cf[1] * jds, R(0), cf[2] * jds};
     R nrm = tau + fabs(aQ) + fabs(aV) + fabs(rQ) + fabs(rV);
     if (!(nrm > R(0.5))) {
-        taylor_step(tau, aQ, aV, rQ, rV, J, S);
+        R acc[4];
+        taylor_inc(tau, aQ, aV, rQ, rV, J, S, acc);
+#pragma unroll
+        for (int i = 0; i < 4; i++) two_sum_add(S[i], Slo[i], acc[i]);
         return;
     }
     R a2 = aQ * aQ + aV * aV, r2 = rQ * rQ + rV * rV, ar = aQ * rQ + aV * rV;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        S[i] += Slo[i];
+        Slo[i] = R(0);
+    }
     if (a2 + r2 == R(0)) {  // isotropic absorption and emission only
         R e = F::exp_(-tau), p = phi1(tau);
 #pragma unroll
@@ -341,7 +374,12 @@ __device__ void substep(const R cf[8], R ds, R S[4]) {
         int m = (int)fmin(ceil(nrm / R(0.5)), R(8192));
         R inv = R(1) / R(m);
         R Js[4] = {J[0] * inv, J[1] * inv, J[2] * inv, J[3] * inv};
-        for (int k = 0; k < m; k++) taylor_step(tau * inv, aQ * inv, aV * inv, rQ * inv, rV * inv, Js, S);
+        for (int k = 0; k < m; k++) {
+            R acc[4];
+            taylor_inc(tau * inv, aQ * inv, aV * inv, rQ * inv, rV * inv, Js, S, acc);
+#pragma unroll
+            for (int i = 0; i < 4; i++) two_sum_add(S[i], Slo[i], acc[i]);
+        }
         return;
     }
     R iD = R(1) / D, P2 = P * P, Q2 = Q * Q;

@@ -36,21 +36,29 @@ __device__ __forceinline__ float to_real<float>(double d) {
     return d2f_int(d);
 }
 
+// o = T v for a 4x4 matrix
 template <typename R>
-__device__ __forceinline__ void heun_transport(R E[4], const R T1[4][4], const R T0[4][4], R h) {
-    R a[4], v[4];
+__device__ __forceinline__ void matvec4(const R T[4][4], const R v[4], R o[4]) {
 #pragma unroll
-    for (int m = 0; m < 4; m++) a[m] = T1[m][0] * E[0] + T1[m][1] * E[1] + T1[m][2] * E[2] + T1[m][3] * E[3];
+    for (int m = 0; m < 4; m++) o[m] = T[m][0] * v[0] + T[m][1] * v[1] + T[m][2] * v[2] + T[m][3] * v[3];
+}
+
+// Heun step of a screen leg held as base + increment, E = eo + u: with a = T(x_{n+1}) E known
+// from the previous point and T0 = T(x_n), v = E + h a and E gains (h/2)(a + T0 v). Only the
+// increment u changes, so E - e (needed by the compensated re-projection) stays exact.
+template <typename R>
+__device__ __forceinline__ void heun_leg(const R eo[4], R u[4], const R a[4], const R T0[4][4], R h) {
+    R v[4];
 #pragma unroll
-    for (int m = 0; m < 4; m++) v[m] = E[m] + h * a[m];
+    for (int m = 0; m < 4; m++) v[m] = (eo[m] + u[m]) + h * a[m];
     R hh = R(0.5) * h;
 #pragma unroll
     for (int m = 0; m < 4; m++)
-        E[m] += hh * (a[m] + T0[m][0] * v[0] + T0[m][1] * v[1] + T0[m][2] * v[2] + T0[m][3] * v[3]);
+        u[m] += hh * (a[m] + T0[m][0] * v[0] + T0[m][1] * v[1] + T0[m][2] * v[2] + T0[m][3] * v[3]);
 }
 
 // Stokes (I, Q, U, V) in the screen (E1, E2) re-expressed on the screen (f1, f2) given as
-// lowered legs: n' = C n C^T, C_{ij} = f_i . E_j.
+// lowered legs: n' = C n C^T, C_{ij} = f_i . E_j. Used once, at the camera.
 template <typename R>
 __device__ __forceinline__ void reproject(const R f1[4], const R f2[4], const R E1[4], const R E2[4], R S[4]) {
     R c11 = f1[0] * E1[0] + f1[1] * E1[1] + f1[2] * E1[2] + f1[3] * E1[3];
@@ -68,6 +76,48 @@ __device__ __forceinline__ void reproject(const R f1[4], const R f2[4], const R 
     S[3] = det * S[3];
 }
 
+// Stokes re-expressed from the transported screen E_k = eo_k + u_k onto the new fluid screen
+// (e1, e2), lowered l1, l2, as a compensated increment. The new coefficients are
+// n' = C n C^T with C = G^{-1} A, A_ik = l_i . E_k and G_ij = l_i . e_j: the dual basis of
+// (e1, e2), so the rounding of their norms does not scale the intensity. Writing
+// E_k = e_k + Delta_k with Delta_k = (eo_k - e_k) + u_k (exact differences of nearby legs plus
+// the transport increment) gives C = 1 + D, D = G^{-1} Lambda, Lambda_ik = l_i . Delta_k, and
+// n' - n = D n + n D^T + D n D^T; V scales by det C = 1 + tr D + det D. The change is small
+// where the screen turns slowly and is added to (S, Slo) without rounding loss.
+template <typename R>
+__device__ __forceinline__ void reproject_comp(const R l1[4], const R l2[4], const R e1[4], const R e2[4],
+                                               const R eo1[4], const R eo2[4], const R u1[4], const R u2[4],
+                                               R S[4], R Slo[4]) {
+    R L11 = 0, L12 = 0, L21 = 0, L22 = 0, g11 = 0, g12 = 0, g21 = 0, g22 = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        R d1 = (eo1[i] - e1[i]) + u1[i];
+        R d2 = (eo2[i] - e2[i]) + u2[i];
+        L11 += l1[i] * d1;
+        L12 += l1[i] * d2;
+        L21 += l2[i] * d1;
+        L22 += l2[i] * d2;
+        g11 += l1[i] * e1[i];
+        g12 += l1[i] * e2[i];
+        g21 += l2[i] * e1[i];
+        g22 += l2[i] * e2[i];
+    }
+    R idet = R(1) / (g11 * g22 - g12 * g21);
+    R d11 = (g22 * L11 - g12 * L21) * idet, d12 = (g22 * L12 - g12 * L22) * idet;
+    R d21 = (g11 * L21 - g21 * L11) * idet, d22 = (g11 * L22 - g21 * L12) * idet;
+    R n11 = R(0.5) * (S[0] + S[1]), n22 = R(0.5) * (S[0] - S[1]), nr = R(0.5) * S[2];
+    R x11 = d11 * n11 + d12 * nr, x12 = d11 * nr + d12 * n22;
+    R x21 = d21 * n11 + d22 * nr, x22 = d21 * nr + d22 * n22;
+    R dn11 = R(2) * x11 + (x11 * d11 + x12 * d12);
+    R dn22 = R(2) * x22 + (x21 * d21 + x22 * d22);
+    R dnr = (x12 + x21) + (x11 * d21 + x12 * d22);
+    R dV = ((d11 + d22) + (d11 * d22 - d12 * d21)) * S[3];
+    two_sum_add(S[0], Slo[0], dn11 + dn22);
+    two_sum_add(S[1], Slo[1], dn11 - dn22);
+    two_sum_add(S[2], Slo[2], R(2) * dnr);
+    two_sum_add(S[3], Slo[3], dV);
+}
+
 template <typename R, typename OutT>
 __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer_kernel(XferArgs p) {
     typedef Mth<R> F;
@@ -83,7 +133,11 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
     long long ray = -1;
     int blk = -1, slot = 0, n = 0, rstat = 0;
     bool live = false, drained = false, basis = false;
-    R S[4], E1[4], E2[4], T1[4][4];
+    // S + Slo: Stokes / nu^3 (invariant) as a value and its compensation; eo + u: screen legs
+    // (base, transport increment); a1, a2: T E of the legs at the previous point; tau, phi:
+    // optical and Faraday depths with their Kahan compensations.
+    R S[4], Slo[4], eo1[4], eo2[4], u1[4], u2[4], a1[4], a2[4];
+    R tau = 0, tauc = 0, phi = 0, phic = 0;
     unsigned long long my_pts = 0, my_emit = 0;
     for (;;) {
         bool want = !live && !drained;
@@ -99,7 +153,8 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
                     n = rec.nstates - 1;
                     basis = false;
 #pragma unroll
-                    for (int i = 0; i < 4; i++) S[i] = R(0);
+                    for (int i = 0; i < 4; i++) S[i] = Slo[i] = R(0);
+                    tau = tauc = phi = phic = R(0);
                     live = true;
                 } else {
                     int ix, iy;
@@ -107,6 +162,10 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
                     long long pix = (long long)iy * c.nx + ix;
                     OutT *o = reinterpret_cast<OutT *>(p.out) + 4 * pix;
                     o[0] = o[1] = o[2] = o[3] = OutT(0);
+                    if (p.depth) {
+                        OutT *d = reinterpret_cast<OutT *>(p.depth) + 2 * pix;
+                        d[0] = d[1] = OutT(0);
+                    }
                     if (p.status) p.status[pix] = (uint8_t)rstat;
                 }
             } else {
@@ -130,61 +189,67 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
         R h = fabs(hs);
         KS<R> m;
         m.eval(a, r, th);
-        if (basis) {
-            if (hs < R(0)) {  // that step crossed the polar axis: bring n+1 into this chart
-                E1[2] = -E1[2];
-                E2[2] = -E2[2];
-#pragma unroll
-                for (int i = 0; i < 4; i++)
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        if ((i == 2) != (j == 2)) T1[i][j] = -T1[i][j];
-            }
-            R T0[4][4];
-            connection_T(m, K, T0);
-            heun_transport(E1, T1, T0, h);
-            heun_transport(E2, T1, T0, h);
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) T1[i][j] = T0[i][j];
+        if (basis && hs < R(0)) {  // that step crossed the polar axis: bring n+1 into this chart
+            eo1[2] = -eo1[2];
+            eo2[2] = -eo2[2];
+            u1[2] = -u1[2];
+            u2[2] = -u2[2];
+            a1[2] = -a1[2];
+            a2[2] = -a2[2];
         }
         Plasma<R> pl;
         if (p.model.kind == 1)
             adaf_plasma(p.model.adaf, a, m, r, pl);
         else
             grid_plasma(p.model.grid, m, r, th, ph, pl);
+        R e1[4], e2[4], w, sth, cth;
+        if (pl.valid) fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
+        if (basis || pl.valid) {
+            // transport the legs from n+1 to n, then T E at n for the next step
+            R T0[4][4];
+            connection_T(m, K, T0);
+            if (basis) {
+                heun_leg(eo1, u1, a1, T0, h);
+                heun_leg(eo2, u2, a2, T0, h);
+            }
+            R E1[4], E2[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                E1[i] = pl.valid ? e1[i] : eo1[i] + u1[i];
+                E2[i] = pl.valid ? e2[i] : eo2[i] + u2[i];
+            }
+            matvec4(T0, E1, a1);
+            matvec4(T0, E2, a2);
+        }
         if (pl.valid) {
-            R e1[4], e2[4], w, sth, cth;
-            fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
             if (basis) {
                 R l1[4], l2[4];
                 m.lower(e1, l1);
                 m.lower(e2, l2);
-                reproject(l1, l2, E1, E2, S);
+                reproject_comp(l1, l2, e1, e2, eo1, eo2, u1, u2, S, Slo);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                eo1[i] = e1[i];
+                eo2[i] = e2[i];
+                u1[i] = u2[i] = R(0);
             }
             R cf[8];
             thermal_coeffs(pl.ne, pl.Te, pl.B, w * nu_obs, sth, cth, sgw, cf);
-            R w3 = w * w * w, iw3 = R(1) / w3;
-#pragma unroll
-            for (int i = 0; i < 4; i++) S[i] *= w3;
-            substep(cf, w * h * L, S);
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                S[i] *= iw3;
-                E1[i] = e1[i];
-                E2[i] = e2[i];
-            }
-            if (!basis) {
-                connection_T(m, K, T1);
-                basis = true;
-            }
+            // invariant form: S holds I/nu^3, so the step takes J/w^3 and the same M
+            R ds = w * h * L;
+            substep(cf, ds, R(1) / (w * w * w), S, Slo);
+            kahan_add(tau, tauc, cf[3] * ds);
+            kahan_add(phi, phic, cf[7] * ds);
+            basis = true;
             my_emit++;
         }
         my_pts++;
         if (n == 0) {
             int ix, iy;
             ray_pixel(ray + p.ray_offset, c.nx, c.ny, ix, iy);
+#pragma unroll
+            for (int i = 0; i < 4; i++) S[i] += Slo[i];
             if (basis) {
                 // camera screen: x along e_phi, y along -e_theta, each normal to the ray
                 double e[4][4], s[3];
@@ -205,9 +270,14 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
                     X[mu] = R(xh[0] * e[1][mu] + xh[1] * e[2][mu] + xh[2] * e[3][mu]);
                     Y[mu] = R(ny * (yh[0] * e[1][mu] + yh[1] * e[2][mu] + yh[2] * e[3][mu]));
                 }
-                R lx[4], ly[4];
+                R lx[4], ly[4], E1[4], E2[4];
                 m.lower(X, lx);
                 m.lower(Y, ly);
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    E1[i] = eo1[i] + u1[i];
+                    E2[i] = eo2[i] + u2[i];
+                }
                 reproject(lx, ly, E1, E2, S);
             }
             long long pix = (long long)iy * c.nx + ix;
@@ -216,6 +286,11 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
             o[1] = OutT(S[1]);
             o[2] = OutT(S[2]);
             o[3] = OutT(S[3]);
+            if (p.depth) {
+                OutT *d = reinterpret_cast<OutT *>(p.depth) + 2 * pix;
+                d[0] = OutT(tau - tauc);
+                d[1] = OutT(phi - phic);
+            }
             if (p.status) p.status[pix] = (uint8_t)rstat;
             live = false;
         }

@@ -75,6 +75,7 @@ def lib():
                                      C.POINTER(C.c_double)]
         L.rt_last_counters.argtypes = [_VP, C.POINTER(rt_counters)]
         L.rt_render_static.argtypes = [_VP, C.c_int, _VP, _VP]
+        L.rt_render_depths.argtypes = [_VP, C.c_int, _VP, _VP, _VP]
         L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
         L.rt_error_string.restype = C.c_char_p
@@ -180,6 +181,14 @@ def rt_render(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
     rc = lib().rt_render(ctx, form, _ptr(out_iquv), _ptr(status))
     if check:
         _check(rc, "rt_render")
+    return rc
+
+
+def rt_render_depths(ctx, form: int, out_iquv, out_depth, status=None, check: bool = True) -> int:
+    """rt_render plus the per-pixel optical and Faraday depths [ny][nx][2]."""
+    rc = lib().rt_render_depths(ctx, form, _ptr(out_iquv), _ptr(status), _ptr(out_depth))
+    if check:
+        _check(rc, "rt_render_depths")
     return rc
 
 
