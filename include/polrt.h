@@ -39,7 +39,8 @@ enum {
     RT_ERR_NOMEM = -3,      /* an allocation failed */
     RT_ERR_NOT_READY = -4,  /* no model or no camera set */
     RT_ERR_WORKSPACE = -5,  /* the path arena ran out; rays carry RT_RAY_OVERFLOW */
-    RT_ERR_SIZE = -6        /* a size beyond a fixed limit of the call */
+    RT_ERR_SIZE = -6,       /* a size beyond a fixed limit of the call */
+    RT_ERR_STALL = -7       /* a bounded wait inside a batched launch ran out; results invalid */
 };
 
 enum { RT_MODEL_ADAF = 1, RT_MODEL_GRID = 2 };
@@ -112,7 +113,8 @@ typedef struct {
     uint64_t rays, steps, points, emitting_points;
     uint64_t arena_blocks_used, arena_blocks_total;
     uint32_t n_horizon, n_escape, n_nmax, n_nan, n_overflow;
-    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events) */
+    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events); 0 after a batch */
+    float ms_total;                 /* device time of the whole render or batch */
 } rt_counters;
 
 /* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t, or
@@ -170,6 +172,49 @@ int rt_image_stats(rt_ctx *ctx, const void *iquv, int form, double *flux_jy, dou
 int rt_last_counters(rt_ctx *ctx, rt_counters *out);
 
 const char *rt_error_string(int code);
+
+/* ---- Batched rendering (image libraries, MCMC fitting) -------------------------------------
+ * Many images of different cameras and model parameters in one persistent launch, replayed
+ * from a CUDA graph. All images share the loaded model (the GRMHD grid or the ADAF). A grid
+ * image may override the mass unit and R_high. */
+typedef struct {
+    rt_camera cam;     /* resolution, inclination, frequency, ... of this image */
+    double M_unit;     /* grid models: this image's mass unit [g]; <= 0 keeps the loaded value */
+    double R_high;     /* grid models: this image's R_high; <= 0 keeps the loaded value */
+    void *out_iquv;    /* device buffer, nx*ny*4 values of the form's type, layout as rt_render */
+    uint8_t *status;   /* optional device nx*ny codes, or NULL */
+    void *out_depth;   /* optional device nx*ny*2 depths (see rt_render_depths), or NULL */
+} rt_job;
+
+/* Launch shape of the batched kernel. Each block has 8 warps: geo_warps of them integrate
+ * geodesics and the rest run the transfer. step_tile is the number of RK4 steps a lane takes
+ * between its queue and pool checks. blocks_per_sm is the number of resident blocks per SM
+ * (the grid is that times the SM count). ms is the time the autotuner measured for this shape
+ * (0 when set by hand). */
+typedef struct {
+    int geo_warps;      /* 1..7 */
+    int step_tile;      /* 1..16 */
+    int blocks_per_sm;  /* 1..(the kernel's occupancy limit) */
+    float ms;
+} rt_batch_config;
+
+/* Render njobs images in one persistent launch. Rays of all images share one work queue. Path
+ * blocks come from a bounded pool that the transfer frees as it walks, so memory does not grow
+ * with the batch. The launch (with its set-up) is captured once into a CUDA graph and replayed
+ * while the form, the image count and the total ray count stay the same. The first call for a
+ * form runs the autotuner (rt_batch_autotune) on this batch unless a shape was set by hand, and
+ * so does a call whose batch has over 4x more or 4x fewer rays than the tuned one. Results
+ * equal rt_render's for each image. Synchronizes; RT_ERR_WORKSPACE if a ray had to be given
+ * up for lack of pool blocks (its pixel is zero, status RT_RAY_OVERFLOW); RT_ERR_STALL if a
+ * bounded wait ran out. At most 2^31 - 1 rays in total. */
+int rt_render_batch(rt_ctx *ctx, int form, const rt_job *jobs, int njobs);
+
+/* Time the candidate launch shapes on a calibration batch (the leading images of `jobs`,
+ * about 2^20 rays, rendered into their own buffers). Keep the fastest for `form`; return it in
+ * *best (may be NULL). Synchronizes. */
+int rt_batch_autotune(rt_ctx *ctx, int form, const rt_job *jobs, int njobs, rt_batch_config *best);
+int rt_set_batch_config(rt_ctx *ctx, int form, const rt_batch_config *cfg);
+int rt_get_batch_config(rt_ctx *ctx, int form, rt_batch_config *cfg);
 
 /* rt_render without any device allocation, for callers that cannot allocate (their device
  * memory is budgeted by someone else, or allocation is forbidden on their code path). The

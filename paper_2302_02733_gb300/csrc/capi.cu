@@ -6,8 +6,8 @@
 #include <cstring>
 #include <new>
 
+#include "host_util.cuh"
 #include "polrt.h"
-#include "rt_ctx.cuh"
 
 using namespace prt;
 
@@ -18,21 +18,6 @@ constexpr int kBudgetBlocksPerRay = 20;  // 640 saved states per ray on average 
 constexpr size_t kPerRayBytes = sizeof(RayRecord) + kBudgetBlocksPerRay * kBlockBytes;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-bool is_device_ptr(const void *p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-double r_isco(double a) {
-    double z1 = 1.0 + std::cbrt(1.0 - a * a) * (std::cbrt(1.0 + a) + std::cbrt(1.0 - a));
-    double z2 = std::sqrt(3.0 * a * a + z1 * z1);
-    return 3.0 + z2 - std::sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
-}
 }  // namespace
 
 
@@ -55,6 +40,7 @@ const char *rt_error_string(int code) {
         case RT_ERR_NOT_READY: return "model or camera not set";
         case RT_ERR_WORKSPACE: return "path arena overflow: enlarge the workspace";
         case RT_ERR_SIZE: return "size beyond the call's fixed limit";
+        case RT_ERR_STALL: return "a bounded wait in the batched kernel ran out";
         default: return "unknown error";
     }
 }
@@ -81,10 +67,14 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     c->geo_bps = geodesic_blocks_per_sm();
     c->fp64_bps = transfer_blocks_per_sm_fp64();
     c->mixed_bps = transfer_blocks_per_sm_mixed();
+    c->pipe_bps[0] = pipe_blocks_per_sm_fp64();
+    c->pipe_bps[1] = pipe_blocks_per_sm_mixed();
     bool ok = cudaMalloc(&c->d_stats, 8 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->d_sctab, kSinTabBytes) == cudaSuccess &&
-              cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess;
+              cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking) == cudaSuccess;
     for (int i = 0; i < 3 && ok; i++) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; i++) ok = cudaEventCreate(&c->bev[i]) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         rt_destroy(c);
@@ -116,6 +106,7 @@ int rt_destroy(rt_ctx *c) {
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     for (int i = 0; i < 3; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    free_batch(c);
     cudaGetLastError();
     delete c;
     return RT_OK;
@@ -136,12 +127,8 @@ int rt_set_integrator(rt_ctx *c, double eps, int nmax) {
 
 int rt_set_camera(rt_ctx *c, const rt_camera *cam) {
     if (!c || !cam) return RT_ERR_INVALID;
-    if (!(std::fabs(cam->a) < 1.0) || !(cam->incl_deg > 0.0 && cam->incl_deg < 180.0) || cam->nx < 1 ||
-        cam->ny < 1 || !(cam->freq_hz > 0.0) || !(cam->fov_M > 0.0) || !(cam->M_bh_g > 0.0) || !(cam->dist_cm > 0.0))
-        return RT_ERR_INVALID;
-    double rh = 1.0 + std::sqrt(1.0 - cam->a * cam->a);
-    if (!(cam->r_cam > 2.0 * rh)) return RT_ERR_INVALID;
-    if ((long long)cam->nx * cam->ny > (1ll << 31)) return RT_ERR_SIZE;
+    int rv = check_camera(*cam);
+    if (rv) return rv;
     c->cam = *cam;
     c->have_cam = true;
     return RT_OK;
@@ -265,51 +252,8 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     if (rv) return rv;
 
     // camera and model in kernel form
-    Camera cam{};
-    cam.a = rc.a;
-    cam.r_cam = rc.r_cam;
-    cam.theta_o = rc.incl_deg * kPi / 180.0;
-    cam.nu_obs = rc.freq_hz;
-    cam.fov = rc.fov_M;
-    cam.L_unit = kG * rc.M_bh_g / (kC * kC);
-    cam.nx = rc.nx;
-    cam.ny = rc.ny;
-    cam.eps = c->eps;
-    cam.nmax = c->nmax;
-    cam.rh = 1.0 + std::sqrt(1.0 - rc.a * rc.a);
-    Model mod{};
-    mod.kind = c->model.kind;
-    if (mod.kind == RT_MODEL_ADAF) {
-        const rt_adaf_params &a = c->model.adaf;
-        mod.adaf = AdafModel{a.n0, a.T0, a.beta, a.f_kep, a.Ti_over_Te, a.r_out, r_isco(rc.a)};
-    } else {
-        const rt_grid_params &g = c->model.grid;
-        GridModel &gm = mod.grid;
-        gm.n1 = g.n1;
-        gm.n2 = g.n2;
-        gm.n3 = g.n3;
-        gm.r_in = g.r_in;
-        gm.r_out = g.r_out;
-        gm.x1in = std::log(g.r_in);
-        gm.dx1 = (std::log(g.r_out) - gm.x1in) / g.n1;
-        gm.dx2 = 1.0 / g.n2;
-        gm.dx3 = 2.0 * kPi / g.n3;
-        gm.hslope = g.hslope;
-        gm.poly_xt = g.poly_xt;
-        gm.poly_alpha = g.poly_alpha;
-        gm.mks_smooth = g.mks_smooth;
-        gm.poly_norm = 0.5 * kPi / (1.0 + 1.0 / ((g.poly_alpha + 1.0) * std::pow(g.poly_xt, g.poly_alpha)));
-        gm.prims = reinterpret_cast<const float4 *>(c->d_prims);
-        gm.x2_table = c->d_x2;
-        double L = cam.L_unit;
-        gm.rho_unit = g.M_unit / (L * L * L);
-        gm.b_unit = kC * std::sqrt(4.0 * kPi * gm.rho_unit);
-        gm.ne_unit = gm.rho_unit / (kMp + kMe);
-        gm.R_high = g.R_high;
-        gm.R_low = g.R_low;
-        gm.sigma_cut = g.sigma_cut;
-        gm.gamma_ad = g.gamma_ad;
-    }
+    Camera cam = make_camera(rc, c->eps, c->nmax);
+    Model mod = make_model(c, cam);
 
     // workspace carving
     char *base = (char *)c->ws;
@@ -377,6 +321,7 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     CK(cudaStreamSynchronize(c->stream));
     c->last_rays = nrays;
     c->last_blocks_total = nblocks;
+    c->last_was_batch = false;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     return RT_OK;
 }
@@ -434,8 +379,13 @@ int rt_last_counters(rt_ctx *c, rt_counters *out) {
     out->n_nan = k.n_status[kNan];
     out->n_overflow = k.n_status[kOverflow];
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out->ms_geodesic = ms;
-    if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) out->ms_transfer = ms;
+    if (c->last_was_batch) {
+        out->ms_total = c->last_ms_total;
+    } else {
+        if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out->ms_geodesic = ms;
+        if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) out->ms_transfer = ms;
+        if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]) == cudaSuccess) out->ms_total = ms;
+    }
     cudaGetLastError();
     return RT_OK;
 }

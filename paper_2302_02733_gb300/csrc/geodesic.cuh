@@ -1,0 +1,95 @@
+// Geodesic building blocks shared by the per-image and the batched kernels: the initial
+// state of a pixel's ray, the radius-scaled step size, one classic RK4 step with polar
+// reflection, and the stop tests (the paper's Section 2.1).
+#pragma once
+#include "camera.cuh"
+#include "rt_kernels.cuh"
+
+namespace prt {
+
+// h = eps / (|K^r|/r + |K^th|/tt + |K^ph| + 1e-40), tt = max(min(th, pi - th), 0.01), taken
+// with one division: h = eps r tt / (|K^r| tt + |K^th| r + (|K^ph| + 1e-40) r tt).
+__device__ __forceinline__ double step_size(double eps, const double y[7]) {
+    double tt = fmax(fmin(y[1], kPi - y[1]), 1e-2);
+    double rt = y[0] * tt;
+    double den = fma(fabs(y[6]) + 1e-40, rt, fma(fabs(y[4]), tt, fabs(y[5]) * y[0]));
+    return eps * rt / den;
+}
+
+// y = (r, theta, phi, K^t, K^r, K^theta, K^phi); t is never needed (stationary metric).
+__device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double a, double h, const double y[7],
+                                         double out[7]) {
+    double k1[7], k2[7], k3[7], k4[7], t[7];
+    auto rhs = [&](const double *z, double *dz) {
+        dz[0] = z[4];
+        dz[1] = z[5];
+        dz[2] = z[6];
+        double acc[4];
+        geo_accel(tab, a, z[0], z[1], z + 3, acc);
+        dz[3] = acc[0];
+        dz[4] = acc[1];
+        dz[5] = acc[2];
+        dz[6] = acc[3];
+    };
+    const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
+    rhs(y, k1);
+#pragma unroll
+    for (int i = 0; i < 7; i++) t[i] = fma(h2, k1[i], y[i]);
+    rhs(t, k2);
+#pragma unroll
+    for (int i = 0; i < 7; i++) t[i] = fma(h2, k2[i], y[i]);
+    rhs(t, k3);
+#pragma unroll
+    for (int i = 0; i < 7; i++) t[i] = fma(h, k3[i], y[i]);
+    rhs(t, k4);
+#pragma unroll
+    for (int i = 0; i < 7; i++) out[i] = fma(h6, k4[i], fma(h3, k3[i], fma(h3, k2[i], fma(h6, k1[i], y[i]))));
+}
+
+// Initial state of the backward ray through pixel (ix, iy): the camera tetrad's past-directed
+// null vector K = -e_0 + s^i e_i at (r_cam, theta_o, 0).
+__device__ __forceinline__ void ray_start(const Camera &c, int ix, int iy, double y[7]) {
+    double e[4][4], s[3];
+    camera_tetrad(c.a, c.r_cam, c.theta_o, e);
+    sky_direction(c, ix, iy, s);
+    y[0] = c.r_cam;
+    y[1] = c.theta_o;
+    y[2] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) y[3 + k] = -e[0][k] + s[0] * e[1][k] + s[1] * e[2][k] + s[2] * e[3][k];
+}
+
+// One step from y: yn, the step h, and whether it crossed the polar axis (then theta is
+// reflected, phi advanced by pi and K^theta reversed).
+__device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const Camera &c, const double y[7],
+                                         double yn[7], double &h) {
+    h = step_size(c.eps, y);
+    rk4_step(tab, c.a, h, y, yn);
+    bool refl = false;
+    if (yn[1] < 0.0) {
+        yn[1] = -yn[1];
+        yn[2] += kPi;
+        yn[5] = -yn[5];
+        refl = true;
+    } else if (yn[1] > kPi) {
+        yn[1] = 2.0 * kPi - yn[1];
+        yn[2] += kPi;
+        yn[5] = -yn[5];
+        refl = true;
+    }
+    return refl;
+}
+
+// Stop test after n steps, in order: non-finite, horizon, escape, step limit; 0 to go on.
+__device__ __forceinline__ uint8_t geo_stop(const Camera &c, const double y[7], int n) {
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 7; k++) bad |= !isfinite(y[k]);
+    if (bad) return kNan;
+    if (y[0] < 1.05 * c.rh) return kHorizon;
+    if (y[0] > c.r_cam && y[4] > 0.0) return kEscape;
+    if (n >= c.nmax) return kNmax;
+    return 0;
+}
+
+}  // namespace prt

@@ -12,7 +12,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "rt_ctx.cuh"
+#include "host_util.cuh"
 
 using namespace prt;
 
@@ -29,21 +29,6 @@ constexpr int kMaxDevices = 64;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 size_t up(size_t x) { return (x + kStaticAlign - 1) / kStaticAlign * kStaticAlign; }
-
-bool on_device(const void *p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-double isco(double a) {
-    double z1 = 1.0 + std::cbrt(1.0 - a * a) * (std::cbrt(1.0 + a) + std::cbrt(1.0 - a));
-    double z2 = std::sqrt(3.0 * a * a + z1 * z1);
-    return 3.0 + z2 - std::sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
-}
 
 }  // namespace
 
@@ -62,7 +47,7 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     const rt_camera &rc = c->cam;
     long long nrays = (long long)rc.nx * rc.ny;
     if (nrays > rt_render_static_max_pixels()) return RT_ERR_SIZE;
-    if (!on_device(out_iquv) || (status && !on_device(status))) return RT_ERR_INVALID;
+    if (!is_device_ptr(out_iquv) || (status && !is_device_ptr(status))) return RT_ERR_INVALID;
     if (cudaSetDevice(c->device) != cudaSuccess) {
         cudaGetLastError();
         return RT_ERR_CUDA;
@@ -78,51 +63,8 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     }
     char *base = (char *)g_scratch_ptr[c->device];
 
-    Camera cam{};
-    cam.a = rc.a;
-    cam.r_cam = rc.r_cam;
-    cam.theta_o = rc.incl_deg * kPi / 180.0;
-    cam.nu_obs = rc.freq_hz;
-    cam.fov = rc.fov_M;
-    cam.L_unit = kG * rc.M_bh_g / (kC * kC);
-    cam.nx = rc.nx;
-    cam.ny = rc.ny;
-    cam.eps = c->eps;
-    cam.nmax = c->nmax;
-    cam.rh = 1.0 + std::sqrt(1.0 - rc.a * rc.a);
-    Model mod{};
-    mod.kind = c->model.kind;
-    if (mod.kind == RT_MODEL_ADAF) {
-        const rt_adaf_params &a = c->model.adaf;
-        mod.adaf = AdafModel{a.n0, a.T0, a.beta, a.f_kep, a.Ti_over_Te, a.r_out, isco(rc.a)};
-    } else {
-        const rt_grid_params &g = c->model.grid;
-        GridModel &gm = mod.grid;
-        gm.n1 = g.n1;
-        gm.n2 = g.n2;
-        gm.n3 = g.n3;
-        gm.r_in = g.r_in;
-        gm.r_out = g.r_out;
-        gm.x1in = std::log(g.r_in);
-        gm.dx1 = (std::log(g.r_out) - gm.x1in) / g.n1;
-        gm.dx2 = 1.0 / g.n2;
-        gm.dx3 = 2.0 * kPi / g.n3;
-        gm.hslope = g.hslope;
-        gm.poly_xt = g.poly_xt;
-        gm.poly_alpha = g.poly_alpha;
-        gm.mks_smooth = g.mks_smooth;
-        gm.poly_norm = 0.5 * kPi / (1.0 + 1.0 / ((g.poly_alpha + 1.0) * std::pow(g.poly_xt, g.poly_alpha)));
-        gm.prims = reinterpret_cast<const float4 *>(c->d_prims);
-        gm.x2_table = c->d_x2;
-        double L = cam.L_unit;
-        gm.rho_unit = g.M_unit / (L * L * L);
-        gm.b_unit = kC * std::sqrt(4.0 * kPi * gm.rho_unit);
-        gm.ne_unit = gm.rho_unit / (kMp + kMe);
-        gm.R_high = g.R_high;
-        gm.R_low = g.R_low;
-        gm.sigma_cut = g.sigma_cut;
-        gm.gamma_ad = g.gamma_ad;
-    }
+    Camera cam = make_camera(rc, c->eps, c->nmax);
+    Model mod = make_model(c, cam);
 
     // carve the static scratch: counters | ray records | arena states | arena links
     Counters *ctr = (Counters *)base;
@@ -158,6 +100,7 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     }
     c->last_rays = nrays;
     c->last_blocks_total = nblocks;
+    c->last_was_batch = false;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     return RT_OK;
 }

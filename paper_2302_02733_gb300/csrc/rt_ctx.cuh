@@ -3,6 +3,8 @@
 #include "polrt.h"
 #include "rt_kernels.cuh"
 
+using prt::RayRecord;
+
 struct rt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -31,4 +33,22 @@ struct rt_ctx {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     long long last_rays = 0, last_blocks_total = 0;
     int geo_bps = 1, fp64_bps = 1, mixed_bps = 1;
+    float last_ms_total = 0.f;
+    bool last_was_batch = false;
+
+    // batched form (rt_render_batch)
+    cudaStream_t bstream = nullptr;       // private stream: graph capture needs a non-legacy stream
+    cudaEvent_t bev[3] = {nullptr, nullptr, nullptr};
+    prt::JobDev *d_jobs = nullptr, *h_jobs = nullptr;  // device table and its pinned staging copy
+    int jobs_cap = 0;
+    RayRecord *d_brec = nullptr;
+    int *d_ready = nullptr;
+    long long brays_cap = 0;
+    prt::Pool pool{};
+    prt::PipeCounters *d_pctr = nullptr, *h_pctr = nullptr;
+    int pipe_bps[2] = {1, 1};             // resident blocks per SM of the fp64 / mixed pipe kernel
+    rt_batch_config bcfg[2] = {};         // per form; geo_warps == 0 means not tuned yet
+    long long bcal_rays[2] = {0, 0};      // rays of the batch the shape was tuned on (0: set by hand)
+    cudaGraphExec_t gexec = nullptr;      // the captured batch of the last call
+    long long gkey[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };

@@ -29,6 +29,59 @@ struct XferArgs {
     void *depth;          // optional [ny][nx][2] optical and Faraday depths, same type as out
 };
 
+// ---- batched rendering: many images in one persistent launch ----------------------------
+// One image of a batch in kernel form. Rays of the batch are numbered image after image.
+struct JobDev {
+    Camera cam;
+    Model model;
+    long long ray_begin;  // global id of the image's first ray
+    void *out;            // [ny][nx][4] of the form's type
+    uint8_t *status;      // optional [ny][nx]
+    void *depth;          // optional [ny][nx][2]
+};
+
+// A bounded pool of path blocks with a free ring, so the memory of a batch does not grow
+// with its ray count: blocks return to the ring as the transfer walks past them.
+struct Pool {
+    PathState *states;  // nblocks * kBlockStates
+    int *prev;          // previous block of the same ray, -1 for the first
+    int *fill;          // states the block holds once closed
+    int *ring;          // free-block ring of nblocks slots, -1 marks an empty slot
+    int nblocks;
+};
+
+struct PipeCounters {
+    unsigned long long geo_next, xfer_next, ready_tail;  // work queues
+    unsigned long long pool_head, pool_tail;             // free-ring ticket and return positions
+    unsigned long long steps, points, emitting;
+    unsigned int n_status[8];
+    unsigned int err;                                    // kPipeErr* bits
+    unsigned int pad1;
+};
+constexpr unsigned kPipeErrRing = 1u;   // a free-ring slot never changed
+constexpr unsigned kPipeErrReady = 2u;  // a transfer lane never received its ray
+
+constexpr int kPipeThreads = 256;  // 8 warps: geo_warps integrate geodesics, the rest transfer
+
+struct PipeArgs {
+    const JobDev *jobs;
+    int njobs;
+    const double *sctab;
+    Pool pool;
+    RayRecord *rec;     // per ray of the batch; pad holds the last block's fill
+    int *ready;         // completed rays in completion order, -1 until written
+    PipeCounters *ctr;
+    long long nrays;
+    int geo_warps;      // 1..7
+    int step_tile;      // RK4 steps per lane between queue and pool checks
+};
+
+void launch_pool_init(const Pool &p, PipeCounters *c, cudaStream_t s);
+void launch_pipe_fp64(const PipeArgs &a, int grid, cudaStream_t s);
+void launch_pipe_mixed(const PipeArgs &a, int grid, cudaStream_t s);
+int pipe_blocks_per_sm_fp64();
+int pipe_blocks_per_sm_mixed();
+
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
 void launch_sincos_table(double *tab, cudaStream_t s);
 constexpr size_t kSinTabBytes = 2048 * 3 * sizeof(double);

@@ -118,26 +118,173 @@ __device__ __forceinline__ void reproject_comp(const R l1[4], const R l2[4], con
     two_sum_add(S[3], Slo[3], dV);
 }
 
+// Per-lane transfer state of one ray. S + Slo: Stokes / nu^3 (invariant) as a value and its
+// compensation; eo + u: screen legs (base, transport increment); a1, a2: T E of the legs at the
+// previous point; tau, phi: optical and Faraday depths with their Kahan compensations.
+template <typename R>
+struct XLane {
+    R S[4], Slo[4], eo1[4], eo2[4], u1[4], u2[4], a1[4], a2[4];
+    R tau, tauc, phi, phic;
+    bool basis;
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int i = 0; i < 4; i++) S[i] = Slo[i] = R(0);
+        tau = tauc = phi = phic = R(0);
+        basis = false;
+    }
+};
+
+// One saved state (q0, q1) of the walk toward the camera: transport the screen legs to it,
+// evaluate the plasma, and where it emits, re-project onto the fluid screen and take the
+// exact constant-coefficient step. m returns the metric at the state. Returns whether the
+// point emits.
+template <typename R>
+__device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, const double4_32a &q0,
+                                           const double4_32a &q1, const R *sgw, XLane<R> &Ln, KS<R> &m) {
+    const R a = R(c.a);
+    R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
+    R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
+    R hs = to_real<R>(q1.w);
+    R h = fabs(hs);
+    m.eval(a, r, th);
+    if (Ln.basis && hs < R(0)) {  // that step crossed the polar axis: bring n+1 into this chart
+        Ln.eo1[2] = -Ln.eo1[2];
+        Ln.eo2[2] = -Ln.eo2[2];
+        Ln.u1[2] = -Ln.u1[2];
+        Ln.u2[2] = -Ln.u2[2];
+        Ln.a1[2] = -Ln.a1[2];
+        Ln.a2[2] = -Ln.a2[2];
+    }
+    Plasma<R> pl;
+    if (mdl.kind == 1)
+        adaf_plasma(mdl.adaf, a, m, r, pl);
+    else
+        grid_plasma(mdl.grid, m, r, th, ph, pl);
+    R e1[4], e2[4], w, sth, cth;
+    if (pl.valid) fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
+    if (Ln.basis || pl.valid) {
+        // transport the legs from n+1 to n, then T E at n for the next step
+        R T0[4][4];
+        connection_T(m, K, T0);
+        if (Ln.basis) {
+            heun_leg(Ln.eo1, Ln.u1, Ln.a1, T0, h);
+            heun_leg(Ln.eo2, Ln.u2, Ln.a2, T0, h);
+        }
+        R E1[4], E2[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            E1[i] = pl.valid ? e1[i] : Ln.eo1[i] + Ln.u1[i];
+            E2[i] = pl.valid ? e2[i] : Ln.eo2[i] + Ln.u2[i];
+        }
+        matvec4(T0, E1, Ln.a1);
+        matvec4(T0, E2, Ln.a2);
+    }
+    if (pl.valid) {
+        if (Ln.basis) {
+            R l1[4], l2[4];
+            m.lower(e1, l1);
+            m.lower(e2, l2);
+            reproject_comp(l1, l2, e1, e2, Ln.eo1, Ln.eo2, Ln.u1, Ln.u2, Ln.S, Ln.Slo);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            Ln.eo1[i] = e1[i];
+            Ln.eo2[i] = e2[i];
+            Ln.u1[i] = Ln.u2[i] = R(0);
+        }
+        R cf[8];
+        thermal_coeffs(pl.ne, pl.Te, pl.B, w * R(c.nu_obs), sth, cth, sgw, cf);
+        // invariant form: S holds I/nu^3, so the step takes J/w^3 and the same M
+        R ds = w * h * R(c.L_unit);
+        substep(cf, ds, R(1) / (w * w * w), Ln.S, Ln.Slo);
+        kahan_add(Ln.tau, Ln.tauc, cf[3] * ds);
+        kahan_add(Ln.phi, Ln.phic, cf[7] * ds);
+        Ln.basis = true;
+    }
+    return pl.valid;
+}
+
+// At the camera (the last state, metric m): project onto the image basis and write pixel
+// (ix, iy) of out (and of depth, if given).
 template <typename R, typename OutT>
-__global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer_kernel(XferArgs p) {
+__device__ __forceinline__ void xfer_finish(const Camera &c, const KS<R> &m, int ix, int iy, XLane<R> &Ln,
+                                            void *out, void *depth) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) Ln.S[i] += Ln.Slo[i];
+    if (Ln.basis) {
+        // camera screen: x along e_phi, y along -e_theta, each normal to the ray
+        double e[4][4], s[3];
+        camera_tetrad(c.a, c.r_cam, c.theta_o, e);
+        sky_direction(c, ix, iy, s);
+        double xh[3] = {-s[2] * s[0], -s[2] * s[1], 1.0 - s[2] * s[2]};
+        double nx = rsqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
+        double yh[3] = {s[1] * s[0], -1.0 + s[1] * s[1], s[1] * s[2]};
+        double yx = yh[0] * xh[0] * nx + yh[1] * xh[1] * nx + yh[2] * xh[2] * nx;
+        R X[4], Y[4];
+        for (int k = 0; k < 3; k++) {
+            xh[k] *= nx;
+            yh[k] -= yx * xh[k];
+        }
+        double ny = rsqrt(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            X[mu] = R(xh[0] * e[1][mu] + xh[1] * e[2][mu] + xh[2] * e[3][mu]);
+            Y[mu] = R(ny * (yh[0] * e[1][mu] + yh[1] * e[2][mu] + yh[2] * e[3][mu]));
+        }
+        R lx[4], ly[4], E1[4], E2[4];
+        m.lower(X, lx);
+        m.lower(Y, ly);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            E1[i] = Ln.eo1[i] + Ln.u1[i];
+            E2[i] = Ln.eo2[i] + Ln.u2[i];
+        }
+        reproject(lx, ly, E1, E2, Ln.S);
+    }
+    long long pix = (long long)iy * c.nx + ix;
+    OutT *o = reinterpret_cast<OutT *>(out) + 4 * pix;
+    o[0] = OutT(Ln.S[0]);
+    o[1] = OutT(Ln.S[1]);
+    o[2] = OutT(Ln.S[2]);
+    o[3] = OutT(Ln.S[3]);
+    if (depth) {
+        OutT *d = reinterpret_cast<OutT *>(depth) + 2 * pix;
+        d[0] = OutT(Ln.tau - Ln.tauc);
+        d[1] = OutT(Ln.phi - Ln.phic);
+    }
+}
+
+// A pixel whose ray has no usable path: zero Stokes (and depths).
+template <typename OutT>
+__device__ __forceinline__ void xfer_zero(long long pix, void *out, void *depth) {
+    OutT *o = reinterpret_cast<OutT *>(out) + 4 * pix;
+    o[0] = o[1] = o[2] = o[3] = OutT(0);
+    if (depth) {
+        OutT *d = reinterpret_cast<OutT *>(depth) + 2 * pix;
+        d[0] = d[1] = OutT(0);
+    }
+}
+
+// Bessel-quadrature weights exp(-(k h)^2) (halved at k = 0) into shared memory.
+template <typename R>
+__device__ __forceinline__ void fill_bessel_weights(R *sgw) {
     typedef Mth<R> F;
-    __shared__ R sgw[32];
     if (threadIdx.x < BesselCfg<R>::nq) {
         R u = R(threadIdx.x) * BesselCfg<R>::h;
         sgw[threadIdx.x] = F::exp_(-u * u) * (threadIdx.x == 0 ? R(0.5) : R(1));
     }
+}
+
+template <typename R, typename OutT>
+__global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer_kernel(XferArgs p) {
+    __shared__ R sgw[32];
+    fill_bessel_weights(sgw);
     __syncthreads();
     const Camera &c = p.cam;
-    const R a = R(c.a);
-    const R nu_obs = R(c.nu_obs), L = R(c.L_unit);
     long long ray = -1;
     int blk = -1, slot = 0, n = 0, rstat = 0;
-    bool live = false, drained = false, basis = false;
-    // S + Slo: Stokes / nu^3 (invariant) as a value and its compensation; eo + u: screen legs
-    // (base, transport increment); a1, a2: T E of the legs at the previous point; tau, phi:
-    // optical and Faraday depths with their Kahan compensations.
-    R S[4], Slo[4], eo1[4], eo2[4], u1[4], u2[4], a1[4], a2[4];
-    R tau = 0, tauc = 0, phi = 0, phic = 0;
+    bool live = false, drained = false;
+    XLane<R> Ln;
     unsigned long long my_pts = 0, my_emit = 0;
     for (;;) {
         bool want = !live && !drained;
@@ -151,21 +298,13 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
                     blk = rec.last_block;
                     slot = (rec.nstates - 1) % kBlockStates;
                     n = rec.nstates - 1;
-                    basis = false;
-#pragma unroll
-                    for (int i = 0; i < 4; i++) S[i] = Slo[i] = R(0);
-                    tau = tauc = phi = phic = R(0);
+                    Ln.reset();
                     live = true;
                 } else {
                     int ix, iy;
                     ray_pixel(ray + p.ray_offset, c.nx, c.ny, ix, iy);
                     long long pix = (long long)iy * c.nx + ix;
-                    OutT *o = reinterpret_cast<OutT *>(p.out) + 4 * pix;
-                    o[0] = o[1] = o[2] = o[3] = OutT(0);
-                    if (p.depth) {
-                        OutT *d = reinterpret_cast<OutT *>(p.depth) + 2 * pix;
-                        d[0] = d[1] = OutT(0);
-                    }
+                    xfer_zero<OutT>(pix, p.out, p.depth);
                     if (p.status) p.status[pix] = (uint8_t)rstat;
                 }
             } else {
@@ -183,115 +322,14 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
         n--;
         const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
         double4_32a q0 = src[0], q1 = src[1];
-        R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
-        R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
-        R hs = to_real<R>(q1.w);
-        R h = fabs(hs);
         KS<R> m;
-        m.eval(a, r, th);
-        if (basis && hs < R(0)) {  // that step crossed the polar axis: bring n+1 into this chart
-            eo1[2] = -eo1[2];
-            eo2[2] = -eo2[2];
-            u1[2] = -u1[2];
-            u2[2] = -u2[2];
-            a1[2] = -a1[2];
-            a2[2] = -a2[2];
-        }
-        Plasma<R> pl;
-        if (p.model.kind == 1)
-            adaf_plasma(p.model.adaf, a, m, r, pl);
-        else
-            grid_plasma(p.model.grid, m, r, th, ph, pl);
-        R e1[4], e2[4], w, sth, cth;
-        if (pl.valid) fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
-        if (basis || pl.valid) {
-            // transport the legs from n+1 to n, then T E at n for the next step
-            R T0[4][4];
-            connection_T(m, K, T0);
-            if (basis) {
-                heun_leg(eo1, u1, a1, T0, h);
-                heun_leg(eo2, u2, a2, T0, h);
-            }
-            R E1[4], E2[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                E1[i] = pl.valid ? e1[i] : eo1[i] + u1[i];
-                E2[i] = pl.valid ? e2[i] : eo2[i] + u2[i];
-            }
-            matvec4(T0, E1, a1);
-            matvec4(T0, E2, a2);
-        }
-        if (pl.valid) {
-            if (basis) {
-                R l1[4], l2[4];
-                m.lower(e1, l1);
-                m.lower(e2, l2);
-                reproject_comp(l1, l2, e1, e2, eo1, eo2, u1, u2, S, Slo);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                eo1[i] = e1[i];
-                eo2[i] = e2[i];
-                u1[i] = u2[i] = R(0);
-            }
-            R cf[8];
-            thermal_coeffs(pl.ne, pl.Te, pl.B, w * nu_obs, sth, cth, sgw, cf);
-            // invariant form: S holds I/nu^3, so the step takes J/w^3 and the same M
-            R ds = w * h * L;
-            substep(cf, ds, R(1) / (w * w * w), S, Slo);
-            kahan_add(tau, tauc, cf[3] * ds);
-            kahan_add(phi, phic, cf[7] * ds);
-            basis = true;
-            my_emit++;
-        }
+        if (xfer_point(c, p.model, q0, q1, sgw, Ln, m)) my_emit++;
         my_pts++;
         if (n == 0) {
             int ix, iy;
             ray_pixel(ray + p.ray_offset, c.nx, c.ny, ix, iy);
-#pragma unroll
-            for (int i = 0; i < 4; i++) S[i] += Slo[i];
-            if (basis) {
-                // camera screen: x along e_phi, y along -e_theta, each normal to the ray
-                double e[4][4], s[3];
-                camera_tetrad(c.a, c.r_cam, c.theta_o, e);
-                sky_direction(c, ix, iy, s);
-                double xh[3] = {-s[2] * s[0], -s[2] * s[1], 1.0 - s[2] * s[2]};
-                double nx = rsqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
-                double yh[3] = {s[1] * s[0], -1.0 + s[1] * s[1], s[1] * s[2]};
-                double yx = yh[0] * xh[0] * nx + yh[1] * xh[1] * nx + yh[2] * xh[2] * nx;
-                R X[4], Y[4];
-                for (int k = 0; k < 3; k++) {
-                    xh[k] *= nx;
-                    yh[k] -= yx * xh[k];
-                }
-                double ny = rsqrt(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
-#pragma unroll
-                for (int mu = 0; mu < 4; mu++) {
-                    X[mu] = R(xh[0] * e[1][mu] + xh[1] * e[2][mu] + xh[2] * e[3][mu]);
-                    Y[mu] = R(ny * (yh[0] * e[1][mu] + yh[1] * e[2][mu] + yh[2] * e[3][mu]));
-                }
-                R lx[4], ly[4], E1[4], E2[4];
-                m.lower(X, lx);
-                m.lower(Y, ly);
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    E1[i] = eo1[i] + u1[i];
-                    E2[i] = eo2[i] + u2[i];
-                }
-                reproject(lx, ly, E1, E2, S);
-            }
-            long long pix = (long long)iy * c.nx + ix;
-            OutT *o = reinterpret_cast<OutT *>(p.out) + 4 * pix;
-            o[0] = OutT(S[0]);
-            o[1] = OutT(S[1]);
-            o[2] = OutT(S[2]);
-            o[3] = OutT(S[3]);
-            if (p.depth) {
-                OutT *d = reinterpret_cast<OutT *>(p.depth) + 2 * pix;
-                d[0] = OutT(tau - tauc);
-                d[1] = OutT(phi - phic);
-            }
-            if (p.status) p.status[pix] = (uint8_t)rstat;
+            xfer_finish<R, OutT>(c, m, ix, iy, Ln, p.out, p.depth);
+            if (p.status) p.status[(long long)iy * c.nx + ix] = (uint8_t)rstat;
             live = false;
         }
     }

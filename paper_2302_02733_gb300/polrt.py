@@ -15,6 +15,7 @@ import numpy as np
 from . import build as _build
 
 RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_NOMEM, RT_ERR_NOT_READY, RT_ERR_WORKSPACE, RT_ERR_SIZE = 0, -1, -2, -3, -4, -5, -6
+RT_ERR_STALL = -7
 RT_MODEL_ADAF, RT_MODEL_GRID = 1, 2
 RT_FP64, RT_MIXED = 0, 1
 RT_RAY_HORIZON, RT_RAY_ESCAPE, RT_RAY_NMAX, RT_RAY_NAN, RT_RAY_OVERFLOW = 1, 2, 3, 4, 5
@@ -47,7 +48,16 @@ class rt_counters(C.Structure):
                 ("emitting_points", C.c_uint64), ("arena_blocks_used", C.c_uint64),
                 ("arena_blocks_total", C.c_uint64), ("n_horizon", C.c_uint32), ("n_escape", C.c_uint32),
                 ("n_nmax", C.c_uint32), ("n_nan", C.c_uint32), ("n_overflow", C.c_uint32),
-                ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float)]
+                ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float), ("ms_total", C.c_float)]
+
+
+class rt_job(C.Structure):
+    _fields_ = [("cam", rt_camera), ("M_unit", C.c_double), ("R_high", C.c_double), ("out_iquv", C.c_void_p),
+                ("status", C.c_void_p), ("out_depth", C.c_void_p)]
+
+
+class rt_batch_config(C.Structure):
+    _fields_ = [("geo_warps", C.c_int), ("step_tile", C.c_int), ("blocks_per_sm", C.c_int), ("ms", C.c_float)]
 
 
 _lib = None
@@ -76,6 +86,10 @@ def lib():
         L.rt_last_counters.argtypes = [_VP, C.POINTER(rt_counters)]
         L.rt_render_static.argtypes = [_VP, C.c_int, _VP, _VP]
         L.rt_render_depths.argtypes = [_VP, C.c_int, _VP, _VP, _VP]
+        L.rt_render_batch.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int]
+        L.rt_batch_autotune.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int, C.POINTER(rt_batch_config)]
+        L.rt_set_batch_config.argtypes = [_VP, C.c_int, C.POINTER(rt_batch_config)]
+        L.rt_get_batch_config.argtypes = [_VP, C.c_int, C.POINTER(rt_batch_config)]
         L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
         L.rt_error_string.restype = C.c_char_p
@@ -123,12 +137,15 @@ def rt_set_stream(ctx, stream):
     _check(lib().rt_set_stream(ctx, stream), "rt_set_stream")
 
 
+def _camera(cam) -> rt_camera:
+    if isinstance(cam, rt_camera):
+        return cam
+    return rt_camera(cam.a, cam.incl_deg, cam.r_cam, cam.freq_hz, cam.fov_M, cam.nx, cam.ny, cam.M_bh_g, cam.dist_cm)
+
+
 def rt_set_camera(ctx, cam):
     """cam: an rt_camera, or any object with the same field names (e.g. synth.Camera)."""
-    if not isinstance(cam, rt_camera):
-        cam = rt_camera(cam.a, cam.incl_deg, cam.r_cam, cam.freq_hz, cam.fov_M, cam.nx, cam.ny, cam.M_bh_g,
-                        cam.dist_cm)
-    _check(lib().rt_set_camera(ctx, C.byref(cam)), "rt_set_camera")
+    _check(lib().rt_set_camera(ctx, C.byref(_camera(cam))), "rt_set_camera")
 
 
 def rt_set_integrator(ctx, eps: float = 0.05, nmax: int = 20000):
@@ -190,6 +207,46 @@ def rt_render_depths(ctx, form: int, out_iquv, out_depth, status=None, check: bo
     if check:
         _check(rc, "rt_render_depths")
     return rc
+
+
+def make_jobs(items) -> C.Array:
+    """items: iterable of (camera, M_unit, R_high, out_iquv, status, out_depth); camera as for
+    rt_set_camera, buffers device tensors (status and out_depth may be None)."""
+    items = list(items)
+    arr = (rt_job * len(items))()
+    for j, (cam, mu, rh, out, st, dep) in zip(arr, items):
+        j.cam = _camera(cam)
+        j.M_unit = mu
+        j.R_high = rh
+        j.out_iquv = _ptr(out)
+        j.status = _ptr(st)
+        j.out_depth = _ptr(dep)
+    return arr
+
+
+def rt_render_batch(ctx, form: int, jobs, check: bool = True) -> int:
+    """Render every job of an rt_job array (see make_jobs) in one persistent launch."""
+    rc = lib().rt_render_batch(ctx, form, jobs, len(jobs))
+    if check:
+        _check(rc, "rt_render_batch")
+    return rc
+
+
+def rt_batch_autotune(ctx, form: int, jobs) -> dict:
+    b = rt_batch_config()
+    _check(lib().rt_batch_autotune(ctx, form, jobs, len(jobs), C.byref(b)), "rt_batch_autotune")
+    return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
+
+
+def rt_set_batch_config(ctx, form: int, geo_warps: int, step_tile: int, blocks_per_sm: int):
+    b = rt_batch_config(geo_warps, step_tile, blocks_per_sm, 0.0)
+    _check(lib().rt_set_batch_config(ctx, form, C.byref(b)), "rt_set_batch_config")
+
+
+def rt_get_batch_config(ctx, form: int) -> dict:
+    b = rt_batch_config()
+    _check(lib().rt_get_batch_config(ctx, form, C.byref(b)), "rt_get_batch_config")
+    return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
 
 
 def rt_render_static(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:

@@ -30,7 +30,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_error_strings(lib):
     from paper_2302_02733_gb300 import polrt
 
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert polrt.rt_error_string(code)
     assert "unknown" in polrt.rt_error_string(-99)
     assert polrt.rt_workspace_min_bytes() > 0
@@ -42,6 +42,10 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rt_destroy(None) == polrt.RT_ERR_INVALID
     assert lib.rt_render(None, 0, None, None) == polrt.RT_ERR_INVALID
     assert lib.rt_set_integrator(None, 0.05, 100) == polrt.RT_ERR_INVALID
+    assert lib.rt_render_batch(None, 0, None, 0) == polrt.RT_ERR_INVALID
+    assert lib.rt_batch_autotune(None, 0, None, 0, None) == polrt.RT_ERR_INVALID
+    assert lib.rt_set_batch_config(None, 0, None) == polrt.RT_ERR_INVALID
+    assert lib.rt_render_depths(None, 0, None, None, None) == polrt.RT_ERR_INVALID
 
 
 def test_create_without_gpu_reports_an_error():
