@@ -1,7 +1,8 @@
 """ctypes front-end of the plain FP64 CPU oracle (test infrastructure only).
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
-import this package. The CUDA library never does. ``build()`` compiles ``oracle.c`` with
+import this package. The CUDA library never does. ``build()`` compiles ``oracle.c`` and
+``kappa.c`` with
 gcc, OpenMP and FP contraction off, so the results do not depend on the host's FMA units.
 """
 from __future__ import annotations
@@ -21,12 +22,12 @@ MODEL_ADAF, MODEL_GRID = 1, 2
 
 
 def build(force: bool = False) -> str:
-    src = os.path.join(_HERE, "oracle.c")
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "kappa.c")]
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
-            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            [os.path.getmtime(f) for f in srcs] + [os.path.getmtime(os.path.join(_HERE, "oracle.h"))]):
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fopenmp", "-fPIC", "-shared", "-o", _SO, src, "-lm"])
+                               "-fopenmp", "-fPIC", "-shared", "-o", _SO] + srcs + ["-lm"])
     return _SO
 
 
@@ -78,6 +79,8 @@ def lib():
         L.ora_bessel_k_scaled.restype = C.c_double
         L.ora_thermal_coeffs.argtypes = [C.c_double] * 5 + [_D]
         L.ora_substep.argtypes = [_D, C.c_double, _D, _D]
+        L.ora_synch_kernels.argtypes = [C.c_double, _D]
+        L.ora_kappa_coeffs.argtypes = [C.c_double] * 6 + [_D]
         L.ora_render_pixels.argtypes = [C.POINTER(Camera), C.POINTER(Model), C.c_int, _I, _I, C.c_int,
                                         _D, _I, _I, _D, _D, C.c_int]
         L.ora_render_pixels.restype = C.c_int
@@ -231,6 +234,21 @@ def bessel_k_scaled(n, z):
 def thermal_coeffs(ne, Te, B, nu, thB):
     out = np.zeros(8)
     lib().ora_thermal_coeffs(ne, Te, B, nu, thB, _dp(out))
+    return out
+
+
+def synch_kernels(x):
+    """(F, G, H)(x): x int_x^inf K_5/3, x K_2/3(x), x K_1/3(x) + int_x^inf K_1/3."""
+    out = np.zeros(3)
+    lib().ora_synch_kernels(x, _dp(out))
+    return out
+
+
+def kappa_coeffs(ne, Te, B, nu, thB, kappa):
+    """Coefficients (jI jQ jV aI aQ aV rQ rV) by quadrature over a kappa distribution
+    (kappa > 3) or, for kappa <= 0, the Maxwell-Juttner distribution."""
+    out = np.zeros(8)
+    lib().ora_kappa_coeffs(ne, Te, B, nu, thB, kappa, _dp(out))
     return out
 
 

@@ -78,6 +78,10 @@ double ora_fluid_tetrad(double a, const double x[4], const double K[4], const do
 double ora_bessel_k_scaled(int n, double z); /* e^z K_n(z) */
 /* out: jI jQ jV aI aQ aV rQ rV (cgs) */
 void ora_thermal_coeffs(double ne, double Thetae, double B, double nu, double thetaB, double out[8]);
+/* kappa.c: synchrotron kernels (F, G, H)(x) and coefficients by quadrature over a kappa
+ * distribution (kappa > 3) or, for kappa <= 0, over the Maxwell-Juttner distribution */
+void ora_synch_kernels(double x, double out[3]);
+void ora_kappa_coeffs(double ne, double Thetae, double B, double nu, double thetaB, double kappa, double out[8]);
 /* coef: jI jQ jU jV aI aQ aU aV rQ rU rV ; exact constant-coefficient solution over ds */
 void ora_substep(const double coef[11], double ds, const double S0[4], double S1[4]);
 
