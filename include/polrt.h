@@ -168,6 +168,68 @@ int rt_render_depths(rt_ctx *ctx, int form, void *out_iquv, uint8_t *status, voi
 int rt_image_stats(rt_ctx *ctx, const void *iquv, int form, double *flux_jy, double *lp_frac,
                    double *cp_frac);
 
+/* Synchrotron coefficients of n plasma points by quadrature over the electron distribution
+ * (the nonthermal models of Section 2.1, integrated numerically as Section 4 proposes).
+ * in: n x 6 doubles per point (n_e [cm^-3], Theta_e, B [G], nu [Hz] in the fluid frame,
+ * theta_B [rad], kappa): kappa > 3 selects the kappa distribution with width
+ * w = (kappa - 3) Theta_e / kappa, kappa <= 0 the Maxwell-Juttner distribution; other kappa
+ * give zeros. out: n x 8 doubles (j_I, j_Q, j_V [erg s^-1 cm^-3 Hz^-1 sr^-1], a_I, a_Q, a_V,
+ * r_Q, r_V [cm^-1]) in the polarization basis of rt_render (Q across the projected field).
+ * Host or device pointers; synchronizes. */
+int rt_kappa_coeffs(rt_ctx *ctx, const double *in, long long n, double *out);
+
+/* ---- The nonthermal coefficient surrogate ---------------------------------------------------
+ * A 4 -> 64 -> 64 -> 64 -> 8 perceptron with SiLU hidden units stands in for rt_kappa_coeffs. It
+ * runs on the tensor cores (BF16 operands, FP32 accumulation), and is trained there.
+ *
+ * Inputs: f = (ln(nu / nu_c), theta_B folded into (0, pi/2], ln Theta_e, kappa) with
+ * nu_c = (3/2) nu_B sin(theta_B) Theta_e^2, each mapped linearly from the box [lo, hi] to
+ * [-1, 1] (x). Targets: the logarithms of the coefficients over known prefactors (the thermal
+ * fits' prefactors; Shcherbakov's corrections for the rotativities), which depend on f only.
+ * Each target k is base[k] . phi(x) + y_mean[k] + y_std[k] y_k with phi the 35 monomials of
+ * degree <= 3 in x (order: 1; x_i; x_i x_j, i <= j; x_i x_j x_k, i <= j <= k) and y the
+ * network's output: the polynomial carries the large trends, the network the standardised
+ * residual. Parameters: RT_MLP_PARAMS floats,
+ * layer after layer (4 -> 64, 64 -> 64, 64 -> 64, 64 -> 8), each as [out][in + 1] with the bias
+ * in the last column. */
+#define RT_MLP_PARAMS 9160
+typedef struct {
+    float lo[4], hi[4];          /* the training box of the inputs */
+    float y_mean[8], y_std[8];   /* residual standardisation */
+    float base[8][35];           /* polynomial baseline of each target */
+} rt_mlp_norm;
+
+/* Load parameters (host or device) and normalisation; builds the tensor-core images. */
+int rt_mlp_set_params(rt_ctx *ctx, const float *theta, const rt_mlp_norm *norm);
+/* Copy the current parameters (theta may be host or device, or NULL) and normalisation out. */
+int rt_mlp_get_params(rt_ctx *ctx, float *theta, rt_mlp_norm *norm);
+/* y[n][8] = network(x[n][4]) on normalised inputs (device pointers). RT_ERR_STALL if a bounded
+ * wait for the tensor core ran out. */
+int rt_mlp_forward(rt_ctx *ctx, const float *x, long long n, float *y);
+/* Gradient of the mean squared error sum_(samples, outputs) (y - t)^2 / (8 n) with respect to
+ * the parameters, and the loss (x, t device; grad host or device, RT_MLP_PARAMS floats). */
+int rt_mlp_grad(rt_ctx *ctx, const float *x, const float *t, long long n, float *grad, float *loss);
+/* Adam (beta 0.9, 0.999; cosine-decayed learning rate from lr) for `steps` steps on batches of
+ * `batch` samples (a multiple of 128) taken as random windows of the n samples (device x, t:
+ * standardised targets). Starts from the loaded parameters; loss_curve (host, steps floats)
+ * may be NULL. */
+int rt_mlp_train(rt_ctx *ctx, const float *x, const float *t, long long n, int steps, int batch, float lr,
+                 uint64_t seed, float *loss_curve);
+/* Training set of n points drawn uniformly (counter-based splitmix64 from seed) in the box
+ * {lo[4], hi[4]} of the inputs (theta_B inside (0, pi/2], kappa > 3): x[n][4] normalised inputs,
+ * y[n][8] unstandardised targets computed by the quadrature, valid[n] whether every target is
+ * finite. Device pointers; synchronizes. */
+int rt_surrogate_dataset(rt_ctx *ctx, const float box[8], long long n, uint64_t seed, float *x, float *y, int *valid);
+/* Prepare training targets from a rt_surrogate_dataset set: fit the polynomial baseline by least
+ * squares over the valid rows, and standardise the residuals. norm: lo and hi set by the caller
+ * (the box); base, y_mean and y_std are filled. t[n][8] receives the standardised residuals
+ * (zeros on invalid rows). Device x, y, valid, t. */
+int rt_surrogate_fit(rt_ctx *ctx, const float *x, const float *y, const int *valid, long long n, float *t,
+                     rt_mlp_norm *norm);
+/* rt_kappa_coeffs through the surrogate: points inside the training box from the network,
+ * others from the quadrature (inside[n], optional, tells which). Device pointers. */
+int rt_surrogate_coeffs(rt_ctx *ctx, const double *in, long long n, double *out, uint8_t *inside);
+
 /* Counters of the last rt_render (synchronizes). */
 int rt_last_counters(rt_ctx *ctx, rt_counters *out);
 

@@ -7,6 +7,7 @@
 #include <new>
 
 #include "host_util.cuh"
+#include "kappa.cuh"
 #include "polrt.h"
 
 using namespace prt;
@@ -71,6 +72,7 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     c->pipe_bps[1] = pipe_blocks_per_sm_mixed();
     bool ok = cudaMalloc(&c->d_stats, 8 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->d_sctab, kSinTabBytes) == cudaSuccess &&
+              cudaMalloc(&c->d_syn, kSynTabBytes) == cudaSuccess && cudaMalloc(&c->d_gl, 16 * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking) == cudaSuccess;
     for (int i = 0; i < 3 && ok; i++) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
@@ -82,7 +84,7 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     }
     memset(c->h_ctr, 0, sizeof(Counters));
     launch_sincos_table(c->d_sctab, c->stream);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    if (launch_kappa_tables(c->d_syn, c->d_gl, c->stream) != 0 || cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaGetLastError();
         rt_destroy(c);
         return RT_ERR_CUDA;
@@ -103,6 +105,12 @@ int rt_destroy(rt_ctx *c) {
     cudaFree(c->d_stage_depth);
     cudaFree(c->d_stats);
     cudaFree(c->d_sctab);
+    cudaFree(c->d_syn);
+    cudaFree(c->d_gl);
+    cudaFree(c->d_theta);
+    cudaFree(c->d_wpk);
+    cudaFree(c->d_tpk);
+    cudaFree(c->d_mlpaux);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     for (int i = 0; i < 3; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -358,6 +366,39 @@ int rt_image_stats(rt_ctx *c, const void *iquv, int form, double *flux_jy, doubl
     if (flux_jy) *flux_jy = h[4];
     if (lp_frac) *lp_frac = h[5];
     if (cp_frac) *cp_frac = h[6];
+    return RT_OK;
+}
+
+int rt_kappa_coeffs(rt_ctx *c, const double *in, long long n, double *out) {
+    if (!c || !in || !out || n < 0) return RT_ERR_INVALID;
+    if (n == 0) return RT_OK;
+    CK(cudaSetDevice(c->device));
+    const double *d_in = in;
+    double *d_out = out;
+    void *tmp = nullptr;
+    bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+    if (!in_dev || !out_dev) {
+        if (cudaMalloc(&tmp, (size_t)n * 14 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ERR_NOMEM;
+        }
+        if (!in_dev) {
+            d_in = (const double *)tmp;
+            CK(cudaMemcpyAsync((void *)d_in, in, (size_t)n * 6 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        }
+        if (!out_dev) d_out = (double *)tmp + 6 * n;
+    }
+    KappaTables T{c->d_syn, c->d_gl, c->d_gl + 8};
+    launch_kappa_quad(T, d_in, d_out, n, c->nsm * 8, c->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !out_dev)
+        e = cudaMemcpyAsync(out, d_out, (size_t)n * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_CUDA;
+    }
     return RT_OK;
 }
 

@@ -29,6 +29,13 @@ struct rt_ctx {
     size_t stage_depth_bytes = 0;
     double *d_stats = nullptr;
     double *d_sctab = nullptr;  // sin/cos table of the FP64 geodesic
+    double *d_syn = nullptr;    // ln F, ln G, ln H tables of the kappa quadrature
+    double *d_gl = nullptr;     // its Gauss-Legendre nodes and weights
+    // surrogate MLP: parameters | Adam m | Adam v | gradient (FP32), tensor-core images, scalars
+    float *d_theta = nullptr;
+    void *d_wpk = nullptr, *d_tpk = nullptr, *d_mlpaux = nullptr;
+    rt_mlp_norm mlp_norm{};
+    bool have_mlp = false;
     prt::Counters *h_ctr = nullptr;  // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     long long last_rays = 0, last_blocks_total = 0;

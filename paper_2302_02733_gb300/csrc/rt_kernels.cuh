@@ -82,6 +82,12 @@ void launch_pipe_mixed(const PipeArgs &a, int grid, cudaStream_t s);
 int pipe_blocks_per_sm_fp64();
 int pipe_blocks_per_sm_mixed();
 
+// ---- kappa-distribution coefficients by quadrature (kappa.cuh) ---------------------------
+constexpr size_t kSynTabBytes = 3 * 4096 * sizeof(double);
+int launch_kappa_tables(double *lnk, double *gl16, cudaStream_t s);  // gl16: 8 nodes + 8 weights
+struct KappaTables;
+void launch_kappa_quad(const KappaTables &T, const double *in, double *out, long long n, int grid, cudaStream_t s);
+
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
 void launch_sincos_table(double *tab, cudaStream_t s);
 constexpr size_t kSinTabBytes = 2048 * 3 * sizeof(double);

@@ -51,6 +51,14 @@ class rt_counters(C.Structure):
                 ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float), ("ms_total", C.c_float)]
 
 
+class rt_mlp_norm(C.Structure):
+    _fields_ = [("lo", C.c_float * 4), ("hi", C.c_float * 4), ("y_mean", C.c_float * 8), ("y_std", C.c_float * 8),
+                ("base", (C.c_float * 35) * 8)]
+
+
+RT_MLP_PARAMS = 9160
+
+
 class rt_job(C.Structure):
     _fields_ = [("cam", rt_camera), ("M_unit", C.c_double), ("R_high", C.c_double), ("out_iquv", C.c_void_p),
                 ("status", C.c_void_p), ("out_depth", C.c_void_p)]
@@ -86,6 +94,15 @@ def lib():
         L.rt_last_counters.argtypes = [_VP, C.POINTER(rt_counters)]
         L.rt_render_static.argtypes = [_VP, C.c_int, _VP, _VP]
         L.rt_render_depths.argtypes = [_VP, C.c_int, _VP, _VP, _VP]
+        L.rt_kappa_coeffs.argtypes = [_VP, _VP, C.c_longlong, _VP]
+        L.rt_mlp_set_params.argtypes = [_VP, _VP, C.POINTER(rt_mlp_norm)]
+        L.rt_mlp_get_params.argtypes = [_VP, _VP, C.POINTER(rt_mlp_norm)]
+        L.rt_mlp_forward.argtypes = [_VP, _VP, C.c_longlong, _VP]
+        L.rt_mlp_grad.argtypes = [_VP, _VP, _VP, C.c_longlong, _VP, C.POINTER(C.c_float)]
+        L.rt_mlp_train.argtypes = [_VP, _VP, _VP, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_uint64, _VP]
+        L.rt_surrogate_dataset.argtypes = [_VP, _VP, C.c_longlong, C.c_uint64, _VP, _VP, _VP]
+        L.rt_surrogate_coeffs.argtypes = [_VP, _VP, C.c_longlong, _VP, _VP]
+        L.rt_surrogate_fit.argtypes = [_VP, _VP, _VP, _VP, C.c_longlong, _VP, C.POINTER(rt_mlp_norm)]
         L.rt_render_batch.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int]
         L.rt_batch_autotune.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int, C.POINTER(rt_batch_config)]
         L.rt_set_batch_config.argtypes = [_VP, C.c_int, C.POINTER(rt_batch_config)]
@@ -207,6 +224,64 @@ def rt_render_depths(ctx, form: int, out_iquv, out_depth, status=None, check: bo
     if check:
         _check(rc, "rt_render_depths")
     return rc
+
+
+def rt_kappa_coeffs(ctx, inp, out):
+    """inp: [n, 6] float64 (ne, Theta_e, B, nu, theta_B, kappa); out: [n, 8] float64."""
+    _check(lib().rt_kappa_coeffs(ctx, _ptr(inp), int(inp.shape[0]), _ptr(out)), "rt_kappa_coeffs")
+
+
+def mlp_norm(lo, hi, y_mean=None, y_std=None) -> rt_mlp_norm:
+    n = rt_mlp_norm()
+    for j in range(4):
+        n.lo[j], n.hi[j] = float(lo[j]), float(hi[j])
+    for k in range(8):
+        n.y_mean[k] = 0.0 if y_mean is None else float(y_mean[k])
+        n.y_std[k] = 1.0 if y_std is None else float(y_std[k])
+    return n
+
+
+def rt_mlp_set_params(ctx, theta, norm: rt_mlp_norm):
+    _check(lib().rt_mlp_set_params(ctx, _ptr(theta), C.byref(norm)), "rt_mlp_set_params")
+
+
+def rt_mlp_get_params(ctx, theta=None) -> rt_mlp_norm:
+    n = rt_mlp_norm()
+    _check(lib().rt_mlp_get_params(ctx, _ptr(theta), C.byref(n)), "rt_mlp_get_params")
+    return n
+
+
+def rt_mlp_forward(ctx, x, y):
+    _check(lib().rt_mlp_forward(ctx, _ptr(x), int(x.shape[0]), _ptr(y)), "rt_mlp_forward")
+
+
+def rt_mlp_grad(ctx, x, t, grad) -> float:
+    loss = C.c_float(0)
+    _check(lib().rt_mlp_grad(ctx, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad), C.byref(loss)), "rt_mlp_grad")
+    return loss.value
+
+
+def rt_mlp_train(ctx, x, t, steps: int, batch: int, lr: float, seed: int, loss_curve=None):
+    _check(lib().rt_mlp_train(ctx, _ptr(x), _ptr(t), int(x.shape[0]), steps, batch, lr, seed, _ptr(loss_curve)),
+           "rt_mlp_train")
+
+
+def rt_surrogate_dataset(ctx, box, n: int, seed: int, x, y, valid):
+    b = (C.c_float * 8)(*[float(v) for v in box])
+    _check(lib().rt_surrogate_dataset(ctx, b, n, seed, _ptr(x), _ptr(y), _ptr(valid)), "rt_surrogate_dataset")
+
+
+def rt_surrogate_fit(ctx, x, y, valid, t, lo, hi) -> rt_mlp_norm:
+    """Baseline fit and standardised residual targets; returns the filled rt_mlp_norm."""
+    n = mlp_norm(lo, hi)
+    _check(lib().rt_surrogate_fit(ctx, _ptr(x), _ptr(y), _ptr(valid), int(x.shape[0]), _ptr(t), C.byref(n)),
+           "rt_surrogate_fit")
+    return n
+
+
+def rt_surrogate_coeffs(ctx, inp, out, inside=None):
+    _check(lib().rt_surrogate_coeffs(ctx, _ptr(inp), int(inp.shape[0]), _ptr(out), _ptr(inside)),
+           "rt_surrogate_coeffs")
 
 
 def make_jobs(items) -> C.Array:
