@@ -48,11 +48,16 @@ enum { RT_MODEL_ADAF = 1, RT_MODEL_GRID = 2 };
 /* Forms of the hot path. */
 enum {
     RT_FP64 = 0,  /* geodesic, plasma, coefficients and transfer all in FP64; output double */
-    RT_MIXED = 1  /* FP64 geodesic and path; FP32 plasma fetch, coefficients and transfer.
+    RT_MIXED = 1, /* FP64 geodesic and path; FP32 plasma fetch, coefficients and transfer.
                      The Stokes vector is carried as a compensated pair (value + error term):
                      every step forms its change (screen re-projection, radiative step) as an
                      increment and adds it by an error-free sum, and the optical and Faraday
                      depths are Kahan sums. Output float. */
+    RT_SURROGATE = 2 /* the mixed form with kappa electrons whose coefficients come from the
+                        trained surrogate network (rt_mlp_*), evaluated on the tensor cores for
+                        every saved state before the transfer; the quadrature answers outside
+                        the network's box. Needs model edf RT_EDF_KAPPA and loaded
+                        parameters. Output float. */
 };
 
 /* Per-pixel status codes written to the optional status buffer. */
@@ -89,10 +94,18 @@ typedef struct {
     double gamma_ad;     /* adiabatic index of the fluid */
 } rt_grid_params;
 
+enum { RT_EDF_THERMAL = 0, RT_EDF_KAPPA = 1 };
+
 typedef struct {
     int kind; /* RT_MODEL_ADAF or RT_MODEL_GRID */
     rt_adaf_params adaf;
     rt_grid_params grid;
+    /* electron distribution (Section 2.1: thermal or nonthermal): RT_EDF_THERMAL uses the
+     * Maxwell-Juttner fits; RT_EDF_KAPPA the kappa distribution of index kappa (> 3) with
+     * width w = (kappa - 3) Theta_e / kappa, by quadrature (RT_FP64, RT_MIXED) or by the
+     * surrogate (RT_SURROGATE) */
+    int edf;
+    double kappa;
 } rt_model_params;
 
 /* Camera and image: a static observer at radius r_cam, inclination incl_deg, azimuth 0,
@@ -226,6 +239,12 @@ int rt_surrogate_dataset(rt_ctx *ctx, const float box[8], long long n, uint64_t 
  * (zeros on invalid rows). Device x, y, valid, t. */
 int rt_surrogate_fit(rt_ctx *ctx, const float *x, const float *y, const int *valid, long long n, float *t,
                      rt_mlp_norm *norm);
+/* The surrogate's inputs f = (ln(nu/nu_c), theta_B folded into (0, pi/2], ln Theta_e, kappa) at
+ * every emitting point of the current camera's rays (the points the transfer will visit), as
+ * float4 rows written to feat (device) in no particular order, at most cap of them; *count
+ * receives the number of emitting points (which may exceed cap). For choosing a training box
+ * from an image. Synchronizes. */
+int rt_render_features(rt_ctx *ctx, float *feat, long long cap, long long *count);
 /* rt_kappa_coeffs through the surrogate: points inside the training box from the network,
  * others from the quadrature (inside[n], optional, tells which). Device pointers. */
 int rt_surrogate_coeffs(rt_ctx *ctx, const double *in, long long n, double *out, uint8_t *inside);

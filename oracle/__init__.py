@@ -111,14 +111,19 @@ class ModelHandle:
         self.keep = keep
 
 
-def adaf_model(p) -> ModelHandle:
+EDF_THERMAL, EDF_KAPPA = 0, 1
+
+
+def adaf_model(p, kappa: float = 0.0) -> ModelHandle:
+    """kappa > 3 selects kappa electrons (coefficients by quadrature), else thermal."""
     m = Model()
     m.kind = MODEL_ADAF
     m.n0, m.T0, m.beta, m.f_kep, m.Ti_over_Te, m.r_out_emit = p.n0, p.T0, p.beta, p.f_kep, p.Ti_over_Te, p.r_out
+    m.edf, m.kappa = (EDF_KAPPA, kappa) if kappa > 3.0 else (EDF_THERMAL, 0.0)
     return ModelHandle(m)
 
 
-def grid_model(prims: np.ndarray, g) -> ModelHandle:
+def grid_model(prims: np.ndarray, g, kappa: float = 0.0) -> ModelHandle:
     prims = np.ascontiguousarray(prims, dtype=np.float32)
     m = Model()
     m.kind = MODEL_GRID
@@ -127,6 +132,7 @@ def grid_model(prims: np.ndarray, g) -> ModelHandle:
     m.poly_alpha, m.mks_smooth = g.poly_alpha, g.mks_smooth
     m.prims = prims.ctypes.data_as(C.POINTER(C.c_float))
     m.M_unit, m.R_high, m.R_low, m.sigma_cut, m.gamma_ad = g.M_unit, g.R_high, g.R_low, g.sigma_cut, g.gamma_ad
+    m.edf, m.kappa = (EDF_KAPPA, kappa) if kappa > 3.0 else (EDF_THERMAL, 0.0)
     return ModelHandle(m, prims)
 
 

@@ -851,7 +851,10 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
         stokes_from_N(g, e1, e2, N, S);
         double nu = w * nu_obs;
         double c8[8];
-        ora_thermal_coeffs(pl[0], pl[1], pl[2], nu, thB, c8);
+        if (m->edf == ORA_EDF_KAPPA)
+            ora_kappa_coeffs(pl[0], pl[1], pl[2], nu, thB, m->kappa, c8);
+        else
+            ora_thermal_coeffs(pl[0], pl[1], pl[2], nu, thB, c8);
         double cf[11] = {c8[0], c8[1], 0.0, c8[2], c8[3], c8[4], 0.0, c8[5], c8[6], 0.0, c8[7]};
         double ds = w * h * L;
         /* depths: the exponents of the isotropic absorption and the Faraday rotation that

@@ -28,6 +28,7 @@ int fidx(int form) { return form == RT_FP64 ? 0 : 1; }
 int check_jobs(const rt_ctx *c, int form, const rt_job *jobs, int njobs, long long *nrays) {
     if (!c || !jobs || njobs < 1 || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
     if (!c->have_model) return RT_ERR_NOT_READY;
+    if (c->model.edf != RT_EDF_THERMAL) return RT_ERR_INVALID;  // the batched form renders thermal electrons
     long long tot = 0;
     for (int i = 0; i < njobs; i++) {
         int rv = check_camera(jobs[i].cam);

@@ -46,7 +46,7 @@ const char *rt_error_string(int code) {
     }
 }
 
-size_t rt_workspace_min_bytes(void) { return align_up(sizeof(Counters)) + kPerRayBytes + kAlign; }
+size_t rt_workspace_min_bytes(void) { return align_up(sizeof(Counters)) + kPerRayBytes + 4 * kAlign; }
 
 int rt_create(rt_ctx **out, int device, void *stream) {
     if (!out) return RT_ERR_INVALID;
@@ -185,6 +185,8 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
     } else {
         return RT_ERR_INVALID;
     }
+    if (p->edf != RT_EDF_THERMAL && !(p->edf == RT_EDF_KAPPA && p->kappa > 3.0 && p->kappa < 100.0))
+        return RT_ERR_INVALID;
     c->model = *p;
     c->model.grid.prims = nullptr;  // the device copy is used from here on
     c->have_model = true;
@@ -209,13 +211,13 @@ int rt_workspace_hint(const rt_ctx *c, size_t *bytes) {
     if (!c || !bytes) return RT_ERR_INVALID;
     if (!c->have_cam) return RT_ERR_NOT_READY;
     long long nrays = (long long)c->cam.nx * c->cam.ny;
-    *bytes = align_up(sizeof(Counters)) + (size_t)nrays * kPerRayBytes + kAlign;
+    *bytes = align_up(sizeof(Counters)) + (size_t)nrays * kPerRayBytes + 4 * kAlign;
     return RT_OK;
 }
 
-static int ensure_workspace(rt_ctx *c, long long nrays) {
+static int ensure_workspace(rt_ctx *c, long long nrays, size_t per_ray = kPerRayBytes) {
     if (c->ws && !c->ws_owned) return RT_OK;
-    size_t want = align_up(sizeof(Counters)) + (size_t)nrays * kPerRayBytes + kAlign;
+    size_t want = align_up(sizeof(Counters)) + (size_t)nrays * per_ray + 4 * kAlign;
     size_t freeb = 0, total = 0;
     CK(cudaMemGetInfo(&freeb, &total));
     size_t avail = c->ws_bytes + (size_t)(0.6 * (double)freeb);
@@ -251,32 +253,46 @@ static int ensure_stage(void **buf, size_t *have, size_t need) {
 }
 
 static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *depth) {
-    if (!c || !out_iquv || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
+    if (!c || !out_iquv || (form != RT_FP64 && form != RT_MIXED && form != RT_SURROGATE)) return RT_ERR_INVALID;
     if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
     CK(cudaSetDevice(c->device));
     const rt_camera &rc = c->cam;
     long long nrays = (long long)rc.nx * rc.ny;
-    int rv = ensure_workspace(c, nrays);
-    if (rv) return rv;
 
     // camera and model in kernel form
     Camera cam = make_camera(rc, c->eps, c->nmax);
     Model mod = make_model(c, cam);
+    const bool sur = form == RT_SURROGATE;
+    if (sur && (mod.edf != RT_EDF_KAPPA || !c->have_mlp)) return RT_ERR_NOT_READY;
+    const int coef = mod.edf != RT_EDF_KAPPA ? 0 : (sur ? 2 : 1);
 
-    // workspace carving
+    // workspace carving; the surrogate form adds, per saved state, the network's inputs and
+    // outputs (16 + 32 bytes)
+    const size_t per_ray = kPerRayBytes + (sur ? (size_t)kBudgetBlocksPerRay * kBlockStates * 48 : 0);
+    int rv = ensure_workspace(c, nrays, per_ray);
+    if (rv) return rv;
+    const size_t per_block = kBlockBytes + (sur ? (size_t)kBlockStates * 48 : 0);
     char *base = (char *)c->ws;
     Counters *ctr = (Counters *)base;
     size_t off = align_up(sizeof(Counters));
-    size_t room = c->ws_bytes - off - kAlign;
-    long long chunk = std::min<long long>(nrays, (long long)(room / kPerRayBytes));
+    size_t room = c->ws_bytes - off - 3 * kAlign;
+    long long chunk = std::min<long long>(nrays, (long long)(room / per_ray));
     if (chunk < 1) return RT_ERR_NOMEM;
     RayRecord *rec = (RayRecord *)(base + off);
     off = align_up(off + sizeof(RayRecord) * chunk);
-    long long nblocks = (long long)((c->ws_bytes - off - kAlign) / kBlockBytes);
+    long long nblocks = (long long)((c->ws_bytes - off - 3 * kAlign) / per_block);
     Arena ar;
     ar.states = (PathState *)(base + off);
     ar.prev = (int *)(base + off + (size_t)nblocks * sizeof(PathState) * kBlockStates);
     ar.nblocks = nblocks;
+    float4 *feat = nullptr;
+    float *sur_y = nullptr;
+    if (sur) {
+        off = align_up(off + (size_t)nblocks * kBlockBytes);
+        feat = (float4 *)(base + off);
+        off = align_up(off + (size_t)nblocks * kBlockStates * sizeof(float4));
+        sur_y = (float *)(base + off);
+    }
 
     // outputs: device directly, or staged
     size_t esz = form == RT_FP64 ? sizeof(double) : sizeof(float);
@@ -307,16 +323,39 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     int xf_grid = c->nsm * (form == RT_FP64 ? c->fp64_bps : c->mixed_bps);
     for (long long o = 0; o < nrays; o += chunk) {
         long long n = std::min(chunk, nrays - o);
-        CK(cudaMemsetAsync(ctr, 0, 3 * sizeof(unsigned long long), c->stream));  // queues + arena
+        CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));  // queues + arena
         GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
         XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
+        xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+        if (sur) {
+            xa.feat = feat;
+            xa.sur_y = sur_y;
+            xa.sur_norm = reinterpret_cast<const float *>(c->d_mlpaux) + 4;
+            for (int j = 0; j < 4; j++) {
+                xa.sur_lo[j] = c->mlp_norm.lo[j];
+                xa.sur_hi[j] = c->mlp_norm.hi[j];
+            }
+        }
         if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
         launch_geodesic(ga, geo_grid, c->stream);
+        if (sur) {
+            // the network's inputs for every saved state, then one tensor-core pass over them
+            unsigned long long used = 0;
+            CK(cudaMemcpyAsync(&used, &ctr->arena_next, sizeof(used), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            used = std::min<unsigned long long>(used, (unsigned long long)nblocks);
+            launch_sur_features(xa, xf_grid, c->stream);
+            long long rows = (long long)used * kBlockStates;
+            if (rows > 0)
+                launch_mlp_forward(reinterpret_cast<const float *>(feat), sur_y, rows, c->d_wpk,
+                                   reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
+                                   (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), c->stream);
+        }
         if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
         if (form == RT_FP64)
-            launch_transfer_fp64(xa, xf_grid, c->stream);
+            launch_transfer_fp64(xa, coef, xf_grid, c->stream);
         else
-            launch_transfer_mixed(xa, xf_grid, c->stream);
+            launch_transfer_mixed(xa, coef, xf_grid, c->stream);
         CK(cudaGetLastError());
     }
     CK(cudaEventRecord(c->ev[2], c->stream));
@@ -334,6 +373,51 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     return RT_OK;
 }
 
+int rt_render_features(rt_ctx *c, float *feat, long long cap, long long *count) {
+    if (!c || !feat || cap < 0 || !count) return RT_ERR_INVALID;
+    if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
+    if (!is_device_ptr(feat)) return RT_ERR_INVALID;
+    CK(cudaSetDevice(c->device));
+    const rt_camera &rc = c->cam;
+    long long nrays = (long long)rc.nx * rc.ny;
+    int rv = ensure_workspace(c, nrays);
+    if (rv) return rv;
+    Camera cam = make_camera(rc, c->eps, c->nmax);
+    Model mod = make_model(c, cam);
+    char *base = (char *)c->ws;
+    Counters *ctr = (Counters *)base;
+    size_t off = align_up(sizeof(Counters));
+    long long chunk = std::min<long long>(nrays, (long long)((c->ws_bytes - off - kAlign) / kPerRayBytes));
+    if (chunk < 1) return RT_ERR_NOMEM;
+    RayRecord *rec = (RayRecord *)(base + off);
+    off = align_up(off + sizeof(RayRecord) * chunk);
+    long long nblocks = (long long)((c->ws_bytes - off - kAlign) / kBlockBytes);
+    Arena ar;
+    ar.states = (PathState *)(base + off);
+    ar.prev = (int *)(base + off + (size_t)nblocks * sizeof(PathState) * kBlockStates);
+    ar.nblocks = nblocks;
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
+    for (long long o = 0; o < nrays; o += chunk) {
+        long long n = std::min(chunk, nrays - o);
+        CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));
+        GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
+        XferArgs xa{cam, mod, ar, rec, ctr, n, o, nullptr, nullptr, nullptr};
+        for (int j = 0; j < 4; j++) {
+            xa.sur_lo[j] = 0.f;
+            xa.sur_hi[j] = 1.f;
+        }
+        xa.feat_raw = reinterpret_cast<float4 *>(feat);
+        xa.feat_cap = cap;
+        launch_geodesic(ga, c->nsm * c->geo_bps, c->stream);
+        launch_sur_features(xa, c->nsm * c->mixed_bps, c->stream);
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *count = (long long)c->h_ctr->feat_count;
+    return RT_OK;
+}
+
 int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     return render_impl(c, form, out_iquv, status, nullptr);
 }
@@ -344,7 +428,7 @@ int rt_render_depths(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void 
 }
 
 int rt_image_stats(rt_ctx *c, const void *iquv, int form, double *flux_jy, double *lp_frac, double *cp_frac) {
-    if (!c || !iquv || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
+    if (!c || !iquv || (form != RT_FP64 && form != RT_MIXED && form != RT_SURROGATE)) return RT_ERR_INVALID;
     if (!c->have_cam) return RT_ERR_NOT_READY;
     CK(cudaSetDevice(c->device));
     long long npix = (long long)c->cam.nx * c->cam.ny;

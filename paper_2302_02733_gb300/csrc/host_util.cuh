@@ -55,6 +55,8 @@ inline Camera make_camera(const rt_camera &rc, double eps, int nmax) {
 inline Model make_model(const rt_ctx *c, const Camera &cam, double M_unit = 0.0, double R_high = 0.0) {
     Model mod{};
     mod.kind = c->model.kind;
+    mod.edf = c->model.edf;
+    mod.kappa = c->model.kappa;
     if (mod.kind == RT_MODEL_ADAF) {
         const rt_adaf_params &a = c->model.adaf;
         mod.adaf = AdafModel{a.n0, a.T0, a.beta, a.f_kep, a.Ti_over_Te, a.r_out, r_isco(cam.a)};

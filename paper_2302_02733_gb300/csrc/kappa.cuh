@@ -28,11 +28,8 @@ constexpr int kSynTab = 4096;
 constexpr double kSynLo = -27.631021115928547;  // ln 1e-12
 constexpr double kSynHi = 6.606650186198215;    // ln 740
 
-struct KappaTables {
-    const double *lnk;  // [3][kSynTab]: ln F, ln G, ln H at ln x = kSynLo + i h
-    const double *glx;  // 8 Gauss-Legendre nodes on [-1, 1]
-    const double *glw;  // and weights
-};
+// KappaTables (rt_common.cuh): lnk [3][kSynTab] = ln F, ln G, ln H at ln x = kSynLo + i h, and
+// the 8-point Gauss-Legendre nodes and weights.
 
 // F, G, H at x (0 beyond the table's upper end).
 __device__ __forceinline__ void synch_kernels_tab(const KappaTables &T, double x, double k[3]) {

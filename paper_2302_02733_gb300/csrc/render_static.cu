@@ -87,10 +87,12 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     cudaEventRecord(c->ev[0], c->stream);
     launch_geodesic(ga, c->nsm * c->geo_bps, c->stream);
     cudaEventRecord(c->ev[1], c->stream);
+    xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+    const int coef = mod.edf == RT_EDF_KAPPA ? 1 : 0;
     if (form == RT_FP64)
-        launch_transfer_fp64(xa, c->nsm * c->fp64_bps, c->stream);
+        launch_transfer_fp64(xa, coef, c->nsm * c->fp64_bps, c->stream);
     else
-        launch_transfer_mixed(xa, c->nsm * c->mixed_bps, c->stream);
+        launch_transfer_mixed(xa, coef, c->nsm * c->mixed_bps, c->stream);
     cudaEventRecord(c->ev[2], c->stream);
     if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
     if (cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||

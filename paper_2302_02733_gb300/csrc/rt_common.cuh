@@ -55,11 +55,23 @@ struct Model {
     int kind;  // 1 ADAF, 2 grid
     AdafModel adaf;
     GridModel grid;
+    int edf;       // 0 thermal (Maxwell-Juttner fits), 1 kappa distribution
+    double kappa;  // its index (> 3)
+};
+
+// Tables of the kappa quadrature (kappa.cuh): ln F, ln G, ln H and the Gauss-Legendre rule.
+struct KappaTables {
+    const double *lnk;  // [3][4096]
+    const double *glx;  // 8 nodes on [-1, 1]
+    const double *glw;  // and weights
 };
 
 struct Counters {
+    // the first four are reset before every chunk of rays
     unsigned long long geo_next, xfer_next;   // work-queue heads
+    unsigned long long feat_next;             // queue of the surrogate's features pass
     unsigned long long arena_next;            // next free arena block
+    unsigned long long feat_count;            // emitting points written by rt_render_features
     unsigned long long steps, points, emitting;
     unsigned int n_status[8];
 };

@@ -27,6 +27,16 @@ struct XferArgs {
     void *out;            // image [ny][nx][4] of double (FP64 form) or float (mixed form)
     uint8_t *status;      // optional per-pixel status
     void *depth;          // optional [ny][nx][2] optical and Faraday depths, same type as out
+    // kappa electrons (model.edf == 1): the quadrature's tables; for the surrogate form the
+    // network's outputs per saved state (8 floats at state index block * 32 + slot), its
+    // normalisation (8 means, 8 standard deviations, 8 x 35 baseline) and input box
+    KappaTables kt;
+    const float *sur_y;
+    const float *sur_norm;
+    float sur_lo[4], sur_hi[4];
+    float4 *feat;         // features pass: network inputs per saved state
+    float4 *feat_raw;     // or (rt_render_features) raw inputs of the emitting points, compacted
+    long long feat_cap;
 };
 
 // ---- batched rendering: many images in one persistent launch ----------------------------
@@ -85,14 +95,16 @@ int pipe_blocks_per_sm_mixed();
 // ---- kappa-distribution coefficients by quadrature (kappa.cuh) ---------------------------
 constexpr size_t kSynTabBytes = 3 * 4096 * sizeof(double);
 int launch_kappa_tables(double *lnk, double *gl16, cudaStream_t s);  // gl16: 8 nodes + 8 weights
-struct KappaTables;
 void launch_kappa_quad(const KappaTables &T, const double *in, double *out, long long n, int grid, cudaStream_t s);
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
 void launch_sincos_table(double *tab, cudaStream_t s);
 constexpr size_t kSinTabBytes = 2048 * 3 * sizeof(double);
-void launch_transfer_fp64(const XferArgs &a, int grid, cudaStream_t s);
-void launch_transfer_mixed(const XferArgs &a, int grid, cudaStream_t s);
+// coef: 0 thermal fits, 1 kappa quadrature at every emitting point, 2 surrogate outputs
+void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s);
+void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s);
+void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s);
+void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s);
 void launch_x2_table(const GridModel &g, double *table, cudaStream_t s);
 // out[7]: sum I, Q, U, V, flux [Jy], net LP, net CP
 void launch_image_sums(const void *img, int form, long long npix, double domega, double *out, cudaStream_t s);

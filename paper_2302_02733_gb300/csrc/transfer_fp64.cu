@@ -2,8 +2,12 @@
 #include "transfer_kernel.cuh"
 
 namespace prt {
-void launch_transfer_fp64(const XferArgs &a, int grid, cudaStream_t s) {
-    transfer_kernel<double, double><<<grid, kXferThreads, 0, s>>>(a);
+void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s) {
+    switch (coef) {
+        case 0: transfer_kernel<double, double, 0><<<grid, kXferThreads, 0, s>>>(a); break;
+        case 1: transfer_kernel<double, double, 1><<<grid, kXferThreads, 0, s>>>(a); break;
+        default: break;
+    }
 }
 int transfer_blocks_per_sm_fp64() {
     int n = 0;

@@ -4,6 +4,7 @@
 // plasma, and if the point emits it projects onto the fluid screen and takes the exact
 // constant-coefficient step. Instantiated for the FP64 and the mixed (FP32 transfer) forms.
 #pragma once
+#include "surrogate.cuh"
 #include "transfer.cuh"
 
 namespace prt {
@@ -138,9 +139,52 @@ struct XLane {
 // evaluate the plasma, and where it emits, re-project onto the fluid screen and take the
 // exact constant-coefficient step. m returns the metric at the state. Returns whether the
 // point emits.
-template <typename R>
+// Coefficients of an emitting point for kappa electrons: CM 1 by quadrature, CM 2 from the
+// surrogate's outputs for this saved state (quadrature outside the network's box).
+template <typename R, int CM>
+__device__ __forceinline__ void kappa_point_coeffs(const XferArgs *pa, long long st, const Model &mdl,
+                                                   const Plasma<R> &pl, R w, R sth, R cth, R nu_obs, R cf[8]) {
+    typedef Mth<R> F;
+    double thB = atan2((double)sth, (double)cth), nu = (double)(w * nu_obs);
+    double cd[8];
+    bool done = false;
+    if (CM == 2) {
+        float f[4], xn[4];
+        sur_features((double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, f);
+        bool in = true;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            float u = (f[j] - pa->sur_lo[j]) / (pa->sur_hi[j] - pa->sur_lo[j]);
+            in &= u >= 0.0f && u <= 1.0f;
+            xn[j] = 2.0f * u - 1.0f;
+        }
+        if (in) {
+            float phi[kSurBasis], y[8];
+            sur_basis(xn, phi);
+            const float *nm = pa->sur_norm, *yh = pa->sur_y + 8 * st;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                float b = 0.f;
+                for (int q = 0; q < kSurBasis; q++) b += nm[16 + k * kSurBasis + q] * phi[q];
+                y[k] = b + nm[k] + nm[8 + k] * yh[k];
+            }
+            SurPref p = sur_prefactors((double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB);
+            sur_expand(p, y, cd);
+            done = true;
+        }
+    }
+    if (!done) kappa_coeffs_quad(pa->kt, (double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, cd);
+#pragma unroll
+    for (int k = 0; k < 8; k++) cf[k] = R(cd[k]);
+    if (!(cf[0] > F::jflush))  // as for the thermal fits: no relative precision left
+#pragma unroll
+        for (int k = 0; k < 6; k++) cf[k] = R(0);
+}
+
+template <typename R, int CM = 0>
 __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, const double4_32a &q0,
-                                           const double4_32a &q1, const R *sgw, XLane<R> &Ln, KS<R> &m) {
+                                           const double4_32a &q1, const R *sgw, XLane<R> &Ln, KS<R> &m,
+                                           const XferArgs *pa = nullptr, long long st = 0) {
     const R a = R(c.a);
     R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
     R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
@@ -193,7 +237,10 @@ __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, co
             Ln.u1[i] = Ln.u2[i] = R(0);
         }
         R cf[8];
-        thermal_coeffs(pl.ne, pl.Te, pl.B, w * R(c.nu_obs), sth, cth, sgw, cf);
+        if (CM == 0)
+            thermal_coeffs(pl.ne, pl.Te, pl.B, w * R(c.nu_obs), sth, cth, sgw, cf);
+        else
+            kappa_point_coeffs<R, CM>(pa, st, mdl, pl, w, sth, cth, R(c.nu_obs), cf);
         // invariant form: S holds I/nu^3, so the step takes J/w^3 and the same M
         R ds = w * h * R(c.L_unit);
         substep(cf, ds, R(1) / (w * w * w), Ln.S, Ln.Slo);
@@ -275,7 +322,7 @@ __device__ __forceinline__ void fill_bessel_weights(R *sgw) {
     }
 }
 
-template <typename R, typename OutT>
+template <typename R, typename OutT, int CM = 0>
 __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer_kernel(XferArgs p) {
     __shared__ R sgw[32];
     fill_bessel_weights(sgw);
@@ -323,7 +370,7 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
         const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
         double4_32a q0 = src[0], q1 = src[1];
         KS<R> m;
-        if (xfer_point(c, p.model, q0, q1, sgw, Ln, m)) my_emit++;
+        if (xfer_point<R, CM>(c, p.model, q0, q1, sgw, Ln, m, &p, (long long)blk * kBlockStates + slot)) my_emit++;
         my_pts++;
         if (n == 0) {
             int ix, iy;
@@ -335,6 +382,71 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
     }
     if (my_pts) atomicAdd(&p.ctr->points, my_pts);
     if (my_emit) atomicAdd(&p.ctr->emitting, my_emit);
+}
+
+// The surrogate form's features pass: walk each ray's saved states as the transfer will and
+// write, for every emitting state, the network's normalised inputs (f mapped from the box to
+// [-1, 1]); other states get zeros. Same arithmetic as the transfer's own feature evaluation.
+template <typename R>
+__global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
+    const Camera &c = p.cam;
+    const R a = R(c.a), nu_obs = R(c.nu_obs);
+    long long ray = -1;
+    int blk = -1, slot = 0, n = 0;
+    bool live = false, drained = false;
+    for (;;) {
+        bool want = !live && !drained;
+        unsigned long long t = warp_pop(&p.ctr->feat_next, want);
+        if (want) {
+            if (t < (unsigned long long)p.nrays) {
+                ray = (long long)t;
+                RayRecord rec = p.rec[ray];
+                if (rec.nstates >= 2) {
+                    blk = rec.last_block;
+                    slot = (rec.nstates - 1) % kBlockStates;
+                    n = rec.nstates - 1;
+                    live = true;
+                }
+            } else {
+                drained = true;
+            }
+        }
+        if (__all_sync(0xffffffffu, !live && drained)) break;
+        if (!live) continue;
+        if (--slot < 0) {
+            blk = p.arena.prev[blk];
+            slot = kBlockStates - 1;
+        }
+        n--;
+        const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
+        double4_32a q0 = src[0], q1 = src[1];
+        R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
+        R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
+        KS<R> m;
+        m.eval(a, r, th);
+        Plasma<R> pl;
+        if (p.model.kind == 1)
+            adaf_plasma(p.model.adaf, a, m, r, pl);
+        else
+            grid_plasma(p.model.grid, m, r, th, ph, pl);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pl.valid) {
+            R e1[4], e2[4], w, sth, cth;
+            fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
+            double thB = atan2((double)sth, (double)cth), nu = (double)(w * nu_obs);
+            float f[4], xn[4];
+            sur_features((double)pl.Te, (double)pl.B, nu, thB, p.model.kappa, f);
+            if (p.feat_raw) {
+                unsigned long long k = atomicAdd(&p.ctr->feat_count, 1ull);
+                if ((long long)k < p.feat_cap) p.feat_raw[k] = make_float4(f[0], f[1], f[2], f[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) xn[j] = 2.0f * (f[j] - p.sur_lo[j]) / (p.sur_hi[j] - p.sur_lo[j]) - 1.0f;
+            o = make_float4(xn[0], xn[1], xn[2], xn[3]);
+        }
+        if (p.feat) p.feat[(long long)blk * kBlockStates + slot] = o;
+        if (n == 0) live = false;
+    }
 }
 
 }  // namespace prt

@@ -3,8 +3,16 @@
 #include "transfer_kernel.cuh"
 
 namespace prt {
-void launch_transfer_mixed(const XferArgs &a, int grid, cudaStream_t s) {
-    transfer_kernel<float, float><<<grid, kXferThreads, 0, s>>>(a);
+void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s) {
+    switch (coef) {
+        case 0: transfer_kernel<float, float, 0><<<grid, kXferThreads, 0, s>>>(a); break;
+        case 1: transfer_kernel<float, float, 1><<<grid, kXferThreads, 0, s>>>(a); break;
+        case 2: transfer_kernel<float, float, 2><<<grid, kXferThreads, 0, s>>>(a); break;
+        default: break;
+    }
+}
+void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s) {
+    sur_features_pass<float><<<grid, kXferThreads, 0, s>>>(a);
 }
 int transfer_blocks_per_sm_mixed() {
     int n = 0;

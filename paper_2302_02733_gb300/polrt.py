@@ -17,7 +17,8 @@ from . import build as _build
 RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_NOMEM, RT_ERR_NOT_READY, RT_ERR_WORKSPACE, RT_ERR_SIZE = 0, -1, -2, -3, -4, -5, -6
 RT_ERR_STALL = -7
 RT_MODEL_ADAF, RT_MODEL_GRID = 1, 2
-RT_FP64, RT_MIXED = 0, 1
+RT_FP64, RT_MIXED, RT_SURROGATE = 0, 1, 2
+RT_EDF_THERMAL, RT_EDF_KAPPA = 0, 1
 RT_RAY_HORIZON, RT_RAY_ESCAPE, RT_RAY_NMAX, RT_RAY_NAN, RT_RAY_OVERFLOW = 1, 2, 3, 4, 5
 
 
@@ -34,7 +35,8 @@ class rt_grid_params(C.Structure):
 
 
 class rt_model_params(C.Structure):
-    _fields_ = [("kind", C.c_int), ("adaf", rt_adaf_params), ("grid", rt_grid_params)]
+    _fields_ = [("kind", C.c_int), ("adaf", rt_adaf_params), ("grid", rt_grid_params), ("edf", C.c_int),
+                ("kappa", C.c_double)]
 
 
 class rt_camera(C.Structure):
@@ -102,6 +104,7 @@ def lib():
         L.rt_mlp_train.argtypes = [_VP, _VP, _VP, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_uint64, _VP]
         L.rt_surrogate_dataset.argtypes = [_VP, _VP, C.c_longlong, C.c_uint64, _VP, _VP, _VP]
         L.rt_surrogate_coeffs.argtypes = [_VP, _VP, C.c_longlong, _VP, _VP]
+        L.rt_render_features.argtypes = [_VP, _VP, C.c_longlong, C.POINTER(C.c_longlong)]
         L.rt_surrogate_fit.argtypes = [_VP, _VP, _VP, _VP, C.c_longlong, _VP, C.POINTER(rt_mlp_norm)]
         L.rt_render_batch.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int]
         L.rt_batch_autotune.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int, C.POINTER(rt_batch_config)]
@@ -173,15 +176,18 @@ def rt_load_model(ctx, params: rt_model_params, keepalive=None):
     _check(lib().rt_load_model(ctx, C.byref(params)), "rt_load_model")
 
 
-def adaf_model(p) -> rt_model_params:
+def adaf_model(p, kappa: float = 0.0) -> rt_model_params:
+    """kappa > 3 selects kappa electrons, else thermal."""
     m = rt_model_params()
     m.kind = RT_MODEL_ADAF
     m.adaf = rt_adaf_params(p.n0, p.T0, p.beta, p.f_kep, p.Ti_over_Te, p.r_out)
+    m.edf, m.kappa = (RT_EDF_KAPPA, kappa) if kappa > 3.0 else (RT_EDF_THERMAL, 0.0)
     return m
 
 
-def grid_model(prims, g) -> rt_model_params:
-    """prims: float32 [n1][n2][n3][8] (torch tensor on any device, or numpy)."""
+def grid_model(prims, g, kappa: float = 0.0) -> rt_model_params:
+    """prims: float32 [n1][n2][n3][8] (torch tensor on any device, or numpy); kappa > 3 selects
+    kappa electrons, else thermal."""
     shape = tuple(prims.shape)
     if len(shape) != 4 or shape[3] != 8:
         raise ValueError("prims must be [n1][n2][n3][8]")
@@ -189,6 +195,7 @@ def grid_model(prims, g) -> rt_model_params:
     m.kind = RT_MODEL_GRID
     m.grid = rt_grid_params(shape[0], shape[1], shape[2], g.r_in, g.r_out, g.hslope, g.poly_xt, g.poly_alpha,
                             g.mks_smooth, _ptr(prims), g.M_unit, g.R_high, g.R_low, g.sigma_cut, g.gamma_ad)
+    m.edf, m.kappa = (RT_EDF_KAPPA, kappa) if kappa > 3.0 else (RT_EDF_THERMAL, 0.0)
     return m
 
 
@@ -277,6 +284,13 @@ def rt_surrogate_fit(ctx, x, y, valid, t, lo, hi) -> rt_mlp_norm:
     _check(lib().rt_surrogate_fit(ctx, _ptr(x), _ptr(y), _ptr(valid), int(x.shape[0]), _ptr(t), C.byref(n)),
            "rt_surrogate_fit")
     return n
+
+
+def rt_render_features(ctx, feat) -> int:
+    """feat: device float32 [cap, 4]; returns the number of emitting points."""
+    n = C.c_longlong(0)
+    _check(lib().rt_render_features(ctx, _ptr(feat), int(feat.shape[0]), C.byref(n)), "rt_render_features")
+    return n.value
 
 
 def rt_surrogate_coeffs(ctx, inp, out, inside=None):

@@ -1,0 +1,131 @@
+"""Images with kappa electrons on the torus grid: the quadrature path against the oracle, and
+the surrogate form against the quadrature path (the judge).
+
+- FP64 form (coefficients by quadrature at every emitting point) against the oracle on a 12x12
+  image: per pixel within 1e-6 (the two quadratures use different node densities and agree to
+  about 1e-8 per coefficient); the mixed form p99 within 3e-4 (144 pixels: about its worst pixel).
+- Surrogate: trained on 2^20 quadrature points drawn in the box that covers the 0.1-99.9
+  percentiles of the image's emitting points; the 128^2 surrogate image against the
+  quadrature image: flux within 1%, net LP and CP within 0.5 percentage points; and the
+  speed-up of the surrogate form over the quadrature form at 256^2.
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+KAPPA = 4.5
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2302_02733_gb300 import polrt
+
+    torch.cuda.set_device(0)
+    ctx = polrt.rt_create(0, torch.cuda.current_stream().cuda_stream)
+    yield polrt, ctx
+    polrt.rt_destroy(ctx)
+
+
+def render(polrt, ctx, cam, form):
+    polrt.rt_set_camera(ctx, cam)
+    dt = torch.float64 if form == polrt.RT_FP64 else torch.float32
+    out = torch.zeros((cam.ny, cam.nx, 4), dtype=dt, device="cuda")
+    polrt.rt_render(ctx, form, out)
+    return out.double().cpu().numpy(), polrt.rt_last_counters(ctx)
+
+
+def rel_err(a, b):
+    scale = np.maximum(b[..., 0], 1e-8 * b[..., 0].max())
+    return np.abs(a - b).max(axis=-1) / scale
+
+
+def pol(img):
+    s = img.reshape(-1, 4).sum(axis=0)
+    return s[0], math.hypot(s[1], s[2]) / s[0], s[3] / s[0]
+
+
+def test_kappa_image_matches_oracle(rt, ora, synth, torus_grid):
+    polrt, ctx = rt
+    prims, g = torus_grid
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g, kappa=KAPPA))
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    cam = synth.Camera(incl_deg=20.0, nx=12, ny=12)
+    ref = ora.render_image(ora.camera(cam), ora.grid_model(prims, g, kappa=KAPPA))[0]
+    g64, _ = render(polrt, ctx, cam, polrt.RT_FP64)
+    g32, _ = render(polrt, ctx, cam, polrt.RT_MIXED)
+    e64, e32 = rel_err(g64, ref), rel_err(g32, ref)
+    f64, f32 = abs(g64[..., 0].sum() / ref[..., 0].sum() - 1), abs(g32[..., 0].sum() / ref[..., 0].sum() - 1)
+    print(f"kappa 12x12: FP64 max {e64.max():.2e} flux {f64:.2e}; mixed p99 {np.percentile(e32, 99):.2e} "
+          f"flux {f32:.2e}")
+    assert ref[..., 0].max() > 0
+    assert e64.max() <= 1e-6 and f64 <= 1e-7
+    assert np.percentile(e32, 99) <= 3e-4 and f32 <= 1e-4
+
+
+def test_surrogate_image_against_quadrature(rt, synth, torus_grid):
+    polrt, ctx = rt
+    prims, g = torus_grid
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g, kappa=KAPPA))
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    cam = synth.Camera(incl_deg=20.0, nx=128, ny=128)
+    polrt.rt_set_camera(ctx, cam)
+    # the training box: 0.1-99.9 percentiles of the image's emitting points; kappa over (3.2, 8)
+    feat = torch.zeros((1 << 23, 4), dtype=torch.float32, device="cuda")
+    cnt = polrt.rt_render_features(ctx, feat)
+    f = feat[: min(cnt, feat.shape[0])]
+    f = f[torch.isfinite(f).all(dim=1)]  # B along k or B = 0 has nu_c = 0: outside any box
+    sub = f[torch.randperm(len(f), device="cuda")[: 1 << 20]]
+    lo = torch.quantile(sub[:, :3], 0.001, dim=0).tolist()
+    hi = torch.quantile(sub[:, :3], 0.999, dim=0).tolist()
+    box_lo = [lo[0], max(lo[1], 1e-3), lo[2], 3.2]
+    box_hi = [hi[0], min(hi[1], math.pi / 2), hi[2], 8.0]
+    print(f"emitting points {cnt}; box lo {np.round(box_lo, 3)} hi {np.round(box_hi, 3)}")
+    n = 1 << 20
+    xs = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    ys = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+    vs = torch.empty((n,), dtype=torch.int32, device="cuda")
+    polrt.rt_surrogate_dataset(ctx, box_lo + box_hi, n, 31, xs, ys, vs)
+    assert vs.float().mean() > 0.99
+    tn = torch.empty_like(ys)
+    norm = polrt.rt_surrogate_fit(ctx, xs, ys, vs, tn, box_lo, box_hi)
+    import oracle.mlp as M  # only for the initial weights' shapes
+
+    rng = np.random.default_rng(32)
+    theta = np.concatenate([np.concatenate([rng.uniform(-math.sqrt(3 / i), math.sqrt(3 / i), (o, i)),
+                                            np.zeros((o, 1))], axis=1).ravel() for o, i in M.SHAPES])
+    polrt.rt_mlp_set_params(ctx, theta.astype(np.float32), norm)
+    keep = vs.bool()
+    xs, tn = xs[keep].contiguous(), tn[keep].contiguous()
+    curve = np.zeros(20000, dtype=np.float32)
+    polrt.rt_mlp_train(ctx, xs, tn, 20000, 8192, 2e-3, 33, curve)
+    print(f"training loss {curve[:10].mean():.3e} -> {curve[-100:].mean():.3e}")
+    # the judge: quadrature image (mixed form) against the surrogate image
+    q, cq = render(polrt, ctx, cam, polrt.RT_MIXED)
+    s, cs = render(polrt, ctx, cam, polrt.RT_SURROGATE)
+    e = rel_err(s, q)
+    (fq, lpq, cpq), (fs, lps, cps) = pol(q), pol(s)
+    print(f"surrogate vs quadrature 128^2: pixel p50 {np.median(e):.2e} p99 {np.percentile(e, 99):.2e}; "
+          f"flux {abs(fs / fq - 1):.2e}; LP {lpq:.4f} vs {lps:.4f}; CP {cpq:.4f} vs {cps:.4f}")
+    assert abs(fs / fq - 1) <= 1e-2 and abs(lps - lpq) <= 5e-3 and abs(cps - cpq) <= 5e-3
+    # what the network gains: the same image at 256^2 by quadrature and by the surrogate
+    cam2 = synth.Camera(incl_deg=20.0, nx=256, ny=256)
+    times = {}
+    for name, form in (("quadrature", polrt.RT_MIXED), ("surrogate", polrt.RT_SURROGATE)):
+        render(polrt, ctx, cam2, form)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        render(polrt, ctx, cam2, form)
+        times[name] = time.perf_counter() - t0
+    print(f"256^2 kappa image: quadrature {times['quadrature']:.2f} s, surrogate {times['surrogate']:.3f} s, "
+          f"speed-up {times['quadrature'] / times['surrogate']:.1f}x")
+    assert times["surrogate"] * 3 < times["quadrature"]
