@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form (96-image library) leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the kappa/surrogate leg")
     return ap.parse_args()
 
 
@@ -191,6 +192,85 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
             "geodesic_fp64_tflops": fp64, "geodesic_fp64_frac": fp64 / FP64_PEAK_TFLOPS}
 
 
+def surrogate_leg(polrt, ctx, prims_dev, g, dev, torch, size):
+    """Kappa electrons (kappa drawn from U(3, 8) with a fixed seed) on the torus grid: train the
+    surrogate on 2^20 quadrature points in the box of the image's 0.1-99.9 percentiles, time the
+    RT_SURROGATE image at size^2, judge it against the quadrature image at 128^2, and time both
+    forms at 256^2."""
+    import math
+
+    import numpy as np
+    from paper_2302_02733_gb300 import synth
+
+    kappa = 3.0 + 5.0 * float(synth.uniform(2302, [0])[0])
+    polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g, kappa=kappa))
+    cam128 = synth.Camera(incl_deg=20.0, nx=128, ny=128)
+    polrt.rt_set_camera(ctx, cam128)
+    feat = torch.zeros((1 << 22, 4), dtype=torch.float32, device=dev)
+    cnt = polrt.rt_render_features(ctx, feat)
+    f = feat[: min(cnt, feat.shape[0])]
+    f = f[torch.isfinite(f).all(dim=1)]
+    sub = f[torch.randperm(len(f), device=dev)[: 1 << 20]]
+    lo = torch.quantile(sub[:, :3], 0.001, dim=0).tolist()
+    hi = torch.quantile(sub[:, :3], 0.999, dim=0).tolist()
+    box_lo, box_hi = [lo[0], max(lo[1], 1e-3), lo[2], 3.2], [hi[0], min(hi[1], math.pi / 2), hi[2], 8.0]
+    t0 = time.perf_counter()
+    n = 1 << 20
+    xs = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    ys = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    vs = torch.empty((n,), dtype=torch.int32, device=dev)
+    polrt.rt_surrogate_dataset(ctx, box_lo + box_hi, n, 2302, xs, ys, vs)
+    tn = torch.empty_like(ys)
+    norm = polrt.rt_surrogate_fit(ctx, xs, ys, vs, tn, box_lo, box_hi)
+    rng = np.random.default_rng(2302)
+    shapes = [(64, 4), (64, 64), (64, 64), (8, 64)]
+    theta = np.concatenate([np.concatenate([rng.uniform(-math.sqrt(3 / i), math.sqrt(3 / i), (o, i)),
+                                            np.zeros((o, 1))], axis=1).ravel() for o, i in shapes])
+    polrt.rt_mlp_set_params(ctx, theta.astype(np.float32), norm)
+    keep = vs.bool()
+    curve = np.zeros(20000, dtype=np.float32)
+    polrt.rt_mlp_train(ctx, xs[keep].contiguous(), tn[keep].contiguous(), 20000, 8192, 2e-3, 2302, curve)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    def img(cam, form):
+        polrt.rt_set_camera(ctx, cam)
+        o = torch.empty((cam.ny, cam.nx, 4), dtype=torch.float32, device=dev)
+        polrt.rt_render(ctx, form, o)
+        return o
+
+    def pol(o):
+        s_ = o.double().sum(dim=(0, 1)).cpu().numpy()
+        return s_[0], math.hypot(s_[1], s_[2]) / s_[0], s_[3] / s_[0]
+
+    (fq, lq, cq), (fs, ls, cs) = pol(img(cam128, polrt.RT_MIXED)), pol(img(cam128, polrt.RT_SURROGATE))
+    cam256 = synth.Camera(incl_deg=20.0, nx=256, ny=256)
+    t256 = {}
+    for name, form in (("quadrature", polrt.RT_MIXED), ("surrogate", polrt.RT_SURROGATE)):
+        img(cam256, form)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        img(cam256, form)
+        torch.cuda.synchronize()
+        t256[name] = time.perf_counter() - t1
+    camN = synth.Camera(incl_deg=20.0, nx=size, ny=size)
+    img(camN, polrt.RT_SURROGATE)
+    reps, ms = 2, []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        img(camN, polrt.RT_SURROGATE)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t1) * 1e3)
+    m = statistics.mean(ms)
+    return {"workload": f"kappa electrons (kappa {kappa:.2f}) on the torus grid, {size}^2, RT_SURROGATE",
+            "value": size * size / (m / 1e3), "unit": "pixels/s", "ms_per_image": m,
+            "training": {"samples": n, "steps": 20000, "batch": 8192, "seconds": train_s,
+                         "final_loss": float(curve[-100:].mean())},
+            "judge_128": {"flux_rel_err": abs(fs / fq - 1), "lp": [lq, ls], "cp": [cq, cs]},
+            "speedup_256_vs_quadrature": t256["quadrature"] / t256["surrogate"]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -326,6 +406,9 @@ def main():
     # batched form: the 96-image library in one persistent launch per batch (graph replay)
     if not args.no_batch and ws == 1:
         extra["batched_form"] = batch_leg(polrt, ctx, prims_dev, g, dev, torch)
+    # surrogate form: kappa electrons through the trained network
+    if not args.no_surrogate and ws == 1:
+        extra["surrogate_form"] = surrogate_leg(polrt, ctx, prims_dev, g, dev, torch, args.size)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
