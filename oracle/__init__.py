@@ -48,7 +48,7 @@ class Model(C.Structure):
                 ("prims", C.POINTER(C.c_float)),
                 ("M_unit", C.c_double), ("R_high", C.c_double), ("R_low", C.c_double),
                 ("sigma_cut", C.c_double), ("gamma_ad", C.c_double),
-                ("edf", C.c_int), ("kappa", C.c_double)]
+                ("edf", C.c_int), ("kappa", C.c_double), ("unpol_test", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -84,6 +84,8 @@ def lib():
         L.ora_render_pixels.argtypes = [C.POINTER(Camera), C.POINTER(Model), C.c_int, _I, _I, C.c_int,
                                         _D, _I, _I, _D, _D, C.c_int]
         L.ora_render_pixels.restype = C.c_int
+        L.ora_render_unpol.argtypes = [C.POINTER(Camera), C.POINTER(Model), C.c_int, _I, _I, _D, C.c_int]
+        L.ora_render_unpol.restype = C.c_int
         L.ora_image_stats.argtypes = [C.POINTER(Camera), _D, C.c_long, _D, _D, _D]
         _lib = L
     return _lib
@@ -167,6 +169,34 @@ def render_image(cam: Camera, model: ModelHandle, pert: int = 0, nthreads: int =
     if depth:
         out = out + (r[4].reshape(cam.ny, cam.nx, 2),)
     return out
+
+
+def render_unpol(cam: Camera, model: ModelHandle, nthreads: int = 0):
+    """Stokes I image [ny][nx] of the unpolarized transfer (j_I and a_I only)."""
+    iy, ix = np.meshgrid(np.arange(cam.ny), np.arange(cam.nx), indexing="ij")
+    ix = np.ascontiguousarray(ix.ravel(), dtype=np.int32)
+    iy = np.ascontiguousarray(iy.ravel(), dtype=np.int32)
+    out = np.zeros(ix.size)
+    if lib().ora_render_unpol(C.byref(cam), C.byref(model.st), ix.size, _ip(ix), _ip(iy), _dp(out), nthreads) != 0:
+        raise MemoryError("oracle render failed")
+    return out.reshape(cam.ny, cam.nx)
+
+
+def visibilities(cam: Camera, plane: np.ndarray) -> np.ndarray:
+    """V(u, v) = sum over pixels of S dOmega exp(-2 pi i (u x + v y)) [Jy] written out: x, y the
+    pixel-centre angles from the image centre, u = k / FOV and v = l / FOV with
+    k = -nx/2 .. nx/2 - 1 (rows l likewise); the double sum taken as the two matrix products
+    of the separable exponential. plane: [ny][nx] intensities (cgs)."""
+    L = 6.67430e-8 * cam.M_bh_g / 2.99792458e10 ** 2
+    dx = cam.fov_M * L / (cam.nx * cam.dist_cm)  # pixel angle [rad]
+    dy = dx
+    x = (np.arange(cam.nx) + 0.5 - cam.nx / 2) * dx
+    y = (np.arange(cam.ny) + 0.5 - cam.ny / 2) * dy
+    u = (np.arange(cam.nx) - cam.nx // 2) / (cam.nx * dx)
+    v = (np.arange(cam.ny) - cam.ny // 2) / (cam.ny * dy)
+    Ex = np.exp(-2j * np.pi * np.outer(u, x))  # [k][i]
+    Ey = np.exp(-2j * np.pi * np.outer(v, y))  # [l][j]
+    return Ey @ (np.asarray(plane, dtype=np.float64) * dx * dy * 1e23) @ Ex.T
 
 
 def trace_geodesic(cam: Camera, px: float, py: float):

@@ -855,6 +855,8 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
             ora_kappa_coeffs(pl[0], pl[1], pl[2], nu, thB, m->kappa, c8);
         else
             ora_thermal_coeffs(pl[0], pl[1], pl[2], nu, thB, c8);
+        if (m->unpol_test)
+            c8[1] = c8[2] = c8[4] = c8[5] = c8[6] = c8[7] = 0.0;
         double cf[11] = {c8[0], c8[1], 0.0, c8[2], c8[3], c8[4], 0.0, c8[5], c8[6], 0.0, c8[7]};
         double ds = w * h * L;
         /* depths: the exponents of the isotropic absorption and the Faraday rotation that
@@ -895,6 +897,65 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
     stokes_from_N(g, X, Y, N, S);
     pix_out o = {{S[0], S[1], S[2], S[3]}, minpol, tau, phi};
     return o;
+}
+
+/* Unpolarized transfer (Stokes I only, emissivity j_I and absorptivity a_I): I/nu^3 is
+ * invariant along the ray, so each segment multiplies it by e^-tau and adds the segment's
+ * emission (j_I ds / w^3) (1 - e^-tau) / tau, at the arrival point, as in the polarized case. */
+static double transfer_unpol(const ora_camera *cam, const ora_model *m, const double *st, int M) {
+    double a = cam->a, nu_obs = cam->freq_hz, L = O_G * cam->M_bh_g / (O_C * O_C);
+    double Iv = 0.0;
+    for (int n = M - 1; n >= 0; n--) {
+        const double *sn = st + n * 9;
+        double h = fabs(sn[8]);
+        double pl[12];
+        ora_plasma(cam, m, sn, pl);
+        if (pl[3] == 0.0) continue;
+        double g[16];
+        ora_metric_ks(a, sn[1], sn[2], g);
+        const double *K = sn + 4, *u = pl + 4, *b = pl + 8;
+        double w = dot4(g, K, u);
+        double e0[4], e1[4], e2[4], e3[4];
+        double thB = fluid_tetrad(g, K, u, b, e0, e1, e2, e3);
+        double c8[8];
+        ora_thermal_coeffs(pl[0], pl[1], pl[2], w * nu_obs, thB, c8);
+        double ds = w * h * L, tau = c8[3] * ds;
+        double f = tau > 1e-8 ? -expm1(-tau) / tau : 1.0 - 0.5 * tau;
+        Iv = Iv * exp(-tau) + c8[0] * ds / (w * w * w) * f;
+    }
+    return Iv;
+}
+
+int ora_render_unpol(const ora_camera *cam, const ora_model *m, int npix, const int *ix, const int *iy,
+                     double *Iout, int nthreads) {
+    int err = 0;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int maxst = cam->nmax + 2;
+        double *st = (double *)malloc((size_t)maxst * 9 * sizeof(double));
+        if (!st) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = -1;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 2)
+#endif
+            for (int p = 0; p < npix; p++) {
+                double px, py;
+                int stat;
+                pixel_xy(cam, ix[p], iy[p], 0, &px, &py);
+                int M = trace(cam, px, py, maxst, st, &stat);
+                Iout[p] = transfer_unpol(cam, m, st, M);
+            }
+            free(st);
+        }
+    }
+    return err;
 }
 
 int ora_render_pixels(const ora_camera *cam, const ora_model *m, int npix, const int *ix, const int *iy,

@@ -50,6 +50,8 @@ typedef struct {
     /* electron distribution */
     int edf;
     double kappa;
+    /* test switch: keep only j_I and a_I in the polarized transfer (for the unpolarized pin) */
+    int unpol_test;
 } ora_model;
 
 /* geometry */
@@ -91,6 +93,9 @@ void ora_substep(const double coef[11], double ds, const double S0[4], double S1
 int ora_render_pixels(const ora_camera *cam, const ora_model *m, int npix, const int *ix,
                       const int *iy, int pert, double *iquv, int *nsteps, int *status,
                       double *minpol, double *depth, int nthreads);
+/* Stokes I alone with j_I and a_I only (the unpolarized transfer), per listed pixel */
+int ora_render_unpol(const ora_camera *cam, const ora_model *m, int npix, const int *ix, const int *iy,
+                     double *Iout, int nthreads);
 void ora_image_stats(const ora_camera *cam, const double *iquv, long npix, double *flux_jy,
                      double *lp, double *cp);
 

@@ -199,3 +199,24 @@ def test_image_stats_scale_with_distance(ora, synth):
     s = img.reshape(-1, 4).sum(axis=0)
     assert np.isclose(lp, np.hypot(s[1], s[2]) / s[0], rtol=1e-12)
     assert np.isclose(cp, s[3] / s[0], rtol=1e-12)
+
+
+def test_unpolarized_transfer_equals_polarized_without_polarization(ora, synth):
+    """The scalar (Stokes I) transfer against the pinned polarized transfer run with every
+    polarized coefficient set to zero. In exact arithmetic an unpolarized coherency stays
+    unpolarized and its I obeys the scalar equation; the polarized path's Heun propagator is
+    an isometry of the screen only to O(h^3) per step, so the two agree to O(eps^2) and the
+    difference must shrink about four-fold when eps halves."""
+    diffs = []
+    for eps in (0.05, 0.025):
+        cam = ora.camera(synth.Camera(incl_deg=60.0, nx=12, ny=12), eps=eps)
+        m = ora.adaf_model(synth.adaf_params(1))
+        u = ora.render_unpol(cam, m)
+        m.st.unpol_test = 1
+        img = ora.render_image(cam, m)[0]
+        assert u.max() > 0
+        scale = np.maximum(img[..., 0], 1e-8 * img[..., 0].max())
+        diffs.append((np.abs(u - img[..., 0]) / scale).max())
+        # the polarization the transport error creates is of the same order
+        assert np.abs(img[..., 1:]).max() <= 2 * diffs[-1] * img[..., 0].max()
+    assert diffs[0] < 1e-3 and 2.5 < diffs[0] / diffs[1] < 6.0, diffs
