@@ -431,7 +431,7 @@ def main():
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (151 MB grid, multi-GB path arena); no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-                "gpu_launches": args.steps * (2 * chunks + 1), **extra}
+                "gpu_launches": args.steps * (2 * chunks + 2), **extra}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

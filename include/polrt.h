@@ -53,11 +53,15 @@ enum {
                      every step forms its change (screen re-projection, radiative step) as an
                      increment and adds it by an error-free sum, and the optical and Faraday
                      depths are Kahan sums. Output float. */
-    RT_SURROGATE = 2 /* the mixed form with kappa electrons whose coefficients come from the
+    RT_SURROGATE = 2, /* the mixed form with kappa electrons whose coefficients come from the
                         trained surrogate network (rt_mlp_*), evaluated on the tensor cores for
                         every saved state before the transfer; the quadrature answers outside
                         the network's box. Needs model edf RT_EDF_KAPPA and loaded
                         parameters. Output float. */
+    RT_UNPOL = 3      /* Stokes I alone with j_I and a_I only (the unpolarized transfer, for
+                        fitting loops): the FP64 geodesic, then an FP32 scalar transfer with a
+                        compensated sum and no coherency transport. Thermal electrons. Output
+                        nx*ny floats [iy][ix]; rt_image_stats gives the flux (LP = CP = 0). */
 };
 
 /* Per-pixel status codes written to the optional status buffer. */
@@ -248,6 +252,32 @@ int rt_render_features(rt_ctx *ctx, float *feat, long long cap, long long *count
 /* rt_kappa_coeffs through the surrogate: points inside the training box from the network,
  * others from the quadrature (inside[n], optional, tells which). Device pointers. */
 int rt_surrogate_coeffs(rt_ctx *ctx, const double *in, long long n, double *out, uint8_t *inside);
+
+/* Adaptive ray tracing (the paper's outlook: dense rays only near image features). Rays are
+ * traced on a lattice of every base_step-th pixel (a power of two >= 2; last row and column
+ * included); then, halving the side each level, the centre of each block between traced corners
+ * is traced, and the block is refined (edge midpoints traced, children examined) when a Stokes
+ * parameter at the centre differs from the corners' bilinear prediction by more than tol times
+ * the lattice's largest intensity, or when the corner and centre rays ended differently;
+ * otherwise its untraced pixels are filled by bilinear interpolation. Features smaller than
+ * base_step that no lattice or centre ray touches are missed: choose base_step below the
+ * smallest feature of interest. out (and
+ * status, optional) are device buffers in rt_render's layout for form RT_FP64, RT_MIXED or
+ * RT_UNPOL; every pixel is written. *rays_traced (optional) receives the number of rays
+ * traced. Synchronizes. */
+int rt_render_adaptive(rt_ctx *ctx, int form, void *out, uint8_t *status, int base_step, double tol,
+                       long long *rays_traced);
+
+/* Visibilities of one Stokes plane of an image (Section 2.1: power-of-two images are Fourier
+ * transformed to the interferometer's visibilities without regridding):
+ *   V(u, v) = sum over pixels of S(x, y) dOmega e^{-2 pi i (u x + v y)}   [Jy],
+ * x, y the pixel-centre angles [rad] from the image centre (x along +e_phi, y along -e_theta),
+ * dOmega the pixel solid angle, on the grid u = k / FOV, v = l / FOV (FOV in radians),
+ * k = -nx/2 .. nx/2 - 1, l = -ny/2 .. ny/2 - 1. img: an image of the current camera in
+ * `form` layout (host or device); stokes: 0..3 for I, Q, U, V (0 only for RT_UNPOL). vis:
+ * nx*ny complex values [l + ny/2][k + nx/2] as (re, im) pairs of double (RT_FP64) or float,
+ * host or device. A cuFFT transform of any size; synchronizes. */
+int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, void *vis);
 
 /* Counters of the last rt_render (synchronizes). */
 int rt_last_counters(rt_ctx *ctx, rt_counters *out);

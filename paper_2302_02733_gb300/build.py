@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if log:
                 print(log)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs]
+        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs, "-lcufft"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "host_util.cuh"
 #include "kappa.cuh"
@@ -70,7 +71,7 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     c->mixed_bps = transfer_blocks_per_sm_mixed();
     c->pipe_bps[0] = pipe_blocks_per_sm_fp64();
     c->pipe_bps[1] = pipe_blocks_per_sm_mixed();
-    bool ok = cudaMalloc(&c->d_stats, 8 * sizeof(double)) == cudaSuccess &&
+    bool ok = cudaMalloc(&c->d_stats, (8 + 4 * kStatBlocks) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->d_sctab, kSinTabBytes) == cudaSuccess &&
               cudaMalloc(&c->d_syn, kSynTabBytes) == cudaSuccess && cudaMalloc(&c->d_gl, 16 * sizeof(double)) == cudaSuccess &&
               cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess &&
@@ -99,6 +100,8 @@ int rt_destroy(rt_ctx *c) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->d_prims);
     cudaFree(c->d_x2);
+    cudaFree(c->d_x2f);
+    cudaFree(c->d_x1c);
     if (c->ws_owned) cudaFree(c->ws);
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
@@ -168,10 +171,29 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
         cudaMemcpyKind kind = is_device_ptr(g.prims) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         CK(cudaMemcpyAsync(c->d_prims, g.prims, bytes, kind, c->stream));
         if (!c->d_x2) {
-            if (cudaMalloc(&c->d_x2, sizeof(double) * kX2TabW * kX2TabT) != cudaSuccess) {
+            if (cudaMalloc(&c->d_x2, sizeof(double) * kX2TabW * kX2TabT) != cudaSuccess ||
+                cudaMalloc(&c->d_x2f, sizeof(float) * kX2TabW * kX2TabT) != cudaSuccess) {
                 cudaGetLastError();
                 return RT_ERR_NOMEM;
             }
+        }
+        if (c->x1c_n != g.n1) {
+            cudaFree(c->d_x1c);
+            c->d_x1c = nullptr;
+            c->x1c_n = 0;
+            if (cudaMalloc(&c->d_x1c, sizeof(double) * g.n1) != cudaSuccess) {
+                cudaGetLastError();
+                return RT_ERR_NOMEM;
+            }
+            c->x1c_n = g.n1;
+        }
+        {
+            // the same X1_in and dx1 as the fetch (make_model)
+            double x1in = std::log(g.r_in), dx1 = (std::log(g.r_out) - x1in) / g.n1;
+            std::vector<double> irc(g.n1);
+            for (int i = 0; i < g.n1; i++) irc[i] = std::exp(-(x1in + (i + 0.5) * dx1));
+            CK(cudaMemcpyAsync(c->d_x1c, irc.data(), sizeof(double) * g.n1, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
         }
         GridModel gm{};
         gm.hslope = g.hslope;
@@ -179,7 +201,7 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
         gm.poly_alpha = g.poly_alpha;
         gm.mks_smooth = g.mks_smooth;
         gm.poly_norm = 0.5 * kPi / (1.0 + 1.0 / ((g.poly_alpha + 1.0) * std::pow(g.poly_xt, g.poly_alpha)));
-        launch_x2_table(gm, c->d_x2, c->stream);
+        launch_x2_table(gm, c->d_x2, c->d_x2f, c->stream);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->stream));
     } else {
@@ -252,18 +274,24 @@ static int ensure_stage(void **buf, size_t *have, size_t need) {
     return RT_OK;
 }
 
-static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *depth) {
-    if (!c || !out_iquv || (form != RT_FP64 && form != RT_MIXED && form != RT_SURROGATE)) return RT_ERR_INVALID;
+static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *depth, const int *list = nullptr,
+                       long long nlist = 0) {
+    if (!c || !out_iquv || form < RT_FP64 || form > RT_UNPOL) return RT_ERR_INVALID;
+    if (form == RT_UNPOL && depth) return RT_ERR_INVALID;
     if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
     CK(cudaSetDevice(c->device));
     const rt_camera &rc = c->cam;
-    long long nrays = (long long)rc.nx * rc.ny;
+    long long nrays = list ? nlist : (long long)rc.nx * rc.ny;
+    if (nrays == 0) return RT_OK;
+    const long long npix_img = (long long)rc.nx * rc.ny;
 
     // camera and model in kernel form
     Camera cam = make_camera(rc, c->eps, c->nmax);
     Model mod = make_model(c, cam);
     const bool sur = form == RT_SURROGATE;
     if (sur && (mod.edf != RT_EDF_KAPPA || !c->have_mlp)) return RT_ERR_NOT_READY;
+    if (form == RT_UNPOL && mod.edf != RT_EDF_THERMAL) return RT_ERR_INVALID;
+    const size_t ncomp = form == RT_UNPOL ? 1 : 4;  // values per pixel
     const int coef = mod.edf != RT_EDF_KAPPA ? 0 : (sur ? 2 : 1);
 
     // workspace carving; the surrogate form adds, per saved state, the network's inputs and
@@ -301,19 +329,19 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     void *d_out = out_iquv;
     uint8_t *d_status = status;
     if (!out_dev) {
-        rv = ensure_stage(&c->d_stage, &c->stage_bytes, (size_t)nrays * 4 * esz);
+        rv = ensure_stage(&c->d_stage, &c->stage_bytes, (size_t)npix_img * ncomp * esz);
         if (rv) return rv;
         d_out = c->d_stage;
     }
     if (status && !st_dev) {
-        rv = ensure_stage((void **)&c->d_stage_status, &c->stage_status_bytes, (size_t)nrays);
+        rv = ensure_stage((void **)&c->d_stage_status, &c->stage_status_bytes, (size_t)npix_img);
         if (rv) return rv;
         d_status = c->d_stage_status;
     }
     bool dep_dev = depth ? is_device_ptr(depth) : true;
     void *d_depth = depth;
     if (depth && !dep_dev) {
-        rv = ensure_stage(&c->d_stage_depth, &c->stage_depth_bytes, (size_t)nrays * 2 * esz);
+        rv = ensure_stage(&c->d_stage_depth, &c->stage_depth_bytes, (size_t)npix_img * 2 * esz);
         if (rv) return rv;
         d_depth = c->d_stage_depth;
     }
@@ -325,7 +353,9 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         long long n = std::min(chunk, nrays - o);
         CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));  // queues + arena
         GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
+        ga.pix_list = list;
         XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
+        xa.pix_list = list;
         xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
         if (sur) {
             xa.feat = feat;
@@ -354,16 +384,18 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
         if (form == RT_FP64)
             launch_transfer_fp64(xa, coef, xf_grid, c->stream);
+        else if (form == RT_UNPOL)
+            launch_unpol(xa, xf_grid, c->stream);
         else
             launch_transfer_mixed(xa, coef, xf_grid, c->stream);
         CK(cudaGetLastError());
     }
     CK(cudaEventRecord(c->ev[2], c->stream));
-    if (!out_dev) CK(cudaMemcpyAsync(out_iquv, d_out, (size_t)nrays * 4 * esz, cudaMemcpyDeviceToHost, c->stream));
+    if (!out_dev) CK(cudaMemcpyAsync(out_iquv, d_out, (size_t)npix_img * ncomp * esz, cudaMemcpyDeviceToHost, c->stream));
     if (status && !st_dev)
-        CK(cudaMemcpyAsync(status, d_status, (size_t)nrays, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(status, d_status, (size_t)npix_img, cudaMemcpyDeviceToHost, c->stream));
     if (depth && !dep_dev)
-        CK(cudaMemcpyAsync(depth, d_depth, (size_t)nrays * 2 * esz, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(depth, d_depth, (size_t)npix_img * 2 * esz, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->last_rays = nrays;
@@ -422,27 +454,39 @@ int rt_render(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     return render_impl(c, form, out_iquv, status, nullptr);
 }
 
+}  // extern "C"
+
+namespace prt {
+// Render only the listed pixels (device list of iy nx + ix) into the full-size device outputs.
+int render_pixel_list(rt_ctx *c, int form, void *out, uint8_t *status, const int *list, long long n) {
+    return render_impl(c, form, out, status, nullptr, list, n);
+}
+}  // namespace prt
+
+extern "C" {
+
 int rt_render_depths(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *out_depth) {
     if (!out_depth) return RT_ERR_INVALID;
     return render_impl(c, form, out_iquv, status, out_depth);
 }
 
 int rt_image_stats(rt_ctx *c, const void *iquv, int form, double *flux_jy, double *lp_frac, double *cp_frac) {
-    if (!c || !iquv || (form != RT_FP64 && form != RT_MIXED && form != RT_SURROGATE)) return RT_ERR_INVALID;
+    if (!c || !iquv || form < RT_FP64 || form > RT_UNPOL) return RT_ERR_INVALID;
     if (!c->have_cam) return RT_ERR_NOT_READY;
     CK(cudaSetDevice(c->device));
     long long npix = (long long)c->cam.nx * c->cam.ny;
     size_t esz = form == RT_FP64 ? sizeof(double) : sizeof(float);
+    size_t ncomp = form == RT_UNPOL ? 1 : 4;
     const void *d_img = iquv;
     if (!is_device_ptr(iquv)) {
-        int rv = ensure_stage(&c->d_stage, &c->stage_bytes, (size_t)npix * 4 * esz);
+        int rv = ensure_stage(&c->d_stage, &c->stage_bytes, (size_t)npix * ncomp * esz);
         if (rv) return rv;
-        CK(cudaMemcpyAsync(c->d_stage, iquv, (size_t)npix * 4 * esz, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->d_stage, iquv, (size_t)npix * ncomp * esz, cudaMemcpyHostToDevice, c->stream));
         d_img = c->d_stage;
     }
     double L = kG * c->cam.M_bh_g / (kC * kC);
     double pix = c->cam.fov_M * L / (c->cam.nx * c->cam.dist_cm);
-    launch_image_sums(d_img, form == RT_FP64 ? 0 : 1, npix, pix * pix, c->d_stats, c->stream);
+    launch_image_sums(d_img, form == RT_FP64 ? 0 : (form == RT_UNPOL ? 2 : 1), npix, pix * pix, c->d_stats, c->stream);
     CK(cudaGetLastError());
     double h[8];
     CK(cudaMemcpyAsync(h, c->d_stats, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             if (t < (unsigned long long)p.nrays) {
                 ray = (long long)t;
                 int ix, iy;
-                ray_pixel(ray + p.ray_offset, c.nx, c.ny, ix, iy);
+                map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
                 ray_start(c, ix, iy, y);
                 n = 0;
                 blk = -1;

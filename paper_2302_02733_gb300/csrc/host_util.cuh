@@ -47,6 +47,9 @@ inline Camera make_camera(const rt_camera &rc, double eps, int nmax) {
     cam.eps = eps;
     cam.nmax = nmax;
     cam.rh = 1.0 + std::sqrt(1.0 - rc.a * rc.a);
+    cam.f_a = (float)cam.a;
+    cam.f_nu_obs = (float)cam.nu_obs;
+    cam.f_L_unit = (float)cam.L_unit;
     return cam;
 }
 
@@ -59,7 +62,22 @@ inline Model make_model(const rt_ctx *c, const Camera &cam, double M_unit = 0.0,
     mod.kappa = c->model.kappa;
     if (mod.kind == RT_MODEL_ADAF) {
         const rt_adaf_params &a = c->model.adaf;
-        mod.adaf = AdafModel{a.n0, a.T0, a.beta, a.f_kep, a.Ti_over_Te, a.r_out, r_isco(cam.a)};
+        AdafModel &m = mod.adaf;
+        m.n0 = a.n0;
+        m.T0 = a.T0;
+        m.beta = a.beta;
+        m.f_kep = a.f_kep;
+        m.ti_te = a.Ti_over_Te;
+        m.r_out = a.r_out;
+        m.r_isco = r_isco(cam.a);
+        m.te0 = a.T0 * kKb / (kMe * kC * kC);
+        m.b0 = std::sqrt(8.0 * kPi * a.n0 * kKb * a.T0 * (1.0 + a.Ti_over_Te) / a.beta);
+        m.f_n0 = (float)m.n0;
+        m.f_te0 = (float)m.te0;
+        m.f_b0 = (float)m.b0;
+        m.f_f_kep = (float)m.f_kep;
+        m.f_r_out = (float)m.r_out;
+        m.f_r_isco = (float)m.r_isco;
     } else {
         const rt_grid_params &g = c->model.grid;
         GridModel &gm = mod.grid;
@@ -79,6 +97,8 @@ inline Model make_model(const rt_ctx *c, const Camera &cam, double M_unit = 0.0,
         gm.poly_norm = 0.5 * kPi / (1.0 + 1.0 / ((g.poly_alpha + 1.0) * std::pow(g.poly_xt, g.poly_alpha)));
         gm.prims = reinterpret_cast<const float4 *>(c->d_prims);
         gm.x2_table = c->d_x2;
+        gm.x1_irc = c->d_x1c;
+        gm.idx3 = g.n3 / (2.0 * kPi);
         double L = cam.L_unit;
         gm.rho_unit = (M_unit > 0.0 ? M_unit : g.M_unit) / (L * L * L);
         gm.b_unit = kC * std::sqrt(4.0 * kPi * gm.rho_unit);
@@ -87,6 +107,25 @@ inline Model make_model(const rt_ctx *c, const Camera &cam, double M_unit = 0.0,
         gm.R_low = g.R_low;
         gm.sigma_cut = g.sigma_cut;
         gm.gamma_ad = g.gamma_ad;
+        gm.x2_table_f = c->d_x2f;
+        gm.f_r_in = (float)gm.r_in;
+        gm.f_r_out = (float)gm.r_out;
+        gm.f_x1in = (float)gm.x1in;
+        gm.f_dx1 = (float)gm.dx1;
+        gm.f_dx2 = (float)gm.dx2;
+        gm.f_dx3 = (float)gm.dx3;
+        gm.f_hslope = (float)gm.hslope;
+        gm.f_poly_xt = (float)gm.poly_xt;
+        gm.f_poly_alpha = (float)gm.poly_alpha;
+        gm.f_poly_alpha1 = (float)(gm.poly_alpha + 1.0);
+        gm.f_poly_norm = (float)gm.poly_norm;
+        gm.f_mks_smooth = (float)gm.mks_smooth;
+        gm.f_b_unit = (float)gm.b_unit;
+        gm.f_ne_unit = (float)gm.ne_unit;
+        gm.f_R_high = (float)gm.R_high;
+        gm.f_R_low = (float)gm.R_low;
+        gm.f_sigma_cut = (float)gm.sigma_cut;
+        gm.f_gamma_ad = (float)gm.gamma_ad;
     }
     return mod;
 }

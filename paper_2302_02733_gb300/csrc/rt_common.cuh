@@ -34,10 +34,14 @@ struct Camera {
     double eps;
     int nmax;
     double rh;             // outer horizon radius
+    float f_a, f_nu_obs, f_L_unit;  // float copies for the FP32 transfer (no per-point conversion)
 };
 
 struct AdafModel {
     double n0, T0, beta, f_kep, ti_te, r_out, r_isco;
+    // derived on the host: Theta_e and B at r = 1 (T_e = te0 / r, B = b0 r^-5/4)
+    double te0, b0;
+    float f_n0, f_te0, f_b0, f_f_kep, f_r_out, f_r_isco;
 };
 
 struct GridModel {
@@ -46,8 +50,27 @@ struct GridModel {
     double hslope, poly_xt, poly_alpha, mks_smooth, poly_norm;
     const float4 *prims;   // [n1][n2][n3] cells of two float4: (rho,u,U1,U2),(U3,B1,B2,B3)
     const double *x2_table;  // inverse FMKS guess table [kX2TabW][kX2TabT]
+    const double *x1_irc;    // 1 / r at the radial cell centres [n1]
+    double idx3;             // 1 / dx3
     double rho_unit, b_unit, ne_unit, R_high, R_low, sigma_cut, gamma_ad;
+    // float copies for the FP32 transfer (no per-point conversion); poly_alpha1 = poly_alpha + 1
+    const float *x2_table_f;
+    float f_r_in, f_r_out, f_x1in, f_dx1, f_dx2, f_dx3, f_hslope, f_poly_xt, f_poly_alpha, f_poly_alpha1, f_poly_norm,
+        f_mks_smooth, f_b_unit, f_ne_unit, f_R_high, f_R_low, f_sigma_cut, f_gamma_ad;
 };
+
+// The constant of the transfer's precision: the double for the FP64 form, the float copy for
+// the FP32 form.
+template <typename R>
+__host__ __device__ __forceinline__ R pick(double d, float f);
+template <>
+__host__ __device__ __forceinline__ double pick<double>(double d, float) {
+    return d;
+}
+template <>
+__host__ __device__ __forceinline__ float pick<float>(double, float f) {
+    return f;
+}
 constexpr int kX2TabW = 64;     // blend weight w = exp(s (X1_in - X1)) in [0, 1]
 constexpr int kX2TabT = 1024;   // theta in [0, pi]
 
@@ -115,6 +138,18 @@ __device__ __forceinline__ void ray_pixel(long long id, int nx, int ny, int &ix,
     } else {
         ix = (int)(id % nx);
         iy = (int)(id / nx);
+    }
+}
+
+// Pixel of ray id: from an explicit pixel list (p = iy nx + ix) when one is given (adaptive
+// rendering), else the 8x4-tiled order.
+__device__ __forceinline__ void map_pixel(const int *list, long long id, int nx, int ny, int &ix, int &iy) {
+    if (list) {
+        int p = list[id];
+        ix = p % nx;
+        iy = p / nx;
+    } else {
+        ray_pixel(id, nx, ny, ix, iy);
     }
 }
 

@@ -16,6 +16,9 @@ struct rt_ctx {
     float *d_prims = nullptr;
     size_t prims_bytes = 0;
     double *d_x2 = nullptr;
+    float *d_x2f = nullptr;     // float copy of the FMKS inverse table
+    double *d_x1c = nullptr;    // 1 / r at the radial cell centres
+    int x1c_n = 0;
     double eps = 0.05;
     int nmax = 20000;
     void *ws = nullptr;

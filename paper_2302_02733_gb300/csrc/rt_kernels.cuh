@@ -15,6 +15,7 @@ struct GeoArgs {
     Counters *ctr;
     long long nrays;      // rays in this chunk
     long long ray_offset; // global id of the chunk's first ray
+    const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering)
 };
 
 struct XferArgs {
@@ -37,6 +38,7 @@ struct XferArgs {
     float4 *feat;         // features pass: network inputs per saved state
     float4 *feat_raw;     // or (rt_render_features) raw inputs of the emitting points, compacted
     long long feat_cap;
+    const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering)
 };
 
 // ---- batched rendering: many images in one persistent launch ----------------------------
@@ -104,9 +106,12 @@ constexpr size_t kSinTabBytes = 2048 * 3 * sizeof(double);
 void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s);
 void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s);
 void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s);
+void launch_unpol(const XferArgs &a, int grid, cudaStream_t s);  // Stokes I only, FP32
 void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s);
-void launch_x2_table(const GridModel &g, double *table, cudaStream_t s);
-// out[7]: sum I, Q, U, V, flux [Jy], net LP, net CP
+void launch_x2_table(const GridModel &g, double *table, float *table_f, cudaStream_t s);
+// out[7]: sum I, Q, U, V, flux [Jy], net LP, net CP; out holds 8 + 4 kStatBlocks doubles
+constexpr int kStatBlocks = 608;
+// form: 0 double IQUV, 1 float IQUV, 2 float I only
 void launch_image_sums(const void *img, int form, long long npix, double domega, double *out, cudaStream_t s);
 // resident blocks per SM of the persistent kernels (for grid sizing)
 int geodesic_blocks_per_sm();

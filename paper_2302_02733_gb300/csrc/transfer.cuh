@@ -210,6 +210,32 @@ __device__ __forceinline__ void thermal_coeffs(R ne, R Te, R B, R nu, R sth, R c
     out[5] = jV * iB;
 }
 
+// j_I and a_I alone (the unpolarized transfer): the same fit and Kirchhoff's law as
+// thermal_coeffs, without the rotativities (and so without the Bessel functions).
+template <typename R>
+__device__ __forceinline__ void thermal_jI_aI(R ne, R Te, R B, R nu, R sth, R &jI, R &aI) {
+    typedef Mth<R> F;
+    jI = aI = R(0);
+    if (!(ne > R(0)) || !(Te > R(0)) || !(B > R(0)) || sth < R(1e-12)) return;
+    const R cB = R(kQe / (2.0 * kPi * kMe * kC));
+    const R cJ = R(kQe * kQe / (2.0 * 1.7320508075688772 * kC));
+    const R cT = R(kH / (kMe * kC * kC));
+    const R c2h = R(2.0 * kH);
+    const R ic = R(1.0 / kC);
+    R nuB = cB * B;
+    R nuc = R(1.5) * nuB * sth * Te * Te;
+    R x = nu / nuc;
+    R x13 = F::cbrt_(x), ix13 = R(1) / x13, ix23 = ix13 * ix13;
+    R ex = F::exp_(R(-1.8899) * x13);
+    R pre = cJ * ne * nu / (Te * Te);
+    R j = pre * R(2.5651) * (R(1) + R(1.92) * ix13 + R(0.9977) * ix23) * ex;
+    if (!(j > F::jflush)) return;
+    R nuic = nu * ic;
+    R Bnu = c2h * nu * nuic * nuic / F::expm1_(cT * nu / Te);
+    jI = j;
+    aI = j * (R(1) / Bnu);
+}
+
 // ------------------------------------------------------------------------------------------
 // Exact constant-coefficient step of dS/ds = J - M S over ds (M as in the transfer matrix
 // with j_U = a_U = r_U = 0): S <- exp(-M ds) S + (int_0^ds exp(-M v) dv) J.
@@ -459,12 +485,12 @@ template <typename R>
 __device__ __forceinline__ void adaf_plasma(const AdafModel &p, R a, const KS<R> &m, R r, Plasma<R> &o) {
     typedef Mth<R> F;
     o.valid = false;
-    if (r > R(p.r_out)) return;
+    if (r > pick<R>(p.r_out, p.f_r_out)) return;
     R ir = R(1) / r;
     R r15 = ir * F::rsqrt_(r);
-    o.ne = R(p.n0) * r15;
-    o.Te = R(p.T0 * kKb / (kMe * kC * kC)) * ir;
-    o.B = R(sqrt(8.0 * kPi * p.n0 * kKb * p.T0 * (1.0 + p.ti_te) / p.beta)) * F::sqrt_(r15 * ir);
+    o.ne = pick<R>(p.n0, p.f_n0) * r15;
+    o.Te = pick<R>(p.te0, p.f_te0) * ir;
+    o.B = pick<R>(p.b0, p.f_b0) * F::sqrt_(r15 * ir);
     // Boyer-Lindquist inverse metric pieces
     R a2 = a * a, s2 = m.s2;
     R del = r * r - R(2) * r + a2;
@@ -474,10 +500,10 @@ __device__ __forceinline__ void adaf_plasma(const AdafModel &p, R a, const KS<R>
     R gtt = -A * isd, gtp = -R(2) * a * r * isd, gpp = (del - a2 * s2) * isd / s2, grr = del * m.isig;
     // -1 - g^tt = (A - Sigma Delta)/(Sigma Delta) = 2r (r^2 + a^2)/(Sigma Delta): no cancellation
     R m1_gtt = R(2) * r * rr2 * isd;
-    R rk = fmax(r, R(p.r_isco));
+    R rk = fmax(r, pick<R>(p.r_isco, p.f_r_isco));
     R sq = F::sqrt_(rk);
     R lK = (rk * rk - R(2) * a * sq + a2) / (rk * sq - R(2) * sq + a);
-    R l = R(p.f_kep) * lK * s2;
+    R l = pick<R>(p.f_kep, p.f_f_kep) * lK * s2;
     R rhs = m1_gtt + R(2) * gtp * l - gpp * l * l;
     R ur_low = -F::sqrt_(fmax(rhs, R(0)) / grr);
     R u[4];
@@ -499,70 +525,114 @@ __device__ __forceinline__ void adaf_plasma(const AdafModel &p, R a, const KS<R>
     o.valid = true;
 }
 
-// FMKS polar angle theta(X2) at blend weight w = exp(s (X1_in - X1)), and d/dX2.
+// FMKS polar angle in offset form: mu = theta - pi/2 as a function of y = X2 - 1/2, at blend
+// weight w = exp(s (X1_in - X1)); also d theta / d X2 and theta_j - theta_g. With x2 = 1/2 + y,
+// sin(2 pi x2) = -sin(2 pi y) and cos(2 pi x2) = -cos(2 pi y), so every term is small near the
+// equator and an FP32 evaluation keeps the relative precision of mu there.
 template <typename R>
-__device__ __forceinline__ R fmks_theta_w(const GridModel &g, R w, R x2, R *dth2, R *thj_m_thg) {
+__device__ __forceinline__ R fmks_mu(const GridModel &g, R w, R y, R *dth2, R *thj_m_thg) {
     typedef Mth<R> F;
     R s2p, c2p;
-    F::sincos_(R(2 * kPi) * x2, &s2p, &c2p);
-    R omh = R(1) - R(g.hslope);
-    R thg = R(kPi) * x2 + R(0.5) * omh * s2p;
-    R dthg = R(kPi) * (R(1) + omh * c2p);
-    R y = R(2) * x2 - R(1);
-    R yx = y / R(g.poly_xt);
-    R ya = F::pow_(fabs(yx), R(g.poly_alpha));
-    R N = R(g.poly_norm);
-    R thj = N * y * (R(1) + ya / R(g.poly_alpha + 1.0)) + R(0.5 * kPi);
+    F::sincos_(R(2 * kPi) * y, &s2p, &c2p);
+    R omh = R(1) - pick<R>(g.hslope, g.f_hslope);
+    R mug = R(kPi) * y - R(0.5) * omh * s2p;  // theta_g - pi/2
+    R dthg = R(kPi) * (R(1) - omh * c2p);
+    R yp = R(2) * y;                          // 2 X2 - 1
+    R yx = yp / pick<R>(g.poly_xt, g.f_poly_xt);
+    R ya = F::pow_(fabs(yx), pick<R>(g.poly_alpha, g.f_poly_alpha));
+    R N = pick<R>(g.poly_norm, g.f_poly_norm);
+    R muj = N * yp * (R(1) + ya / pick<R>(g.poly_alpha + 1.0, g.f_poly_alpha1));  // theta_j - pi/2
     R dthj = R(2) * N * (R(1) + ya);
     if (dth2) *dth2 = dthg + w * (dthj - dthg);
-    if (thj_m_thg) *thj_m_thg = thj - thg;
-    return thg + w * (thj - thg);
+    if (thj_m_thg) *thj_m_thg = muj - mug;
+    return mug + w * (muj - mug);
 }
 
+// FMKS polar angle theta(X2) at blend weight w, and d/dX2.
 template <typename R>
-__device__ __forceinline__ R fmks_x2(const GridModel &g, R w, R th) {
-    // table guess in (w, theta), then Newton
+__device__ __forceinline__ R fmks_theta_w(const GridModel &g, R w, R x2, R *dth2, R *thj_m_thg) {
+    return R(0.5 * kPi) + fmks_mu(g, w, x2 - R(0.5), dth2, thj_m_thg);
+}
+
+// y = X2 - 1/2 of the point at polar angle th (mu = th - pi/2, formed before rounding to R):
+// a table guess in (w, theta), then Newton on mu.
+template <typename R>
+__device__ __forceinline__ R fmks_y(const GridModel &g, R w, R th, R mu) {
     R fw = w * R(kX2TabW - 1);
     int iw = min(max((int)fw, 0), kX2TabW - 2);
     R tw = fw - R(iw);
     R ft = th * R((kX2TabT - 1) / kPi);
     int it = min(max((int)ft, 0), kX2TabT - 2);
     R tt = ft - R(it);
-    const double *T = g.x2_table;
-    R x00 = R(T[iw * kX2TabT + it]), x01 = R(T[iw * kX2TabT + it + 1]);
-    R x10 = R(T[(iw + 1) * kX2TabT + it]), x11 = R(T[(iw + 1) * kX2TabT + it + 1]);
-    R x2 = (R(1) - tw) * ((R(1) - tt) * x00 + tt * x01) + tw * ((R(1) - tt) * x10 + tt * x11);
+    R x00, x01, x10, x11;
+    if (sizeof(R) == 8) {
+        const double *T = g.x2_table;
+        x00 = R(T[iw * kX2TabT + it]), x01 = R(T[iw * kX2TabT + it + 1]);
+        x10 = R(T[(iw + 1) * kX2TabT + it]), x11 = R(T[(iw + 1) * kX2TabT + it + 1]);
+    } else {
+        const float *T = g.x2_table_f;
+        x00 = R(T[iw * kX2TabT + it]), x01 = R(T[iw * kX2TabT + it + 1]);
+        x10 = R(T[(iw + 1) * kX2TabT + it]), x11 = R(T[(iw + 1) * kX2TabT + it + 1]);
+    }
+    R y = (R(1) - tw) * ((R(1) - tt) * x00 + tt * x01) + tw * ((R(1) - tt) * x10 + tt * x11) - R(0.5);
     const int iters = sizeof(R) == 8 ? 3 : 2;
 #pragma unroll
     for (int k = 0; k < iters; k++) {
         R d;
-        R f = fmks_theta_w(g, w, x2, &d, (R *)nullptr) - th;
-        x2 -= f / d;
+        R f = fmks_mu(g, w, y, &d, (R *)nullptr) - mu;
+        y -= f / d;
     }
-    return fmin(fmax(x2, R(0)), R(1));
+    return fmin(fmax(y, R(-0.5)), R(0.5));
 }
 
+// Corner index and fraction of one axis of the trilinear fetch, from an approximate cell
+// coordinate (within one cell of the truth) and the exact fraction relative to that corner;
+// clamped to the first and last cell centres.
 template <typename R>
-__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, R r, R th, R ph, Plasma<R> &o) {
+__device__ __forceinline__ void cell_axis(int n, int &i0, R &f) {
+    if (f < R(0) && i0 > 0) {
+        i0--;
+        f += R(1);
+    } else if (f >= R(1) && i0 < n - 2) {
+        i0++;
+        f -= R(1);
+    }
+    if (i0 < 0) i0 = 0, f = R(0);
+    if (i0 > n - 2) i0 = n - 2, f = R(1);
+    f = fmin(fmax(f, R(0)), R(1));
+}
+
+// Plasma state of the FMKS grid at (r, theta, phi). The trilinear fractions are formed from
+// FP64 differences to a cell centre (r / r_c - 1, theta - pi/2 of the equator, phi / dx3 minus
+// its floor) before rounding to R: on a grid with structure from cell to cell, a fraction taken
+// from the absolute FP32 coordinates (X1 up to ln r_out, the cell index up to n) is off by
+// 1e-5 of a cell, which the steep thermal emissivity magnifies about twentyfold.
+template <typename R>
+__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, double rd, double thd, double phd,
+                                            Plasma<R> &o) {
     typedef Mth<R> F;
     o.valid = false;
-    if (r < R(g.r_in) || r > R(g.r_out)) return;
+    R r = R(rd), th = R(thd);
+    if (r < pick<R>(g.r_in, g.f_r_in) || r > pick<R>(g.r_out, g.f_r_out)) return;
     R X1 = F::log_(r);
-    R w = F::exp_(R(g.mks_smooth) * (R(g.x1in) - X1));
-    R X2 = fmks_x2(g, w, th);
-    R X3 = F::fmod_(ph, R(2.0 * kPi));
-    if (X3 < R(0)) X3 += R(2.0 * kPi);
-    R fi = (X1 - R(g.x1in)) / R(g.dx1) - R(0.5);
-    R fj = X2 / R(g.dx2) - R(0.5);
-    R fk = X3 / R(g.dx3) - R(0.5);
-    fi = fmin(fmax(fi, R(0)), R(g.n1 - 1));
-    fj = fmin(fmax(fj, R(0)), R(g.n2 - 1));
-    int i0 = min((int)fi, g.n1 - 2), j0 = min((int)fj, g.n2 - 2);
-    R w1 = fi - R(i0), w2 = fj - R(j0);
-    R kf = F::floor_(fk);
-    R w3 = fk - kf;
-    int k0 = (int)kf;
-    k0 = ((k0 % g.n3) + g.n3) % g.n3;
+    R w = F::exp_(pick<R>(g.mks_smooth, g.f_mks_smooth) * (pick<R>(g.x1in, g.f_x1in) - X1));
+    // radial: corner from the approximate X1, fraction ln(r / r_c) / dx1 about that centre
+    int i0 = (int)F::floor_((X1 - pick<R>(g.x1in, g.f_x1in)) / pick<R>(g.dx1, g.f_dx1) - R(0.5));
+    i0 = min(max(i0, 0), g.n1 - 2);
+    R w1 = F::log1p_(R(rd * g.x1_irc[i0] - 1.0)) / pick<R>(g.dx1, g.f_dx1);
+    cell_axis(g.n1, i0, w1);
+    // polar: y = X2 - 1/2; fj = y n2 + (n2 - 1)/2, fraction about the half-integer j0 - (n2 - 1)/2
+    R y = fmks_y(g, w, th, R(thd - 0.5 * kPi));
+    R t = y * R(g.n2), c2 = R(0.5 * (g.n2 - 1));
+    int j0 = (int)F::floor_(t + c2);
+    j0 = min(max(j0, 0), g.n2 - 2);
+    R w2 = t - (R(j0) - c2);
+    cell_axis(g.n2, j0, w2);
+    // azimuthal (periodic)
+    double fk = phd * g.idx3 - 0.5, kf = floor(fk);
+    R w3 = R(fk - kf);
+    long long kl = (long long)kf % g.n3;
+    int k0 = (int)(kl < 0 ? kl + g.n3 : kl);
     int k1 = k0 + 1 == g.n3 ? 0 : k0 + 1;
     R P[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -589,8 +659,8 @@ __device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, 
     R rho = P[0], uu = P[1];
     if (!(rho > R(0)) || !(uu > R(0))) return;
     R dth2, dd;
-    fmks_theta_w(g, w, X2, &dth2, &dd);
-    R dth1 = -R(g.mks_smooth) * w * dd;
+    fmks_mu(g, w, y, &dth2, &dd);
+    R dth1 = -pick<R>(g.mks_smooth, g.f_mks_smooth) * w * dd;
     R Ut[4] = {R(0), r * P[2], dth1 * P[2] + dth2 * P[3], P[4]};
     R Bi[4] = {R(0), r * P[5], dth1 * P[5] + dth2 * P[6], P[7]};
     // KS lapse 1/sqrt(1+q), shift beta^r = q/(1+q)
@@ -611,15 +681,16 @@ __device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, 
     o.b[2] = (Bi[2] + bt * o.u[2]) * iut;
     o.b[3] = (Bi[3] + bt * o.u[3]) * iut;
     R bsq = m.dot(o.b, o.b);
-    if (bsq > R(g.sigma_cut) * rho) return;
-    R ga = R(g.gamma_ad);
+    if (bsq > pick<R>(g.sigma_cut, g.f_sigma_cut) * rho) return;
+    R ga = pick<R>(g.gamma_ad, g.f_gamma_ad);
     // R = (R_high beta^2 + R_low)/(1 + beta^2), written in 1/beta so nothing overflows
     R ib = bsq / (R(2) * (ga - R(1)) * uu);
     R ib2 = ib * ib;
-    R Rt = ib2 < R(1e30) ? (R(g.R_high) + R(g.R_low) * ib2) / (R(1) + ib2) : R(g.R_low);
-    o.ne = rho * R(g.ne_unit);
+    R Rt = ib2 < R(1e30) ? (pick<R>(g.R_high, g.f_R_high) + pick<R>(g.R_low, g.f_R_low) * ib2) / (R(1) + ib2)
+                         : pick<R>(g.R_low, g.f_R_low);
+    o.ne = rho * pick<R>(g.ne_unit, g.f_ne_unit);
     o.Te = R(kMp / kMe) * (ga - R(1)) * uu / (rho * (R(1) + Rt));
-    o.B = F::sqrt_(fmax(bsq, R(0))) * R(g.b_unit);
+    o.B = F::sqrt_(fmax(bsq, R(0))) * pick<R>(g.b_unit, g.f_b_unit);
     o.valid = true;
 }
 

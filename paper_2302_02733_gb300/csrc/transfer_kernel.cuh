@@ -185,7 +185,7 @@ template <typename R, int CM = 0>
 __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, const double4_32a &q0,
                                            const double4_32a &q1, const R *sgw, XLane<R> &Ln, KS<R> &m,
                                            const XferArgs *pa = nullptr, long long st = 0) {
-    const R a = R(c.a);
+    const R a = pick<R>(c.a, c.f_a);
     R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
     R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
     R hs = to_real<R>(q1.w);
@@ -203,7 +203,7 @@ __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, co
     if (mdl.kind == 1)
         adaf_plasma(mdl.adaf, a, m, r, pl);
     else
-        grid_plasma(mdl.grid, m, r, th, ph, pl);
+        grid_plasma(mdl.grid, m, q0.x, q0.y, q0.z, pl);
     R e1[4], e2[4], w, sth, cth;
     if (pl.valid) fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
     if (Ln.basis || pl.valid) {
@@ -238,11 +238,11 @@ __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, co
         }
         R cf[8];
         if (CM == 0)
-            thermal_coeffs(pl.ne, pl.Te, pl.B, w * R(c.nu_obs), sth, cth, sgw, cf);
+            thermal_coeffs(pl.ne, pl.Te, pl.B, w * pick<R>(c.nu_obs, c.f_nu_obs), sth, cth, sgw, cf);
         else
-            kappa_point_coeffs<R, CM>(pa, st, mdl, pl, w, sth, cth, R(c.nu_obs), cf);
+            kappa_point_coeffs<R, CM>(pa, st, mdl, pl, w, sth, cth, pick<R>(c.nu_obs, c.f_nu_obs), cf);
         // invariant form: S holds I/nu^3, so the step takes J/w^3 and the same M
-        R ds = w * h * R(c.L_unit);
+        R ds = w * h * pick<R>(c.L_unit, c.f_L_unit);
         substep(cf, ds, R(1) / (w * w * w), Ln.S, Ln.Slo);
         kahan_add(Ln.tau, Ln.tauc, cf[3] * ds);
         kahan_add(Ln.phi, Ln.phic, cf[7] * ds);
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
                     live = true;
                 } else {
                     int ix, iy;
-                    ray_pixel(ray + p.ray_offset, c.nx, c.ny, ix, iy);
+                    map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
                     long long pix = (long long)iy * c.nx + ix;
                     xfer_zero<OutT>(pix, p.out, p.depth);
                     if (p.status) p.status[pix] = (uint8_t)rstat;
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
         my_pts++;
         if (n == 0) {
             int ix, iy;
-            ray_pixel(ray + p.ray_offset, c.nx, c.ny, ix, iy);
+            map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
             xfer_finish<R, OutT>(c, m, ix, iy, Ln, p.out, p.depth);
             if (p.status) p.status[(long long)iy * c.nx + ix] = (uint8_t)rstat;
             live = false;
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
 template <typename R>
 __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
     const Camera &c = p.cam;
-    const R a = R(c.a), nu_obs = R(c.nu_obs);
+    const R a = pick<R>(c.a, c.f_a), nu_obs = pick<R>(c.nu_obs, c.f_nu_obs);
     long long ray = -1;
     int blk = -1, slot = 0, n = 0;
     bool live = false, drained = false;
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
         if (p.model.kind == 1)
             adaf_plasma(p.model.adaf, a, m, r, pl);
         else
-            grid_plasma(p.model.grid, m, r, th, ph, pl);
+            grid_plasma(p.model.grid, m, q0.x, q0.y, q0.z, pl);
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (pl.valid) {
             R e1[4], e2[4], w, sth, cth;
@@ -447,6 +447,98 @@ __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
         if (p.feat) p.feat[(long long)blk * kBlockStates + slot] = o;
         if (n == 0) live = false;
     }
+}
+
+// The unpolarized transfer (Stokes I only, for fitting loops): I/nu^3 is a scalar invariant,
+// so nothing is transported. At each emitting point: the pitch angle from scalar products
+// (the ray's fluid-frame direction is -K - w u, b is spatial in that frame), j_I and a_I, and the
+// exact step I <- I e^-tau + (j ds / w^3) (1 - e^-tau)/tau, added as the increment
+// (J - tau I) (1 - e^-tau)/tau with TwoSum compensation. Output: one value per pixel.
+template <typename R>
+__global__ void __launch_bounds__(kXferThreads, 4) unpol_kernel(XferArgs p) {
+    typedef Mth<R> F;
+    const Camera &c = p.cam;
+    const R a = pick<R>(c.a, c.f_a), nu_obs = pick<R>(c.nu_obs, c.f_nu_obs), L = pick<R>(c.L_unit, c.f_L_unit);
+    long long ray = -1;
+    int blk = -1, slot = 0, n = 0, rstat = 0;
+    bool live = false, drained = false;
+    R I = 0, Ilo = 0;
+    unsigned long long my_pts = 0, my_emit = 0;
+    for (;;) {
+        bool want = !live && !drained;
+        unsigned long long t = warp_pop(&p.ctr->xfer_next, want);
+        if (want) {
+            if (t < (unsigned long long)p.nrays) {
+                ray = (long long)t;
+                RayRecord rec = p.rec[ray];
+                rstat = rec.status;
+                if (rec.nstates >= 2) {
+                    blk = rec.last_block;
+                    slot = (rec.nstates - 1) % kBlockStates;
+                    n = rec.nstates - 1;
+                    I = Ilo = R(0);
+                    live = true;
+                } else {
+                    int ix, iy;
+                    map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
+                    long long pix = (long long)iy * c.nx + ix;
+                    reinterpret_cast<R *>(p.out)[pix] = R(0);
+                    if (p.status) p.status[pix] = (uint8_t)rstat;
+                }
+            } else {
+                drained = true;
+            }
+        }
+        if (__all_sync(0xffffffffu, !live && drained)) break;
+        if (!live) continue;
+        if (--slot < 0) {
+            blk = p.arena.prev[blk];
+            slot = kBlockStates - 1;
+        }
+        n--;
+        const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
+        double4_32a q0 = src[0], q1 = src[1];
+        R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
+        R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
+        R h = fabs(to_real<R>(q1.w));
+        KS<R> m;
+        m.eval(a, r, th);
+        Plasma<R> pl;
+        if (p.model.kind == 1)
+            adaf_plasma(p.model.adaf, a, m, r, pl);
+        else
+            grid_plasma(p.model.grid, m, q0.x, q0.y, q0.z, pl);
+        if (pl.valid) {
+            R w = m.dot(K, pl.u);
+            R kp[4], bn[4];
+            R bs = fmax(fmax(fabs(pl.b[0]), fabs(pl.b[1])), fmax(fabs(pl.b[2]), fabs(pl.b[3])));
+            R ibs = bs > R(0) ? R(1) / bs : R(0);
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                kp[i] = -K[i] - w * pl.u[i];
+                bn[i] = pl.b[i] * ibs;
+            }
+            R bb = m.dot(bn, bn), kk = m.dot(kp, kp), bk = m.dot(bn, kp);
+            R sth = (bb > R(0) && kk > R(0)) ? F::sqrt_(fmax(bb - bk * bk / kk, R(0)) / bb) : R(0);
+            R jI, aI;
+            thermal_jI_aI(pl.ne, pl.Te, pl.B, w * nu_obs, sth, jI, aI);
+            R ds = w * h * L, tau = aI * ds;
+            R J = jI * ds / (w * w * w);
+            two_sum_add(I, Ilo, (J - tau * I) * phi1(tau));
+            my_emit++;
+        }
+        my_pts++;
+        if (n == 0) {
+            int ix, iy;
+            map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
+            long long pix = (long long)iy * c.nx + ix;
+            reinterpret_cast<R *>(p.out)[pix] = I + Ilo;
+            if (p.status) p.status[pix] = (uint8_t)rstat;
+            live = false;
+        }
+    }
+    if (my_pts) atomicAdd(&p.ctr->points, my_pts);
+    if (my_emit) atomicAdd(&p.ctr->emitting, my_emit);
 }
 
 }  // namespace prt

@@ -17,7 +17,7 @@ from . import build as _build
 RT_OK, RT_ERR_INVALID, RT_ERR_CUDA, RT_ERR_NOMEM, RT_ERR_NOT_READY, RT_ERR_WORKSPACE, RT_ERR_SIZE = 0, -1, -2, -3, -4, -5, -6
 RT_ERR_STALL = -7
 RT_MODEL_ADAF, RT_MODEL_GRID = 1, 2
-RT_FP64, RT_MIXED, RT_SURROGATE = 0, 1, 2
+RT_FP64, RT_MIXED, RT_SURROGATE, RT_UNPOL = 0, 1, 2, 3
 RT_EDF_THERMAL, RT_EDF_KAPPA = 0, 1
 RT_RAY_HORIZON, RT_RAY_ESCAPE, RT_RAY_NMAX, RT_RAY_NAN, RT_RAY_OVERFLOW = 1, 2, 3, 4, 5
 
@@ -104,6 +104,8 @@ def lib():
         L.rt_mlp_train.argtypes = [_VP, _VP, _VP, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_uint64, _VP]
         L.rt_surrogate_dataset.argtypes = [_VP, _VP, C.c_longlong, C.c_uint64, _VP, _VP, _VP]
         L.rt_surrogate_coeffs.argtypes = [_VP, _VP, C.c_longlong, _VP, _VP]
+        L.rt_render_adaptive.argtypes = [_VP, C.c_int, _VP, _VP, C.c_int, C.c_double, C.POINTER(C.c_longlong)]
+        L.rt_image_visibilities.argtypes = [_VP, _VP, C.c_int, C.c_int, _VP]
         L.rt_render_features.argtypes = [_VP, _VP, C.c_longlong, C.POINTER(C.c_longlong)]
         L.rt_surrogate_fit.argtypes = [_VP, _VP, _VP, _VP, C.c_longlong, _VP, C.POINTER(rt_mlp_norm)]
         L.rt_render_batch.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int]
@@ -284,6 +286,19 @@ def rt_surrogate_fit(ctx, x, y, valid, t, lo, hi) -> rt_mlp_norm:
     _check(lib().rt_surrogate_fit(ctx, _ptr(x), _ptr(y), _ptr(valid), int(x.shape[0]), _ptr(t), C.byref(n)),
            "rt_surrogate_fit")
     return n
+
+
+def rt_render_adaptive(ctx, form: int, out, status=None, base_step: int = 8, tol: float = 1e-3) -> int:
+    """Adaptive render into device buffers; returns the number of rays traced."""
+    n = C.c_longlong(0)
+    _check(lib().rt_render_adaptive(ctx, form, _ptr(out), _ptr(status), base_step, tol, C.byref(n)),
+           "rt_render_adaptive")
+    return n.value
+
+
+def rt_image_visibilities(ctx, img, form: int, stokes: int, vis):
+    """vis: complex buffer [ny][nx] (complex128 for RT_FP64, complex64 otherwise)."""
+    _check(lib().rt_image_visibilities(ctx, _ptr(img), form, stokes, _ptr(vis)), "rt_image_visibilities")
 
 
 def rt_render_features(ctx, feat) -> int:

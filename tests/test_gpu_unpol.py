@@ -1,0 +1,72 @@
+"""The unpolarized fast path (RT_UNPOL: Stokes I with j_I and a_I only, FP32 scalar transfer
+with a compensated sum) against the oracle's scalar transfer: ADAF 64^2 per-pixel p99 <= 1e-5
+and flux <= 1e-6; torus 32^2 p99 <= 1e-4 and flux <= 1e-4; the image statistics (flux) from
+the I-only layout; and its speed against the polarized mixed form."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2302_02733_gb300 import polrt
+
+    torch.cuda.set_device(0)
+    ctx = polrt.rt_create(0, torch.cuda.current_stream().cuda_stream)
+    yield polrt, ctx
+    polrt.rt_destroy(ctx)
+
+
+def test_unpolarized_images_match_oracle(rt, ora, synth, torus_grid):
+    polrt, ctx = rt
+    prims, g = torus_grid
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    cases = [("adaf64", synth.Camera(incl_deg=60.0, nx=64, ny=64), polrt.adaf_model(synth.adaf_params(1)),
+              ora.adaf_model(synth.adaf_params(1)), 1e-5, 1e-6),
+             ("grid32", synth.Camera(incl_deg=20.0, nx=32, ny=32), polrt.grid_model(prims, g),
+              ora.grid_model(prims, g), 1e-4, 1e-4)]
+    for name, cam, model, omodel, tp, tf in cases:
+        polrt.rt_set_camera(ctx, cam)
+        polrt.rt_load_model(ctx, model)
+        out = torch.full((cam.ny, cam.nx), float("nan"), dtype=torch.float32, device="cuda")
+        st = torch.zeros((cam.ny, cam.nx), dtype=torch.uint8, device="cuda")
+        polrt.rt_render(ctx, polrt.RT_UNPOL, out, st)
+        g1 = out.double().cpu().numpy()
+        ref = ora.render_unpol(ora.camera(cam), omodel)
+        scale = np.maximum(ref, 1e-8 * ref.max())
+        err = np.abs(g1 - ref) / scale
+        f_err = abs(g1.sum() / ref.sum() - 1)
+        flux, lp, cp = polrt.rt_image_stats(ctx, out, polrt.RT_UNPOL)
+        o = ora.camera(cam)
+        print(f"unpol {name}: p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e} "
+              f"flux {f_err:.2e}")
+        assert np.isfinite(g1).all() and np.percentile(err, 99) <= tp and f_err <= tf
+        assert lp == 0.0 and cp == 0.0 and flux > 0
+        ostats = ora.image_stats(o, np.stack([ref, 0 * ref, 0 * ref, 0 * ref], axis=-1))
+        assert abs(flux / ostats[0] - 1) <= 2 * tf
+
+
+def test_unpolarized_form_is_faster(rt, synth, torus_grid):
+    polrt, ctx = rt
+    prims, g = torus_grid
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
+    cam = synth.Camera(incl_deg=20.0, nx=512, ny=512)
+    polrt.rt_set_camera(ctx, cam)
+    out_i = torch.zeros((512, 512), dtype=torch.float32, device="cuda")
+    out_p = torch.zeros((512, 512, 4), dtype=torch.float32, device="cuda")
+    res = {}
+    for name, form, o in (("unpol", polrt.RT_UNPOL, out_i), ("mixed", polrt.RT_MIXED, out_p)):
+        polrt.rt_render(ctx, form, o)
+        polrt.rt_render(ctx, form, o)
+        c = polrt.rt_last_counters(ctx)
+        res[name] = (c["ms_geodesic"], c["ms_transfer"])
+    print(f"512^2 torus: unpolarized transfer {res['unpol'][1]:.1f} ms vs polarized {res['mixed'][1]:.1f} ms "
+          f"(geodesic {res['unpol'][0]:.1f} ms)")
+    assert res["unpol"][1] * 2 < res["mixed"][1]
