@@ -145,7 +145,7 @@ class TorusParams:
     r_in: float = 6.0
     r_max: float = 12.0
     kappa_poly: float = 1.0e-3
-    beta_min: float = 1.0
+    beta_min: float = 0.1
     aphi_cut: float = 0.2
     sigma_pert: float = 0.5
     rho_atm: float = 1.0e-5
