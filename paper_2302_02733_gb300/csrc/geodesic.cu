@@ -9,7 +9,14 @@
 
 namespace prt {
 
+static_assert(kSinTabBytes == 3 * kSinTab * sizeof(double), "sin/cos table size");
+
 __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
+    // the sin/cos table in shared memory: the RK4 stages read it at data-dependent indices, and
+    // through the texture path those reads queued behind the transfer's gathers
+    __shared__ double tab[3 * kSinTab];
+    for (int i = threadIdx.x; i < 3 * kSinTab; i += blockDim.x) tab[i] = p.sctab[i];
+    __syncthreads();
     const Camera &c = p.cam;
     double y[7];
     long long ray = -1;
@@ -37,7 +44,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
         if (!live) continue;
 
         double h, yn[7];
-        bool refl = geo_step(p.sctab, c, y, yn, h);
+        bool refl = geo_step(tab, c, y, yn, h);
         // save state n with the step taken from it; then n+1 becomes current
         uint8_t status = 0;
         for (int pass = 0; pass < 2; pass++) {

@@ -7,13 +7,21 @@
 
 namespace prt {
 
+// Order of positive doubles by their bit patterns (as signed 64-bit integers a negative
+// double orders below every positive one). Comparisons on the integer pipe keep the FP64 pipe,
+// the kernel's bound, for arithmetic.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double pos_min(double x, double y) { return dbits(x) < dbits(y) ? x : y; }
+__device__ __forceinline__ double pos_max(double x, double y) { return dbits(x) < dbits(y) ? y : x; }
+
 // h = eps / (|K^r|/r + |K^th|/tt + |K^ph| + 1e-40), tt = max(min(th, pi - th), 0.01), taken
-// with one division: h = eps r tt / (|K^r| tt + |K^th| r + (|K^ph| + 1e-40) r tt).
+// with one reciprocal: h = eps r tt / (|K^r| tt + |K^th| r + (|K^ph| + 1e-40) r tt). Here
+// 0 <= th <= pi, so min and max compare bit patterns.
 __device__ __forceinline__ double step_size(double eps, const double y[7]) {
-    double tt = fmax(fmin(y[1], kPi - y[1]), 1e-2);
+    double tt = pos_max(pos_min(y[1], kPi - y[1]), 1e-2);
     double rt = y[0] * tt;
     double den = fma(fabs(y[6]) + 1e-40, rt, fma(fabs(y[4]), tt, fabs(y[5]) * y[0]));
-    return eps * rt / den;
+    return (eps * rt) * recip_nr(den);
 }
 
 // y = (r, theta, phi, K^t, K^r, K^theta, K^phi); t is never needed (stationary metric).
@@ -66,12 +74,13 @@ __device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const C
     h = step_size(c.eps, y);
     rk4_step(tab, c.a, h, y, yn);
     bool refl = false;
-    if (yn[1] < 0.0) {
+    long long tb = dbits(yn[1]);
+    if (tb < 0 && (tb << 1) != 0) {  // theta < 0 (not -0)
         yn[1] = -yn[1];
         yn[2] += kPi;
         yn[5] = -yn[5];
         refl = true;
-    } else if (yn[1] > kPi) {
+    } else if (tb > dbits(kPi)) {  // theta > pi
         yn[1] = 2.0 * kPi - yn[1];
         yn[2] += kPi;
         yn[5] = -yn[5];
@@ -84,10 +93,10 @@ __device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const C
 __device__ __forceinline__ uint8_t geo_stop(const Camera &c, const double y[7], int n) {
     bool bad = false;
 #pragma unroll
-    for (int k = 0; k < 7; k++) bad |= !isfinite(y[k]);
+    for (int k = 0; k < 7; k++) bad |= (__double2hiint(y[k]) & 0x7ff00000) == 0x7ff00000;  // inf or NaN
     if (bad) return kNan;
-    if (y[0] < 1.05 * c.rh) return kHorizon;
-    if (y[0] > c.r_cam && y[4] > 0.0) return kEscape;
+    if (dbits(y[0]) < dbits(c.r_stop)) return kHorizon;
+    if (dbits(y[0]) > dbits(c.r_cam) && dbits(y[4]) > 0) return kEscape;
     if (n >= c.nmax) return kNmax;
     return 0;
 }

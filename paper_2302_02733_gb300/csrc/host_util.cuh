@@ -47,6 +47,7 @@ inline Camera make_camera(const rt_camera &rc, double eps, int nmax) {
     cam.eps = eps;
     cam.nmax = nmax;
     cam.rh = 1.0 + std::sqrt(1.0 - rc.a * rc.a);
+    cam.r_stop = 1.05 * cam.rh;
     cam.f_a = (float)cam.a;
     cam.f_nu_obs = (float)cam.nu_obs;
     cam.f_L_unit = (float)cam.L_unit;

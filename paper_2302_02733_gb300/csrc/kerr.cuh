@@ -128,30 +128,42 @@ struct DK {
 };
 
 // sin and cos of theta for the FP64 geodesic by table-driven angle addition: theta_k from a
-// table of (theta_k, sin theta_k, cos theta_k) at spacing h = 1.5 pi / 2048 over
-// [-pi/4, 5 pi/4], delta = theta - theta_k (|delta| <= h/2 < 1.2e-3), then
-// sin(theta_k + delta) = s_k cos(delta) + c_k sin(delta) with the Taylor polynomials
-// sin d = d - d^3/6 + d^5/120 and cos d = 1 - d^2/2 + d^4/24 - d^6/720 (remainders below
-// 1e-20 relative). Outside the table range it falls back to sincos().
-constexpr int kSinTab = 2048;
+// table of (theta_k, sin theta_k, cos theta_k) at spacing h = 1.5 pi / 1023 over
+// [-pi/4, 5 pi/4] (24 KB, small enough for shared memory), delta = theta - theta_k
+// (|delta| <= h/2 < 2.4e-3), then sin(theta_k + delta) = s_k cos(delta) + c_k sin(delta) with
+// the Taylor polynomials sin d = d - d^3/6 + d^5/120 and cos d = 1 - d^2/2 + d^4/24 - d^6/720
+// (remainders below 1e-22 absolute). Outside the table range it falls back to sincos().
+constexpr int kSinTab = 1024;
 constexpr double kSinLo = -0.25 * kPi;
 constexpr double kSinH = 1.5 * kPi / (kSinTab - 1);
 
 __device__ __forceinline__ void sincos_tab(const double *__restrict__ tab, double th, double *s, double *c) {
-    double t = (th - kSinLo) * (1.0 / kSinH);
-    if (!(t > 1.0 && t < kSinTab - 2.0)) {
+    int k = __double2int_rn(fma(th, 1.0 / kSinH, -kSinLo / kSinH));
+    if (k < 1 || k > kSinTab - 2) {  // outside the table (a NaN converts to INT_MIN)
         sincos(th, s, c);
         return;
     }
-    int k = __double2int_rn(t);
     const double *e = tab + 3 * k;
-    double d = th - __ldg(e);
-    double sk = __ldg(e + 1), ck = __ldg(e + 2);
+    double d = th - e[0];  // |d| <= kSinH / 2
+    double sk = e[1], ck = e[2];
     double d2 = d * d;
-    double sd = fma(d * d2, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);
-    double cd = fma(d2, fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
-    *s = fma(sk, cd, ck * sd);
-    *c = fma(ck, cd, -sk * sd);
+    double sd = fma(d * d2, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);       // sin d
+    double cm = d2 * fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5);  // cos d - 1
+    *s = fma(sk, cm, fma(ck, sd, sk));
+    *c = fma(ck, cm, fma(-sk, sd, ck));
+}
+
+// 1/x for positive normal x: the approximate FP64 reciprocal of the PTX ISA
+// (rcp.approx.ftz.f64, relative error below 2^-22) refined by two Newton-Raphson steps
+// r <- r + r (1 - x r). Each step squares the relative error, so the result is within an ulp
+// of the correctly rounded quotient, in 5 FP64 instructions instead of a full division.
+__device__ __forceinline__ double recip_nr(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
 }
 
 // Geodesic acceleration dK/dl = -Gamma K K (FP64 path), arranged for the FP64 pipe: every
@@ -168,7 +180,7 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double s2 = s * s, sc = s * c;
     double r2 = r * r;
     double sig = fma(a2 * c, c, r2);
-    double iss = 1.0 / (sig * s2);  // 1/(Sigma sin^2)
+    double iss = recip_nr(sig * s2);  // 1/(Sigma sin^2)
     double isig = iss * s2;         // 1/Sigma
     double tr = r + r;
     double q = tr * isig;           // 2r/Sigma

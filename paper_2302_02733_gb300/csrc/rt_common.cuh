@@ -34,6 +34,7 @@ struct Camera {
     double eps;
     int nmax;
     double rh;             // outer horizon radius
+    double r_stop;         // 1.05 rh: the horizon stop
     float f_a, f_nu_obs, f_L_unit;  // float copies for the FP32 transfer (no per-point conversion)
 };
 

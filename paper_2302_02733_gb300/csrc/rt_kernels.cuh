@@ -9,7 +9,7 @@ constexpr int kXferThreads = 128;
 
 struct GeoArgs {
     Camera cam;
-    const double *sctab;  // (theta, sin, cos) table of the FP64 geodesic, 2048 entries
+    const double *sctab;  // (theta, sin, cos) table of the FP64 geodesic, 1024 entries
     Arena arena;
     RayRecord *rec;       // per ray of this chunk
     Counters *ctr;
@@ -101,7 +101,7 @@ void launch_kappa_quad(const KappaTables &T, const double *in, double *out, long
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
 void launch_sincos_table(double *tab, cudaStream_t s);
-constexpr size_t kSinTabBytes = 2048 * 3 * sizeof(double);
+constexpr size_t kSinTabBytes = 1024 * 3 * sizeof(double);
 // coef: 0 thermal fits, 1 kappa quadrature at every emitting point, 2 surrogate outputs
 void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s);
 void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s);
