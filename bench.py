@@ -33,6 +33,10 @@ METRIC = "Stokes-IQUV pixels/s at 1024^2, chosen form (FP64 geodesic + FP32 tran
 GEO_FLOP_PER_STEP = 612
 XFER_FLOP_PER_POINT = {"fp64": 1450, "mixed": 1450}
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# DRAM bytes (read + write) per RK4 step of geodesic_kernel: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum = 0.004478 + 1.424551 GB over 22,982,083 steps (torus, 256^2, one launch).
+# The kernel's traffic is the path arena it writes (64 B per state), so it scales with the steps.
+GEO_DRAM_BYTES_PER_STEP = (0.004478e9 + 1.424551e9) / 22982083
 
 
 def parse():
@@ -312,7 +316,7 @@ def main():
             torch.distributed.barrier()
 
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if ws == 1 else None
-    kt_geo, kt_xf, counters = [], [], None
+    kt_geo, kt_xf, counters, launches = [], [], None, 0
     barrier()
     torch.cuda.synchronize()
     with Clocks(gpu_index) as clk:
@@ -324,6 +328,7 @@ def main():
             counters = polrt.rt_last_counters(ctx)
             kt_geo.append(counters["ms_geodesic"])
             kt_xf.append(counters["ms_transfer"])
+            launches += 2 * counters["chunks"] + 2  # geodesic + transfer per chunk, two image-sum kernels
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -335,19 +340,37 @@ def main():
         ms_max = float(t.item())
     value = ws * npix / (ms_max / 1e3)
 
-    # per-kernel roofline of the dominant kernel (measured live with CUDA events in the library)
+    # per-kernel roofline of the dominant kernel (measured live with CUDA events in the library).
+    # In the overlapped launch shape the geodesic of one chunk shares the SMs with the transfer of
+    # the previous one, so its durations include that sharing; the kernel alone (one pass of each
+    # kernel, the shape used below 2^19 rays) is timed once after the timed region.
     geo_ms, xf_ms = statistics.mean(kt_geo), statistics.mean(kt_xf)
     steps_per_launch = counters["steps"]
     pts_per_launch = counters["points"]
+    chunks = counters["chunks"]
+    polrt.rt_set_render_config(ctx, 0, 0, 1)
+    step()
+    alone = polrt.rt_last_counters(ctx)
+    polrt.rt_set_render_config(ctx, 0, 0, 0)
     if geo_ms >= xf_ms:
         achieved = steps_per_launch * GEO_FLOP_PER_STEP / (geo_ms / 1e3) / 1e12
+        achieved_alone = steps_per_launch * GEO_FLOP_PER_STEP / (alone["ms_geodesic"] / 1e3) / 1e12
         dom = "geodesic_kernel (FP64 RK4)"
     else:
         achieved = pts_per_launch * XFER_FLOP_PER_POINT[args.form] / (xf_ms / 1e3) / 1e12
+        achieved_alone = pts_per_launch * XFER_FLOP_PER_POINT[args.form] / (alone["ms_transfer"] / 1e3) / 1e12
         dom = f"transfer_kernel ({args.form})"
+    traffic = GEO_DRAM_BYTES_PER_STEP * steps_per_launch / max(chunks, 1) if geo_ms >= xf_ms else None
     roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "traffic_source": "bytes per launch, scaled by steps from the ncu capture of the 256^2 case",
+            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+            "launches_per_image": chunks,
+            "note": ("overlapped: each launch shares the SMs with the transfer of the previous chunk"
+                     if chunks > 1 else "one launch per image"),
+            "alone": {"achieved": achieved_alone, "frac": achieved_alone / FP64_PEAK_TFLOPS,
+                      "ms_geodesic": alone["ms_geodesic"], "ms_transfer": alone["ms_transfer"],
+                      "ms_total": alone["ms_total"]}}
 
     extra = {"kernel_ms": {"geodesic": geo_ms, "transfer": xf_ms}, "steps_per_image": steps_per_launch,
              "points_per_image": pts_per_launch, "mean_steps_per_ray": steps_per_launch / npix}
@@ -421,7 +444,6 @@ def main():
 
     polrt.rt_destroy(ctx)
     if rank == 0:
-        chunks = 1
         line = {"metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64 geodesic + f32 transfer" if form == polrt.RT_MIXED else "f64",
@@ -431,7 +453,7 @@ def main():
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (151 MB grid, multi-GB path arena); no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-                "gpu_launches": args.steps * (2 * chunks + 2), **extra}
+                "gpu_launches": launches, **extra}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

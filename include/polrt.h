@@ -130,8 +130,11 @@ typedef struct {
     uint64_t rays, steps, points, emitting_points;
     uint64_t arena_blocks_used, arena_blocks_total;
     uint32_t n_horizon, n_escape, n_nmax, n_nan, n_overflow;
-    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events); 0 after a batch */
+    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events; summed over the
+                                     * chunks of an overlapped render); 0 after a batch */
     float ms_total;                 /* device time of the whole render or batch */
+    uint32_t chunks;                /* ray chunks of the last rt_render (each one geodesic and one
+                                     * transfer launch); 0 after a batch */
 } rt_counters;
 
 /* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t, or
@@ -278,6 +281,27 @@ int rt_render_adaptive(rt_ctx *ctx, int form, void *out, uint8_t *status, int ba
  * nx*ny complex values [l + ny/2][k + nx/2] as (re, im) pairs of double (RT_FP64) or float,
  * host or device. A cuFFT transform of any size; synchronizes. */
 int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, void *vis);
+
+/* Launch shape of rt_render and rt_render_depths (forms RT_FP64, RT_MIXED, RT_UNPOL).
+ * geo_blocks_per_sm and xfer_blocks_per_sm are the resident blocks per SM the geodesic and
+ * transfer kernels are launched with (the grid is that times the SM count; 0 = automatic).
+ * chunks >= 2 overlaps the two phases: the rays are split into that many chunks, each with its
+ * own half of the workspace in turn, and the geodesic kernel of chunk i + 1 runs on one
+ * internal stream beside the transfer kernel of chunk i on another, so the FP64 geodesic and
+ * the FP32 transfer share the SMs. chunks 1 runs the phases one after the other on the
+ * context's stream. chunks 0 (the default, with {0, 0, 0}) is automatic: images of 2^19 rays
+ * or more are overlapped in 4 to 16 chunks of about 2^17 rays, with the geodesic at 1 block per
+ * SM (2 for RT_FP64) and the transfer at its occupancy; smaller images run in one pass of each
+ * kernel, whose per-chunk tails would cost more than the overlap saves. The image is the same
+ * either way (every ray takes the same arithmetic); only the time differs. Shapes that exceed
+ * the kernels' occupancy or chunks above 64 return RT_ERR_INVALID. */
+typedef struct {
+    int geo_blocks_per_sm;
+    int xfer_blocks_per_sm;
+    int chunks;
+} rt_render_config;
+int rt_set_render_config(rt_ctx *ctx, const rt_render_config *cfg);
+int rt_get_render_config(rt_ctx *ctx, rt_render_config *cfg);
 
 /* Counters of the last rt_render (synchronizes). */
 int rt_last_counters(rt_ctx *ctx, rt_counters *out);

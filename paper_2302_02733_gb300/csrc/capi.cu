@@ -102,6 +102,11 @@ int rt_destroy(rt_ctx *c) {
     cudaFree(c->d_x2);
     cudaFree(c->d_x2f);
     cudaFree(c->d_x1c);
+    for (int i = 0; i < 2; i++)
+        if (c->ostream[i]) cudaStreamDestroy(c->ostream[i]);
+    if (c->have_oev)
+        for (int i = 0; i < 4 * rt_ctx::kMaxChunks; i++) cudaEventDestroy(c->oev[i]);
+    if (c->h_ctr2) cudaFreeHost(c->h_ctr2);
     if (c->ws_owned) cudaFree(c->ws);
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
@@ -274,6 +279,113 @@ static int ensure_stage(void **buf, size_t *have, size_t need) {
     return RT_OK;
 }
 
+// Streams, events and the second pinned counter block of the overlapped render, made on first use.
+static int ensure_overlap(rt_ctx *c) {
+    for (int i = 0; i < 2; i++)
+        if (!c->ostream[i] && cudaStreamCreateWithFlags(&c->ostream[i], cudaStreamNonBlocking) != cudaSuccess)
+            return RT_ERR_CUDA;
+    if (!c->h_ctr2 && cudaMallocHost(&c->h_ctr2, sizeof(Counters)) != cudaSuccess) return RT_ERR_CUDA;
+    if (!c->have_oev) {
+        for (int i = 0; i < 4 * rt_ctx::kMaxChunks; i++)
+            if (cudaEventCreate(&c->oev[i]) != cudaSuccess) {
+                for (int j = 0; j < i; j++) cudaEventDestroy(c->oev[j]);
+                return RT_ERR_CUDA;
+            }
+        c->have_oev = true;
+    }
+    return RT_OK;
+}
+
+// Overlapped render. The rays are split into K chunks that alternate between two halves of the
+// workspace, each half with its own counters, ray records and arena. Chunk i's geodesic runs on
+// ostream[0] once the transfer of chunk i - 2 (the same half) has finished, and its transfer on
+// ostream[1] once its geodesic has; so the geodesic of chunk i + 1 shares the SMs with the
+// transfer of chunk i. Returns RT_ERR_NOMEM when a half cannot hold a chunk of at most
+// kMaxChunks-th of the rays.
+static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, const Model &mod, const int *list,
+                          long long nrays, int chunks, void *d_out, uint8_t *d_status, void *d_depth, int geo_grid,
+                          int xf_grid) {
+    int rv = ensure_overlap(c);
+    if (rv) return rv;
+    const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
+    const size_t off_rec = align_up(sizeof(Counters));
+    // the most rays a half holds at the arena budget per ray
+    if (half < off_rec + 4 * kAlign + kPerRayBytes) return RT_ERR_NOMEM;
+    long long cap = (long long)((half - off_rec - 4 * kAlign) / kPerRayBytes);
+    long long K = std::max<long long>(chunks, (nrays + cap - 1) / cap);
+    K = std::min<long long>(K, nrays);
+    if (K > rt_ctx::kMaxChunks) return RT_ERR_NOMEM;
+    const long long chunk = (nrays + K - 1) / K;
+    Counters *ctr[2];
+    RayRecord *rec[2];
+    Arena ar[2];
+    for (int h = 0; h < 2; h++) {
+        char *base = (char *)c->ws + h * half;
+        ctr[h] = (Counters *)base;
+        rec[h] = (RayRecord *)(base + off_rec);
+        size_t off = align_up(off_rec + sizeof(RayRecord) * chunk);
+        long long nb = (long long)((half - off - 3 * kAlign) / kBlockBytes);
+        ar[h].states = (PathState *)(base + off);
+        ar[h].prev = (int *)(base + off + (size_t)nb * sizeof(PathState) * kBlockStates);
+        ar[h].nblocks = nb;
+    }
+    cudaStream_t sg = c->ostream[0], st = c->ostream[1];
+    cudaEvent_t *gs = c->oev, *ge = c->oev + rt_ctx::kMaxChunks, *ts = c->oev + 2 * rt_ctx::kMaxChunks,
+                *te = c->oev + 3 * rt_ctx::kMaxChunks;
+    CK(cudaMemsetAsync(ctr[0], 0, sizeof(Counters), c->stream));
+    CK(cudaMemsetAsync(ctr[1], 0, sizeof(Counters), c->stream));
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(cudaStreamWaitEvent(sg, c->ev[0], 0));
+    CK(cudaStreamWaitEvent(st, c->ev[0], 0));
+    for (long long i = 0; i < K; i++) {
+        const int h = (int)(i & 1);
+        const long long o = i * chunk, n = std::min(chunk, nrays - o);
+        if (i >= 2) CK(cudaStreamWaitEvent(sg, te[i - 2], 0));
+        CK(cudaMemsetAsync(ctr[h], 0, 4 * sizeof(unsigned long long), sg));  // queues + arena
+        GeoArgs ga{cam, c->d_sctab, ar[h], rec[h], ctr[h], n, o};
+        ga.pix_list = list;
+        XferArgs xa{cam, mod, ar[h], rec[h], ctr[h], n, o, d_out, d_status, d_depth};
+        xa.pix_list = list;
+        xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+        CK(cudaEventRecord(gs[i], sg));
+        launch_geodesic(ga, geo_grid, sg);
+        CK(cudaEventRecord(ge[i], sg));
+        CK(cudaStreamWaitEvent(st, ge[i], 0));
+        CK(cudaEventRecord(ts[i], st));
+        if (form == RT_FP64)
+            launch_transfer_fp64(xa, coef, xf_grid, st);
+        else if (form == RT_UNPOL)
+            launch_unpol(xa, xf_grid, st);
+        else
+            launch_transfer_mixed(xa, coef, xf_grid, st);
+        CK(cudaEventRecord(te[i], st));
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamWaitEvent(c->stream, ge[K - 1], 0));
+    CK(cudaStreamWaitEvent(c->stream, te[K - 1], 0));
+    CK(cudaEventRecord(c->ev[2], c->stream));
+    CK(cudaMemcpyAsync(c->h_ctr2, ctr[1], sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->h_ctr, ctr[0], sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    Counters &a = *c->h_ctr, &b = *c->h_ctr2;
+    a.steps += b.steps;
+    a.points += b.points;
+    a.emitting += b.emitting;
+    a.arena_next = std::max(a.arena_next, b.arena_next);
+    for (int k = 0; k < 8; k++) a.n_status[k] += b.n_status[k];
+    float g = 0.f, x = 0.f, ms = 0.f;
+    for (long long i = 0; i < K; i++) {
+        if (cudaEventElapsedTime(&ms, gs[i], ge[i]) == cudaSuccess) g += ms;
+        if (cudaEventElapsedTime(&ms, ts[i], te[i]) == cudaSuccess) x += ms;
+    }
+    cudaGetLastError();
+    c->last_ms_geo = g;
+    c->last_ms_xfer = x;
+    c->last_chunks = (int)K;
+    c->last_blocks_total = ar[0].nblocks;
+    return RT_OK;
+}
+
 static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *depth, const int *list = nullptr,
                        long long nlist = 0) {
     if (!c || !out_iquv || form < RT_FP64 || form > RT_UNPOL) return RT_ERR_INVALID;
@@ -297,7 +409,22 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     // workspace carving; the surrogate form adds, per saved state, the network's inputs and
     // outputs (16 + 32 bytes)
     const size_t per_ray = kPerRayBytes + (sur ? (size_t)kBudgetBlocksPerRay * kBlockStates * 48 : 0);
-    int rv = ensure_workspace(c, nrays, per_ray);
+
+    // launch shape: the configured one, or automatic (overlapped chunks of about 2^17 rays for
+    // images of 2^19 rays or more, the geodesic at 1 block per SM, 2 for the FP64 form, beside
+    // the transfer at its occupancy; one pass of each kernel below that)
+    int chunks = c->rcfg.chunks, geo_b = c->rcfg.geo_blocks_per_sm;
+    if (chunks == 0) {
+        chunks = nrays >= (1ll << 19) ? (int)std::min<long long>(16, std::max<long long>(4, nrays >> 17)) : 1;
+        if (chunks >= 2 && geo_b == 0) geo_b = form == RT_FP64 ? std::min(2, c->geo_bps) : 1;
+    }
+    const bool ovl = chunks >= 2 && !sur && nrays >= 2;
+    // the overlapped form holds two chunks at a time, each half with its own counters
+    long long ws_rays = nrays;
+    if (ovl)
+        ws_rays = 2 * ((nrays + chunks - 1) / chunks) +
+                  2 * (long long)((align_up(sizeof(Counters)) + 4 * kAlign + per_ray - 1) / per_ray) + 1;
+    int rv = ensure_workspace(c, ws_rays, per_ray);
     if (rv) return rv;
     const size_t per_block = kBlockBytes + (sur ? (size_t)kBlockStates * 48 : 0);
     char *base = (char *)c->ws;
@@ -346,60 +473,71 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         d_depth = c->d_stage_depth;
     }
 
-    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
-    int geo_grid = c->nsm * c->geo_bps;
-    int xf_grid = c->nsm * (form == RT_FP64 ? c->fp64_bps : c->mixed_bps);
-    for (long long o = 0; o < nrays; o += chunk) {
-        long long n = std::min(chunk, nrays - o);
-        CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));  // queues + arena
-        GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
-        ga.pix_list = list;
-        XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
-        xa.pix_list = list;
-        xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
-        if (sur) {
-            xa.feat = feat;
-            xa.sur_y = sur_y;
-            xa.sur_norm = reinterpret_cast<const float *>(c->d_mlpaux) + 4;
-            for (int j = 0; j < 4; j++) {
-                xa.sur_lo[j] = c->mlp_norm.lo[j];
-                xa.sur_hi[j] = c->mlp_norm.hi[j];
+    const int xf_max = form == RT_FP64 ? c->fp64_bps : c->mixed_bps;
+    const int geo_grid = c->nsm * (geo_b > 0 ? geo_b : c->geo_bps);
+    const int xf_grid =
+        c->nsm * (c->rcfg.xfer_blocks_per_sm > 0 ? std::min(c->rcfg.xfer_blocks_per_sm, xf_max) : xf_max);
+    c->last_was_overlap = false;
+    if (ovl) {
+        rv = render_overlap(c, form, coef, cam, mod, list, nrays, chunks, d_out, d_status, d_depth, geo_grid,
+                            xf_grid);
+        if (rv) return rv;
+        c->last_was_overlap = true;
+    } else {
+        CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
+        c->last_chunks = (int)((nrays + chunk - 1) / chunk);
+        for (long long o = 0; o < nrays; o += chunk) {
+            long long n = std::min(chunk, nrays - o);
+            CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));  // queues + arena
+            GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
+            ga.pix_list = list;
+            XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
+            xa.pix_list = list;
+            xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+            if (sur) {
+                xa.feat = feat;
+                xa.sur_y = sur_y;
+                xa.sur_norm = reinterpret_cast<const float *>(c->d_mlpaux) + 4;
+                for (int j = 0; j < 4; j++) {
+                    xa.sur_lo[j] = c->mlp_norm.lo[j];
+                    xa.sur_hi[j] = c->mlp_norm.hi[j];
+                }
             }
+            if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
+            launch_geodesic(ga, geo_grid, c->stream);
+            if (sur) {
+                // the network's inputs for every saved state, then one tensor-core pass over them
+                unsigned long long used = 0;
+                CK(cudaMemcpyAsync(&used, &ctr->arena_next, sizeof(used), cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                used = std::min<unsigned long long>(used, (unsigned long long)nblocks);
+                launch_sur_features(xa, xf_grid, c->stream);
+                long long rows = (long long)used * kBlockStates;
+                if (rows > 0)
+                    launch_mlp_forward(reinterpret_cast<const float *>(feat), sur_y, rows, c->d_wpk,
+                                       reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
+                                       (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), c->stream);
+            }
+            if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
+            if (form == RT_FP64)
+                launch_transfer_fp64(xa, coef, xf_grid, c->stream);
+            else if (form == RT_UNPOL)
+                launch_unpol(xa, xf_grid, c->stream);
+            else
+                launch_transfer_mixed(xa, coef, xf_grid, c->stream);
+            CK(cudaGetLastError());
         }
-        if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
-        launch_geodesic(ga, geo_grid, c->stream);
-        if (sur) {
-            // the network's inputs for every saved state, then one tensor-core pass over them
-            unsigned long long used = 0;
-            CK(cudaMemcpyAsync(&used, &ctr->arena_next, sizeof(used), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            used = std::min<unsigned long long>(used, (unsigned long long)nblocks);
-            launch_sur_features(xa, xf_grid, c->stream);
-            long long rows = (long long)used * kBlockStates;
-            if (rows > 0)
-                launch_mlp_forward(reinterpret_cast<const float *>(feat), sur_y, rows, c->d_wpk,
-                                   reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
-                                   (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), c->stream);
-        }
-        if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
-        if (form == RT_FP64)
-            launch_transfer_fp64(xa, coef, xf_grid, c->stream);
-        else if (form == RT_UNPOL)
-            launch_unpol(xa, xf_grid, c->stream);
-        else
-            launch_transfer_mixed(xa, coef, xf_grid, c->stream);
-        CK(cudaGetLastError());
+        CK(cudaEventRecord(c->ev[2], c->stream));
+        CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+        c->last_blocks_total = nblocks;
     }
-    CK(cudaEventRecord(c->ev[2], c->stream));
     if (!out_dev) CK(cudaMemcpyAsync(out_iquv, d_out, (size_t)npix_img * ncomp * esz, cudaMemcpyDeviceToHost, c->stream));
     if (status && !st_dev)
         CK(cudaMemcpyAsync(status, d_status, (size_t)npix_img, cudaMemcpyDeviceToHost, c->stream));
     if (depth && !dep_dev)
         CK(cudaMemcpyAsync(depth, d_depth, (size_t)npix_img * 2 * esz, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->last_rays = nrays;
-    c->last_blocks_total = nblocks;
     c->last_was_batch = false;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     return RT_OK;
@@ -530,6 +668,22 @@ int rt_kappa_coeffs(rt_ctx *c, const double *in, long long n, double *out) {
     return RT_OK;
 }
 
+int rt_set_render_config(rt_ctx *c, const rt_render_config *cfg) {
+    if (!c || !cfg) return RT_ERR_INVALID;
+    if (cfg->geo_blocks_per_sm < 0 || cfg->geo_blocks_per_sm > c->geo_bps) return RT_ERR_INVALID;
+    if (cfg->xfer_blocks_per_sm < 0 || cfg->xfer_blocks_per_sm > std::max(c->mixed_bps, c->fp64_bps))
+        return RT_ERR_INVALID;
+    if (cfg->chunks < 0 || cfg->chunks > rt_ctx::kMaxChunks) return RT_ERR_INVALID;
+    c->rcfg = *cfg;
+    return RT_OK;
+}
+
+int rt_get_render_config(rt_ctx *c, rt_render_config *cfg) {
+    if (!c || !cfg) return RT_ERR_INVALID;
+    *cfg = c->rcfg;
+    return RT_OK;
+}
+
 int rt_last_counters(rt_ctx *c, rt_counters *out) {
     if (!c || !out) return RT_ERR_INVALID;
     CK(cudaSetDevice(c->device));
@@ -551,8 +705,14 @@ int rt_last_counters(rt_ctx *c, rt_counters *out) {
     if (c->last_was_batch) {
         out->ms_total = c->last_ms_total;
     } else {
-        if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out->ms_geodesic = ms;
-        if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) out->ms_transfer = ms;
+        out->chunks = (uint32_t)c->last_chunks;
+        if (c->last_was_overlap) {
+            out->ms_geodesic = c->last_ms_geo;
+            out->ms_transfer = c->last_ms_xfer;
+        } else {
+            if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out->ms_geodesic = ms;
+            if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) out->ms_transfer = ms;
+        }
         if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]) == cudaSuccess) out->ms_total = ms;
     }
     cudaGetLastError();

@@ -46,6 +46,18 @@ struct rt_ctx {
     float last_ms_total = 0.f;
     bool last_was_batch = false;
 
+    // overlapped rt_render: geodesic of chunk i + 1 on ostream[0] beside the transfer of chunk i
+    // on ostream[1]; per chunk the events geodesic start/end, transfer start/end
+    static constexpr int kMaxChunks = 64;
+    rt_render_config rcfg{};
+    cudaStream_t ostream[2] = {nullptr, nullptr};
+    cudaEvent_t oev[4 * kMaxChunks] = {};
+    bool have_oev = false;
+    prt::Counters *h_ctr2 = nullptr;  // pinned: the second half's counters
+    float last_ms_geo = 0.f, last_ms_xfer = 0.f;
+    bool last_was_overlap = false;
+    int last_chunks = 0;
+
     // batched form (rt_render_batch)
     cudaStream_t bstream = nullptr;       // private stream: graph capture needs a non-legacy stream
     cudaEvent_t bev[3] = {nullptr, nullptr, nullptr};

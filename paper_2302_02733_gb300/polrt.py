@@ -50,7 +50,8 @@ class rt_counters(C.Structure):
                 ("emitting_points", C.c_uint64), ("arena_blocks_used", C.c_uint64),
                 ("arena_blocks_total", C.c_uint64), ("n_horizon", C.c_uint32), ("n_escape", C.c_uint32),
                 ("n_nmax", C.c_uint32), ("n_nan", C.c_uint32), ("n_overflow", C.c_uint32),
-                ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float), ("ms_total", C.c_float)]
+                ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float), ("ms_total", C.c_float),
+                ("chunks", C.c_uint32)]
 
 
 class rt_mlp_norm(C.Structure):
@@ -72,6 +73,10 @@ class rt_batch_config(C.Structure):
 
 _lib = None
 _VP = C.c_void_p
+
+
+class rt_render_config(C.Structure):
+    _fields_ = [("geo_blocks_per_sm", C.c_int), ("xfer_blocks_per_sm", C.c_int), ("chunks", C.c_int)]
 
 
 def lib():
@@ -112,6 +117,8 @@ def lib():
         L.rt_batch_autotune.argtypes = [_VP, C.c_int, C.POINTER(rt_job), C.c_int, C.POINTER(rt_batch_config)]
         L.rt_set_batch_config.argtypes = [_VP, C.c_int, C.POINTER(rt_batch_config)]
         L.rt_get_batch_config.argtypes = [_VP, C.c_int, C.POINTER(rt_batch_config)]
+        L.rt_set_render_config.argtypes = [_VP, C.POINTER(rt_render_config)]
+        L.rt_get_render_config.argtypes = [_VP, C.POINTER(rt_render_config)]
         L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
         L.rt_error_string.restype = C.c_char_p
@@ -351,6 +358,17 @@ def rt_get_batch_config(ctx, form: int) -> dict:
     b = rt_batch_config()
     _check(lib().rt_get_batch_config(ctx, form, C.byref(b)), "rt_get_batch_config")
     return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
+
+
+def rt_set_render_config(ctx, geo_blocks_per_sm: int = 0, xfer_blocks_per_sm: int = 0, chunks: int = 0):
+    cfg = rt_render_config(geo_blocks_per_sm, xfer_blocks_per_sm, chunks)
+    _check(lib().rt_set_render_config(ctx, C.byref(cfg)), "rt_set_render_config")
+
+
+def rt_get_render_config(ctx) -> dict:
+    cfg = rt_render_config()
+    _check(lib().rt_get_render_config(ctx, C.byref(cfg)), "rt_get_render_config")
+    return {k: getattr(cfg, k) for k, _ in rt_render_config._fields_}
 
 
 def rt_render_static(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
