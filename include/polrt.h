@@ -130,8 +130,9 @@ typedef struct {
     uint64_t rays, steps, points, emitting_points;
     uint64_t arena_blocks_used, arena_blocks_total;
     uint32_t n_horizon, n_escape, n_nmax, n_nan, n_overflow;
-    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events; summed over the
-                                     * chunks of an overlapped render); 0 after a batch */
+    float ms_geodesic, ms_transfer; /* device time of the two kernels (CUDA events); in an
+                                     * overlapped render the span from the first launch's start
+                                     * to the last one's end; 0 after a batch */
     float ms_total;                 /* device time of the whole render or batch */
     uint32_t chunks;                /* ray chunks of the last rt_render (each one geodesic and one
                                      * transfer launch); 0 after a batch */
@@ -289,12 +290,15 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
  * own half of the workspace in turn, and the geodesic kernel of chunk i + 1 runs on one
  * internal stream beside the transfer kernel of chunk i on another, so the FP64 geodesic and
  * the FP32 transfer share the SMs. chunks 1 runs the phases one after the other on the
- * context's stream. chunks 0 (the default, with {0, 0, 0}) is automatic: images of 2^19 rays
- * or more are overlapped in 4 to 16 chunks of about 2^17 rays, with the geodesic at 1 block per
- * SM (2 for RT_FP64) and the transfer at its occupancy; smaller images run in one pass of each
- * kernel, whose per-chunk tails would cost more than the overlap saves. The image is the same
- * either way (every ray takes the same arithmetic); only the time differs. Shapes that exceed
- * the kernels' occupancy or chunks above 64 return RT_ERR_INVALID. */
+ * context's stream. chunks 0 (the default, with {0, 0, 0}) is automatic: RT_MIXED and RT_UNPOL
+ * images of 2^19 rays or more are overlapped in 4 to 16 chunks of about 2^17 rays, with the
+ * geodesic at 1 block per SM and the transfer at its occupancy; smaller images, and the RT_FP64
+ * form, run one pass of each kernel.
+ * Independently of the shape, a full render records each pixel's step count, and the next
+ * render of the same camera and integrator takes its rays longest first (dealt round-robin to
+ * the chunks), so that no launch ends waiting for a few long photon-ring rays. The image is the
+ * same either way (every ray takes the same arithmetic); only the time differs. Shapes that
+ * exceed the kernels' occupancy or chunks above 64 return RT_ERR_INVALID. */
 typedef struct {
     int geo_blocks_per_sm;
     int xfer_blocks_per_sm;

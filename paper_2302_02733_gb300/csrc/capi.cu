@@ -107,6 +107,9 @@ int rt_destroy(rt_ctx *c) {
     if (c->have_oev)
         for (int i = 0; i < 4 * rt_ctx::kMaxChunks; i++) cudaEventDestroy(c->oev[i]);
     if (c->h_ctr2) cudaFreeHost(c->h_ctr2);
+    cudaFree(c->d_steps);
+    cudaFree(c->d_order);
+    cudaFree(c->d_ohist);
     if (c->ws_owned) cudaFree(c->ws);
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
@@ -300,22 +303,61 @@ static int ensure_overlap(rt_ctx *c) {
 // workspace, each half with its own counters, ray records and arena. Chunk i's geodesic runs on
 // ostream[0] once the transfer of chunk i - 2 (the same half) has finished, and its transfer on
 // ostream[1] once its geodesic has; so the geodesic of chunk i + 1 shares the SMs with the
-// transfer of chunk i. Returns RT_ERR_NOMEM when a half cannot hold a chunk of at most
-// kMaxChunks-th of the rays.
+// transfer of chunk i. (A second geodesic stream, letting chunk i + 1's geodesic start beside
+// chunk i's, was slower: the two geodesics crowded the transfer out of the SMs.) Returns
+// RT_ERR_NOMEM when a half cannot hold a chunk of at most kMaxChunks-th of the rays.
+// Step-count and order arrays for npix pixels; a camera or integrator other than the one the
+// recorded steps belong to drops them.
+static int prepare_order(rt_ctx *c, const Camera &cam, long long npix) {
+    const double key[8] = {cam.a, cam.r_cam, cam.theta_o, cam.fov, (double)cam.nx, (double)cam.ny, cam.eps,
+                           (double)cam.nmax};
+    if (memcmp(key, c->order_key, sizeof(key)) != 0) {
+        memcpy(c->order_key, key, sizeof(key));
+        c->have_steps = false;
+        c->order_K = 0;
+    }
+    if (npix > c->order_cap) {
+        cudaFree(c->d_steps);
+        cudaFree(c->d_order);
+        c->d_steps = nullptr;
+        c->d_order = nullptr;
+        c->order_cap = 0;
+        c->have_steps = false;
+        c->order_K = 0;
+        if (cudaMalloc(&c->d_steps, sizeof(uint16_t) * npix) != cudaSuccess ||
+            cudaMalloc(&c->d_order, sizeof(int) * npix) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ERR_NOMEM;
+        }
+        c->order_cap = npix;
+    }
+    if (!c->d_ohist && cudaMalloc(&c->d_ohist, sizeof(unsigned) * kOrderBuckets) != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_NOMEM;
+    }
+    return RT_OK;
+}
+
+// Chunks of an overlapped render of nrays rays: at least `chunks`, more when a workspace half
+// cannot hold that many rays; -1 when that would need more than kMaxChunks.
+static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks) {
+    const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
+    const size_t off_rec = align_up(sizeof(Counters));
+    if (half < off_rec + 4 * kAlign + kPerRayBytes) return -1;
+    long long cap = (long long)((half - off_rec - 4 * kAlign) / kPerRayBytes);
+    long long K = std::min<long long>(std::max<long long>(chunks, (nrays + cap - 1) / cap), nrays);
+    return K > rt_ctx::kMaxChunks ? -1 : K;
+}
+
 static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, const Model &mod, const int *list,
-                          long long nrays, int chunks, void *d_out, uint8_t *d_status, void *d_depth, int geo_grid,
-                          int xf_grid) {
+                          uint16_t *steps_out, long long nrays, long long K, void *d_out, uint8_t *d_status,
+                          void *d_depth, int geo_grid, int xf_grid) {
     int rv = ensure_overlap(c);
     if (rv) return rv;
     const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
     const size_t off_rec = align_up(sizeof(Counters));
-    // the most rays a half holds at the arena budget per ray
-    if (half < off_rec + 4 * kAlign + kPerRayBytes) return RT_ERR_NOMEM;
-    long long cap = (long long)((half - off_rec - 4 * kAlign) / kPerRayBytes);
-    long long K = std::max<long long>(chunks, (nrays + cap - 1) / cap);
-    K = std::min<long long>(K, nrays);
-    if (K > rt_ctx::kMaxChunks) return RT_ERR_NOMEM;
-    const long long chunk = (nrays + K - 1) / K;
+    // chunk k: n / K rays, one more for k < n % K (the layout of a longest-first order)
+    const long long base_n = nrays / K, extra = nrays % K, chunk = base_n + (extra ? 1 : 0);
     Counters *ctr[2];
     RayRecord *rec[2];
     Arena ar[2];
@@ -339,11 +381,12 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     CK(cudaStreamWaitEvent(st, c->ev[0], 0));
     for (long long i = 0; i < K; i++) {
         const int h = (int)(i & 1);
-        const long long o = i * chunk, n = std::min(chunk, nrays - o);
+        const long long o = i * base_n + std::min(i, extra), n = base_n + (i < extra ? 1 : 0);
         if (i >= 2) CK(cudaStreamWaitEvent(sg, te[i - 2], 0));
         CK(cudaMemsetAsync(ctr[h], 0, 4 * sizeof(unsigned long long), sg));  // queues + arena
         GeoArgs ga{cam, c->d_sctab, ar[h], rec[h], ctr[h], n, o};
         ga.pix_list = list;
+        ga.steps_out = steps_out;
         XferArgs xa{cam, mod, ar[h], rec[h], ctr[h], n, o, d_out, d_status, d_depth};
         xa.pix_list = list;
         xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
@@ -361,8 +404,7 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
         CK(cudaEventRecord(te[i], st));
         CK(cudaGetLastError());
     }
-    CK(cudaStreamWaitEvent(c->stream, ge[K - 1], 0));
-    CK(cudaStreamWaitEvent(c->stream, te[K - 1], 0));
+    CK(cudaStreamWaitEvent(c->stream, te[K - 1], 0));  // after every geodesic and transfer (in order)
     CK(cudaEventRecord(c->ev[2], c->stream));
     CK(cudaMemcpyAsync(c->h_ctr2, ctr[1], sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(c->h_ctr, ctr[0], sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
@@ -373,11 +415,10 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     a.emitting += b.emitting;
     a.arena_next = std::max(a.arena_next, b.arena_next);
     for (int k = 0; k < 8; k++) a.n_status[k] += b.n_status[k];
-    float g = 0.f, x = 0.f, ms = 0.f;
-    for (long long i = 0; i < K; i++) {
-        if (cudaEventElapsedTime(&ms, gs[i], ge[i]) == cudaSuccess) g += ms;
-        if (cudaEventElapsedTime(&ms, ts[i], te[i]) == cudaSuccess) x += ms;
-    }
+    // spans: first geodesic start to last geodesic end, first transfer start to last end
+    float g = 0.f, x = 0.f;
+    if (cudaEventElapsedTime(&g, gs[0], ge[K - 1]) != cudaSuccess) g = 0.f;
+    if (cudaEventElapsedTime(&x, ts[0], te[K - 1]) != cudaSuccess) x = 0.f;
     cudaGetLastError();
     c->last_ms_geo = g;
     c->last_ms_xfer = x;
@@ -410,13 +451,16 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     // outputs (16 + 32 bytes)
     const size_t per_ray = kPerRayBytes + (sur ? (size_t)kBudgetBlocksPerRay * kBlockStates * 48 : 0);
 
-    // launch shape: the configured one, or automatic (overlapped chunks of about 2^17 rays for
-    // images of 2^19 rays or more, the geodesic at 1 block per SM, 2 for the FP64 form, beside
-    // the transfer at its occupancy; one pass of each kernel below that)
+    // launch shape: the configured one, or automatic. The FP32 forms overlap images of 2^19 rays
+    // or more in chunks of about 2^17 rays, the geodesic at 1 block per SM beside the transfer
+    // at its occupancy. Smaller images, and the FP64 form (whose FP64 transfer competes with
+    // the geodesic for the same pipe), run one pass of each kernel.
     int chunks = c->rcfg.chunks, geo_b = c->rcfg.geo_blocks_per_sm;
     if (chunks == 0) {
-        chunks = nrays >= (1ll << 19) ? (int)std::min<long long>(16, std::max<long long>(4, nrays >> 17)) : 1;
-        if (chunks >= 2 && geo_b == 0) geo_b = form == RT_FP64 ? std::min(2, c->geo_bps) : 1;
+        chunks = nrays >= (1ll << 19) && form != RT_FP64
+                     ? (int)std::min<long long>(16, std::max<long long>(4, nrays >> 17))
+                     : 1;
+        if (chunks >= 2 && geo_b == 0) geo_b = 1;
     }
     const bool ovl = chunks >= 2 && !sur && nrays >= 2;
     // the overlapped form holds two chunks at a time, each half with its own counters
@@ -426,6 +470,25 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
                   2 * (long long)((align_up(sizeof(Counters)) + 4 * kAlign + per_ray - 1) / per_ray) + 1;
     int rv = ensure_workspace(c, ws_rays, per_ray);
     if (rv) return rv;
+    long long K = 1;
+    if (ovl && (K = overlap_chunks(c, nrays, chunks)) < 0) return RT_ERR_NOMEM;
+
+    // ray order: longest first once a full render of this camera has recorded its step counts
+    const int *ray_list = list;
+    uint16_t *steps_out = nullptr;
+    if (!list) {
+        rv = prepare_order(c, cam, npix_img);
+        if (rv) return rv;
+        steps_out = c->d_steps;
+        if (c->have_steps) {
+            if (c->order_K != (int)K) {
+                launch_order_build(c->d_steps, npix_img, (int)K, c->d_ohist, c->d_order, c->stream);
+                CK(cudaGetLastError());
+                c->order_K = (int)K;
+            }
+            ray_list = c->d_order;
+        }
+    }
     const size_t per_block = kBlockBytes + (sur ? (size_t)kBlockStates * 48 : 0);
     char *base = (char *)c->ws;
     Counters *ctr = (Counters *)base;
@@ -479,8 +542,8 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         c->nsm * (c->rcfg.xfer_blocks_per_sm > 0 ? std::min(c->rcfg.xfer_blocks_per_sm, xf_max) : xf_max);
     c->last_was_overlap = false;
     if (ovl) {
-        rv = render_overlap(c, form, coef, cam, mod, list, nrays, chunks, d_out, d_status, d_depth, geo_grid,
-                            xf_grid);
+        rv = render_overlap(c, form, coef, cam, mod, ray_list, steps_out, nrays, K, d_out, d_status, d_depth,
+                            geo_grid, xf_grid);
         if (rv) return rv;
         c->last_was_overlap = true;
     } else {
@@ -490,9 +553,10 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
             long long n = std::min(chunk, nrays - o);
             CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));  // queues + arena
             GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
-            ga.pix_list = list;
+            ga.pix_list = ray_list;
+            ga.steps_out = steps_out;
             XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
-            xa.pix_list = list;
+            xa.pix_list = ray_list;
             xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
             if (sur) {
                 xa.feat = feat;
@@ -540,6 +604,7 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     c->last_rays = nrays;
     c->last_was_batch = false;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
+    if (steps_out) c->have_steps = true;  // every ray of this camera recorded its steps
     return RT_OK;
 }
 

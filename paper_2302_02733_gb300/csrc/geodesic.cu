@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
     const Camera &c = p.cam;
     double y[7];
     long long ray = -1;
-    int n = 0, blk = -1, slot = kBlockStates;
+    int n = 0, blk = -1, slot = kBlockStates, pix = 0;
     bool live = false, drained = false;
     unsigned long long my_steps = 0;
     for (;;) {
@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
                 ray = (long long)t;
                 int ix, iy;
                 map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
+                pix = iy * c.nx + ix;
                 ray_start(c, ix, iy, y);
                 n = 0;
                 blk = -1;
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             rec.nstates = ok ? n + 1 : 0;
             rec.status = status;
             p.rec[ray] = rec;
+            if (p.steps_out) p.steps_out[pix] = (uint16_t)min(n, 65535);
             my_steps += (unsigned long long)n;
             atomicAdd(&p.ctr->n_status[status], 1u);
             live = false;

@@ -54,6 +54,16 @@ struct rt_ctx {
     cudaEvent_t oev[4 * kMaxChunks] = {};
     bool have_oev = false;
     prt::Counters *h_ctr2 = nullptr;  // pinned: the second half's counters
+
+    // longest-first ray order (order.cu), from the step counts of the last full render of the
+    // same camera and integrator
+    uint16_t *d_steps = nullptr;  // per pixel
+    int *d_order = nullptr;       // pixel of each ray
+    unsigned *d_ohist = nullptr;  // kOrderBuckets counters
+    long long order_cap = 0;      // pixels the two arrays hold
+    double order_key[8] = {};     // camera and integrator the steps belong to
+    bool have_steps = false;
+    int order_K = 0;              // chunks d_order is dealt to; 0: not built
     float last_ms_geo = 0.f, last_ms_xfer = 0.f;
     bool last_was_overlap = false;
     int last_chunks = 0;

@@ -15,7 +15,8 @@ struct GeoArgs {
     Counters *ctr;
     long long nrays;      // rays in this chunk
     long long ray_offset; // global id of the chunk's first ray
-    const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering)
+    const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering, ray order)
+    uint16_t *steps_out;  // optional: per pixel (row-major), the ray's RK4 step count (capped at 65535)
 };
 
 struct XferArgs {
@@ -100,6 +101,12 @@ int launch_kappa_tables(double *lnk, double *gl16, cudaStream_t s);  // gl16: 8 
 void launch_kappa_quad(const KappaTables &T, const double *in, double *out, long long n, int grid, cudaStream_t s);
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
+// Longest-first ray order from the step counts of a previous render of the same camera:
+// order[i] is the pixel of ray i, by step count descending (16-step buckets), dealt round-robin
+// to K chunks; chunk k holds n / K + (k < n % K) rays from index k (n / K) + min(k, n % K).
+// hist: kOrderBuckets unsigned of scratch.
+constexpr int kOrderBuckets = 1024;
+void launch_order_build(const uint16_t *steps, long long n, int K, unsigned *hist, int *order, cudaStream_t s);
 void launch_sincos_table(double *tab, cudaStream_t s);
 constexpr size_t kSinTabBytes = 1024 * 3 * sizeof(double);
 // coef: 0 thermal fits, 1 kappa quadrature at every emitting point, 2 surrogate outputs

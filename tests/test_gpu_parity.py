@@ -89,6 +89,28 @@ def test_adaf_fp64_64(rt, ora, synth):
     print(f"adaf64 fp64: max err {err[~mask].max():.2e}, mask {mask.sum()} px")
 
 
+def test_adaf_against_stored_oracle_image(rt, synth):
+    """The FP64 and mixed forms against the stored oracle image (tests/golden/adaf16_i60.txt,
+    written by tests/golden/make_golden.py): FP64 within 1e-9 per pixel outside its stored
+    sensitivity mask, mixed within 5e-6 at the 99th percentile."""
+    import os
+
+    d = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "adaf16_i60.txt"))
+    ref = d[:, 2:6].reshape(16, 16, 4)
+    mask = d[:, 8].reshape(16, 16) > 0
+    polrt = rt[0]
+    cam = synth.Camera(incl_deg=60.0, nx=16, ny=16)
+    for form, tol in ((polrt.RT_FP64, 1e-9), (polrt.RT_MIXED, 5e-6)):
+        rc, gpu, st, cnt = gpu_render(rt, cam, polrt.adaf_model(synth.adaf_params(1)), form)
+        assert rc == 0
+        assert np.array_equal(st.astype(int), d[:, 7].reshape(16, 16).astype(int))
+        err = per_pixel_error(gpu, ref)
+        if form == polrt.RT_FP64:
+            assert err[~mask].max() <= tol, err.max()
+        else:
+            assert np.percentile(err, 99) <= tol, np.percentile(err, 99)
+
+
 @pytest.mark.parametrize("nx,ny", [(32, 32), (30, 22)])
 def test_grid_fp64_small_images(rt, ora, synth, torus_grid, nx, ny):
     prims, g = torus_grid
@@ -104,8 +126,12 @@ def test_grid_fp64_small_images(rt, ora, synth, torus_grid, nx, ny):
 
 
 def test_grid_fp64_1024_sampled(rt, ora, synth, torus_grid):
-    """The benchmark workload (torus grid, 1024x1024, i = 20 deg) at full size; the oracle
-    checks 256 seeded pixels one by one."""
+    """The benchmark workload (torus grid, 1024x1024, i = 20 deg) at full size, in the launch
+    shapes the benchmark times (automatic: one pass for the FP64 form, 8 overlapped chunks for
+    the mixed form, rays longest first from the second render on); the oracle checks 256
+    seeded pixels one by one. The FP64 form is held to 1e-9 outside the sensitivity mask; the mixed
+    form (the benchmark's form) to 2e-3 on every sampled pixel and 1e-5 at the median (on the
+    whole image it measures p99 9e-5, max 8e-4 against the FP64 form)."""
     prims, g = torus_grid
     cam = synth.Camera(incl_deg=20.0, nx=1024, ny=1024)
     polrt = rt[0]
@@ -121,7 +147,12 @@ def test_grid_fp64_1024_sampled(rt, ora, synth, torus_grid):
     scale = np.maximum(ref[:, 0], 1e-8 * gpu[..., 0].max())
     err = np.abs(g_px - ref).max(axis=-1) / scale
     assert err[~mask].max() <= 1e-9, err[~mask].max()
-    assert cnt["n_overflow"] == 0 and cnt["rays"] == 1024 * 1024
+    assert cnt["n_overflow"] == 0 and cnt["rays"] == 1024 * 1024 and cnt["chunks"] == 1
+    rc, mix, st_m, cnt_m = gpu_render(rt, cam, polrt.grid_model(torch.from_numpy(prims).cuda(), g), polrt.RT_MIXED)
+    assert rc == 0 and cnt_m["chunks"] == 8 and np.array_equal(st_m, st)
+    err_m = np.abs(mix[iy, ix] - ref).max(axis=-1) / scale
+    print(f"mixed 1024 sampled: median {np.median(err_m):.1e} max {err_m.max():.1e}")
+    assert err_m.max() <= 2e-3 and np.median(err_m) <= 1e-5
 
 
 def net_pol(img):
