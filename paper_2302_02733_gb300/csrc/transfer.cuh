@@ -35,6 +35,7 @@ struct Mth<double> {
     static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { sincos(x, s, c); }
     static __device__ __forceinline__ double sin_(double x) { return sin(x); }
     static __device__ __forceinline__ double cos_(double x) { return cos(x); }
+    static __device__ __forceinline__ double atan2_(double y, double x) { return atan2(y, x); }
     static __device__ __forceinline__ double sinh_(double x) { return sinh(x); }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
     static __device__ __forceinline__ double fmod_(double x, double y) { return fmod(x, y); }
@@ -57,6 +58,7 @@ struct Mth<float> {
     static __device__ __forceinline__ void sincos_(float x, float *s, float *c) { sincosf(x, s, c); }
     static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
     static __device__ __forceinline__ float cos_(float x) { return cosf(x); }
+    static __device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
     static __device__ __forceinline__ float sinh_(float x) { return sinhf(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
     static __device__ __forceinline__ float fmod_(float x, float y) { return fmodf(x, y); }

@@ -139,18 +139,84 @@ struct XLane {
 // evaluate the plasma, and where it emits, re-project onto the fluid screen and take the
 // exact constant-coefficient step. m returns the metric at the state. Returns whether the
 // point emits.
+// The surrogate's maps (surrogate.cuh) in the transfer's precision R, from the tetrad's sin and
+// cos of the field angle (sth >= 0) instead of the angle, for the FP32 render: the prefactors are
+// written as in the thermal fits (nu_B / nu and e^2 / (m c) grouped) so every intermediate
+// stays within FP32 range.
+template <typename R>
+struct SurPrefR {
+    R Pj, PjV, Pa, PaV, PrQ, PrV, sgn;
+};
+
+template <typename R>
+__device__ __forceinline__ SurPrefR<R> sur_prefactors_r(R ne, R Te, R B, R nu, R sth, R cth) {
+    typedef Mth<R> F;
+    const R cB = R(kQe / (2.0 * kPi * kMe * kC));             // nu_B / B
+    const R cQ2 = R(kQe * kQe / (kMe * kC));                  // e^2 / (m c)
+    const R cJ = R(kQe * kQe / (2.0 * 1.7320508075688772 * kC));
+    SurPrefR<R> p;
+    R as = fabs(sth), ac = fabs(cth);
+    R rb = cB * B / nu;
+    R cot = as > R(0) ? ac / as : R(0);
+    p.Pj = cJ * ne * nu / (Te * Te);
+    p.PjV = p.Pj * (R(4) / (R(3) * Te)) * cot;
+    p.Pa = cQ2 * ne / (R(4.0 * 1.7320508075688772) * nu * Te * Te * Te);
+    p.PaV = p.Pa * cot;
+    R X = Te * F::sqrt_(R(1.4142135623730951) * as * R(1e3) * rb);
+    R f = R(2.011) * F::exp_(-F::pow_(X, R(1.035)) / R(4.7)) -
+          F::cos_(R(0.5) * X) * F::exp_(-F::pow_(X, R(1.2)) / R(2.73)) - R(0.011) * F::exp_(-X / R(47.2));
+    if (X > R(1))
+        f += (R(0.011) * F::exp_(-X / R(47.2)) - R(369.6934286909082) * F::pow_(X, R(-8.0 / 3.0))) * R(0.5) *
+             (R(1) + F::tanh_(R(10) * F::log_(X / R(120))));
+    p.PrQ = cQ2 * ne * rb * rb / nu * sth * sth * f;
+    p.PrV = R(2) * cQ2 * ne * rb / nu * ac * (R(1) - R(0.11) * F::log1p_(R(0.035) * X));
+    p.sgn = cth < R(0) ? R(-1) : R(1);
+    return p;
+}
+
+template <typename R>
+__device__ __forceinline__ void sur_features_r(R Te, R B, R nu, R sth, R cth, R kappa, float f[4]) {
+    typedef Mth<R> F;
+    const R cB = R(kQe / (2.0 * kPi * kMe * kC));
+    R tf = F::atan2_(sth, fabs(cth));  // theta_B folded into [0, pi/2]
+    f[0] = (float)(-F::log_(R(1.5) * cB * B / nu * sth * Te * Te));
+    f[1] = (float)tf;
+    f[2] = (float)F::log_(Te);
+    f[3] = (float)kappa;
+}
+
+template <typename R>
+__device__ __forceinline__ void sur_expand_r(const SurPrefR<R> &p, const float y[8], R c[8]) {
+    typedef Mth<R> F;
+    c[0] = p.Pj * F::exp_(R(y[0]));
+    c[1] = p.Pj * F::exp_(R(y[1]));
+    c[2] = p.sgn * p.PjV * F::exp_(R(y[2]));
+    c[3] = p.Pa * F::exp_(R(y[3]));
+    c[4] = p.Pa * F::exp_(R(y[4]));
+    c[5] = p.sgn * p.PaV * F::exp_(R(y[5]));
+    c[6] = p.PrQ * F::exp_(R(y[6]));
+    c[7] = p.sgn * p.PrV * F::exp_(R(y[7]));
+    R pj = F::sqrt_(c[1] * c[1] + c[2] * c[2]);
+    if (pj > c[0] && pj > R(0)) {
+        c[1] *= c[0] / pj;
+        c[2] *= c[0] / pj;
+    }
+    R pa = F::sqrt_(c[4] * c[4] + c[5] * c[5]);
+    if (pa > c[3] && pa > R(0)) {
+        c[4] *= c[3] / pa;
+        c[5] *= c[3] / pa;
+    }
+}
+
 // Coefficients of an emitting point for kappa electrons: CM 1 by quadrature, CM 2 from the
 // surrogate's outputs for this saved state (quadrature outside the network's box).
 template <typename R, int CM>
 __device__ __forceinline__ void kappa_point_coeffs(const XferArgs *pa, long long st, const Model &mdl,
                                                    const Plasma<R> &pl, R w, R sth, R cth, R nu_obs, R cf[8]) {
     typedef Mth<R> F;
-    double thB = atan2((double)sth, (double)cth), nu = (double)(w * nu_obs);
-    double cd[8];
-    bool done = false;
-    if (CM == 2) {
+    if (CM == 2) {  // the network, in R, inside its box
         float f[4], xn[4];
-        sur_features((double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, f);
+        sur_features_r<R>(pl.Te, pl.B, w * nu_obs, sth, cth, R(mdl.kappa), f);
         bool in = true;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -168,12 +234,17 @@ __device__ __forceinline__ void kappa_point_coeffs(const XferArgs *pa, long long
                 for (int q = 0; q < kSurBasis; q++) b += nm[16 + k * kSurBasis + q] * phi[q];
                 y[k] = b + nm[k] + nm[8 + k] * yh[k];
             }
-            SurPref p = sur_prefactors((double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB);
-            sur_expand(p, y, cd);
-            done = true;
+            sur_expand_r<R>(sur_prefactors_r<R>(pl.ne, pl.Te, pl.B, w * nu_obs, sth, cth), y, cf);
+            if (!(cf[0] > F::jflush))
+#pragma unroll
+                for (int k = 0; k < 6; k++) cf[k] = R(0);
+            return;
         }
     }
-    if (!done) kappa_coeffs_quad(pa->kt, (double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, cd);
+    // quadrature (CM 1, or CM 2 outside the network's box), in FP64
+    double thB = atan2((double)sth, (double)cth), nu = (double)(w * nu_obs);
+    double cd[8];
+    kappa_coeffs_quad(pa->kt, (double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, cd);
 #pragma unroll
     for (int k = 0; k < 8; k++) cf[k] = R(cd[k]);
     if (!(cf[0] > F::jflush))  // as for the thermal fits: no relative precision left
@@ -433,9 +504,8 @@ __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
         if (pl.valid) {
             R e1[4], e2[4], w, sth, cth;
             fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
-            double thB = atan2((double)sth, (double)cth), nu = (double)(w * nu_obs);
             float f[4], xn[4];
-            sur_features((double)pl.Te, (double)pl.B, nu, thB, p.model.kappa, f);
+            sur_features_r<R>(pl.Te, pl.B, w * nu_obs, sth, cth, R(p.model.kappa), f);
             if (p.feat_raw) {
                 unsigned long long k = atomicAdd(&p.ctr->feat_count, 1ull);
                 if ((long long)k < p.feat_cap) p.feat_raw[k] = make_float4(f[0], f[1], f[2], f[3]);
