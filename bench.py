@@ -120,8 +120,8 @@ def workload(size):
     return cam, prims, g
 
 
-def oracle_sample(cam, prims, g, npix, seed=0):
-    """Time the CPU oracle (as it stands, all host cores) on npix strided pixels."""
+def oracle_sample(cam, prims, g, npix, seed=0, nthreads=0):
+    """Time the CPU oracle (as it stands; all host cores, or nthreads) on npix strided pixels."""
     import numpy as np
 
     import oracle
@@ -132,7 +132,7 @@ def oracle_sample(cam, prims, g, npix, seed=0):
     ix, iy = ix.ravel()[:npix], iy.ravel()[:npix]
     ocam, om = oracle.camera(cam), oracle.grid_model(prims, g)
     t = time.perf_counter()
-    oracle.render_pixels(ocam, om, ix, iy)
+    oracle.render_pixels(ocam, om, ix, iy, nthreads=nthreads)
     dt = time.perf_counter() - t
     return ix.size / dt, ix.size, stride, dt
 
@@ -443,8 +443,11 @@ def main():
 
         oracle.build()
         rate, n, stride, dt = oracle_sample(cam, prims, g, 8192)
+        rate1, n1, stride1, dt1 = oracle_sample(cam, prims, g, 512, nthreads=1)
         cpu = {"value": rate, "unit": "pixels/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} pixels (stride {stride}) of the {cam.nx}^2 image, {dt:.1f} s"}
+               "sample": f"{n} pixels (stride {stride}) of the {cam.nx}^2 image, {dt:.1f} s",
+               "single_thread": {"value": rate1, "unit": "pixels/s", "cores": 1,
+                                 "sample": f"{n1} pixels (stride {stride1}) of the {cam.nx}^2 image, {dt1:.1f} s"}}
 
     polrt.rt_destroy(ctx)
     if rank == 0:
