@@ -112,6 +112,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(v, device="cpu"):
+    """The largest v over the ranks of the process group (v itself outside one)."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, npix, seconds):
+    """Whole-job throughput: every rank renders its own npix-pixel image (replicas), so the
+    job does ws * npix pixels in the slowest rank's time."""
+    return ws * npix / seconds
+
+
 def workload(size):
     from paper_2302_02733_gb300 import synth
 
@@ -337,12 +354,8 @@ def main():
         torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * npix / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dev)
+    value = job_rate(ws, npix, ms_max / 1e3)
 
     # per-kernel roofline of the dominant kernel (measured live with CUDA events in the library).
     # In the overlapped launch shape the geodesic of one chunk shares the SMs with the transfer of
@@ -422,12 +435,8 @@ def main():
             polrt.rt_render(ctx, form, host_out)
             polrt.rt_image_stats(ctx, host_out, form)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.steps
-        if ws > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * npix / dt, "unit": "pixels/s", "h2d_bytes_per_step": int(prims.nbytes),
+        dt = max_over_ranks((time.perf_counter() - t0) / args.steps, dev)
+        e2e = {"value": job_rate(ws, npix, dt), "unit": "pixels/s", "h2d_bytes_per_step": int(prims.nbytes),
                "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()), "ms_per_step": dt * 1e3}
 
     # batched form: the 96-image library in one persistent launch per batch (graph replay)
