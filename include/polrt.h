@@ -293,7 +293,8 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
  * context's stream. chunks 0 (the default, with {0, 0, 0}) is automatic: RT_MIXED and RT_UNPOL
  * images of 2^19 rays or more are overlapped in 4 to 16 chunks of about 2^17 rays, with the
  * geodesic at 1 block per SM and the transfer at its occupancy; smaller images, and the RT_FP64
- * form, run one pass of each kernel.
+ * and RT_SURROGATE forms, run one pass of each kernel (RT_SURROGATE overlaps its features,
+ * network and transfer passes when chunks >= 2 is set).
  * Independently of the shape, a full render records each pixel's step count, and the next
  * render of the same camera and integrator takes its rays longest first (dealt round-robin to
  * the chunks), so that no launch ends waiting for a few long photon-ring rays. The image is the

@@ -282,6 +282,29 @@ static int ensure_stage(void **buf, size_t *have, size_t need) {
     return RT_OK;
 }
 
+// Surrogate-form arguments of a transfer: where the network's inputs and outputs of each
+// saved state live, its normalisation and its input box.
+static void set_surrogate_args(const rt_ctx *c, XferArgs &xa, float4 *feat, float *sur_y) {
+    xa.feat = feat;
+    xa.sur_y = sur_y;
+    xa.sur_norm = reinterpret_cast<const float *>(c->d_mlpaux) + 4;
+    for (int j = 0; j < 4; j++) {
+        xa.sur_lo[j] = c->mlp_norm.lo[j];
+        xa.sur_hi[j] = c->mlp_norm.hi[j];
+    }
+}
+
+// The network's inputs for every saved state of a chunk, then one tensor-core pass over
+// them; the pass reads the number of arena blocks in use on the device.
+static void launch_network_pass(const rt_ctx *c, const XferArgs &xa, float *sur_y, long long nblocks,
+                                const unsigned long long *used_blocks, int xf_grid, cudaStream_t s) {
+    launch_sur_features(xa, xf_grid, s);
+    long long rows = nblocks * kBlockStates;
+    launch_mlp_forward(reinterpret_cast<const float *>(xa.feat), sur_y, rows, c->d_wpk,
+                       reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
+                       (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), s, used_blocks);
+}
+
 // Streams, events and the second pinned counter block of the overlapped render, made on first use.
 static int ensure_overlap(rt_ctx *c) {
     for (int i = 0; i < 2; i++)
@@ -340,11 +363,11 @@ static int prepare_order(rt_ctx *c, const Camera &cam, long long npix) {
 
 // Chunks of an overlapped render of nrays rays: at least `chunks`, more when a workspace half
 // cannot hold that many rays; -1 when that would need more than kMaxChunks.
-static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks) {
+static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks, size_t per_ray) {
     const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
     const size_t off_rec = align_up(sizeof(Counters));
-    if (half < off_rec + 4 * kAlign + kPerRayBytes) return -1;
-    long long cap = (long long)((half - off_rec - 4 * kAlign) / kPerRayBytes);
+    if (half < off_rec + 6 * kAlign + per_ray) return -1;
+    long long cap = (long long)((half - off_rec - 6 * kAlign) / per_ray);
     long long K = std::min<long long>(std::max<long long>(chunks, (nrays + cap - 1) / cap), nrays);
     return K > rt_ctx::kMaxChunks ? -1 : K;
 }
@@ -352,6 +375,10 @@ static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks) {
 static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, const Model &mod, const int *list,
                           uint16_t *steps_out, long long nrays, long long K, void *d_out, uint8_t *d_status,
                           void *d_depth, int geo_grid, int xf_grid) {
+    const bool sur = form == RT_SURROGATE;
+    // per arena block: the states and the prev link, and for the surrogate form the network's
+    // inputs and outputs of each state (16 + 32 bytes)
+    const size_t per_block = kBlockBytes + (sur ? (size_t)kBlockStates * 48 : 0);
     int rv = ensure_overlap(c);
     if (rv) return rv;
     const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
@@ -361,15 +388,23 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     Counters *ctr[2];
     RayRecord *rec[2];
     Arena ar[2];
+    float4 *feat[2] = {nullptr, nullptr};
+    float *sur_y[2] = {nullptr, nullptr};
     for (int h = 0; h < 2; h++) {
         char *base = (char *)c->ws + h * half;
         ctr[h] = (Counters *)base;
         rec[h] = (RayRecord *)(base + off_rec);
         size_t off = align_up(off_rec + sizeof(RayRecord) * chunk);
-        long long nb = (long long)((half - off - 3 * kAlign) / kBlockBytes);
+        long long nb = (long long)((half - off - 5 * kAlign) / per_block);
         ar[h].states = (PathState *)(base + off);
         ar[h].prev = (int *)(base + off + (size_t)nb * sizeof(PathState) * kBlockStates);
         ar[h].nblocks = nb;
+        if (sur) {
+            off = align_up(off + (size_t)nb * kBlockBytes);
+            feat[h] = (float4 *)(base + off);
+            off = align_up(off + (size_t)nb * kBlockStates * sizeof(float4));
+            sur_y[h] = (float *)(base + off);
+        }
     }
     cudaStream_t sg = c->ostream[0], st = c->ostream[1];
     cudaEvent_t *gs = c->oev, *ge = c->oev + rt_ctx::kMaxChunks, *ts = c->oev + 2 * rt_ctx::kMaxChunks,
@@ -390,11 +425,13 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
         XferArgs xa{cam, mod, ar[h], rec[h], ctr[h], n, o, d_out, d_status, d_depth};
         xa.pix_list = list;
         xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+        if (sur) set_surrogate_args(c, xa, feat[h], sur_y[h]);
         CK(cudaEventRecord(gs[i], sg));
         launch_geodesic(ga, geo_grid, sg);
         CK(cudaEventRecord(ge[i], sg));
         CK(cudaStreamWaitEvent(st, ge[i], 0));
         CK(cudaEventRecord(ts[i], st));
+        if (sur) launch_network_pass(c, xa, sur_y[h], ar[h].nblocks, &ctr[h]->arena_next, xf_grid, st);
         if (form == RT_FP64)
             launch_transfer_fp64(xa, coef, xf_grid, st);
         else if (form == RT_UNPOL)
@@ -451,27 +488,28 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     // outputs (16 + 32 bytes)
     const size_t per_ray = kPerRayBytes + (sur ? (size_t)kBudgetBlocksPerRay * kBlockStates * 48 : 0);
 
-    // launch shape: the configured one, or automatic. The FP32 forms overlap images of 2^19 rays
-    // or more in chunks of about 2^17 rays, the geodesic at 1 block per SM beside the transfer
-    // at its occupancy. Smaller images, and the FP64 form (whose FP64 transfer competes with
-    // the geodesic for the same pipe), run one pass of each kernel.
+    // launch shape: the configured one, or automatic. RT_MIXED and RT_UNPOL overlap images of
+    // 2^19 rays or more in chunks of about 2^17 rays, the geodesic at 1 block per SM beside the
+    // transfer at its occupancy. Smaller images run one pass of each kernel, and so do RT_FP64
+    // (its FP64 transfer competes with the geodesic for the same pipe) and RT_SURROGATE (the
+    // network pass beside the geodesic measured slower than one pass: 859 against 536 ms).
     int chunks = c->rcfg.chunks, geo_b = c->rcfg.geo_blocks_per_sm;
     if (chunks == 0) {
-        chunks = nrays >= (1ll << 19) && form != RT_FP64
+        chunks = nrays >= (1ll << 19) && (form == RT_MIXED || form == RT_UNPOL)
                      ? (int)std::min<long long>(16, std::max<long long>(4, nrays >> 17))
                      : 1;
         if (chunks >= 2 && geo_b == 0) geo_b = 1;
     }
-    const bool ovl = chunks >= 2 && !sur && nrays >= 2;
+    const bool ovl = chunks >= 2 && nrays >= 2;
     // the overlapped form holds two chunks at a time, each half with its own counters
     long long ws_rays = nrays;
     if (ovl)
         ws_rays = 2 * ((nrays + chunks - 1) / chunks) +
-                  2 * (long long)((align_up(sizeof(Counters)) + 4 * kAlign + per_ray - 1) / per_ray) + 1;
+                  2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
     int rv = ensure_workspace(c, ws_rays, per_ray);
     if (rv) return rv;
     long long K = 1;
-    if (ovl && (K = overlap_chunks(c, nrays, chunks)) < 0) return RT_ERR_NOMEM;
+    if (ovl && (K = overlap_chunks(c, nrays, chunks, per_ray)) < 0) return RT_ERR_NOMEM;
 
     // ray order: longest first once a full render of this camera has recorded its step counts
     const int *ray_list = list;
@@ -558,30 +596,10 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
             XferArgs xa{cam, mod, ar, rec, ctr, n, o, d_out, d_status, d_depth};
             xa.pix_list = ray_list;
             xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
-            if (sur) {
-                xa.feat = feat;
-                xa.sur_y = sur_y;
-                xa.sur_norm = reinterpret_cast<const float *>(c->d_mlpaux) + 4;
-                for (int j = 0; j < 4; j++) {
-                    xa.sur_lo[j] = c->mlp_norm.lo[j];
-                    xa.sur_hi[j] = c->mlp_norm.hi[j];
-                }
-            }
+            if (sur) set_surrogate_args(c, xa, feat, sur_y);
             if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
             launch_geodesic(ga, geo_grid, c->stream);
-            if (sur) {
-                // the network's inputs for every saved state, then one tensor-core pass over them
-                unsigned long long used = 0;
-                CK(cudaMemcpyAsync(&used, &ctr->arena_next, sizeof(used), cudaMemcpyDeviceToHost, c->stream));
-                CK(cudaStreamSynchronize(c->stream));
-                used = std::min<unsigned long long>(used, (unsigned long long)nblocks);
-                launch_sur_features(xa, xf_grid, c->stream);
-                long long rows = (long long)used * kBlockStates;
-                if (rows > 0)
-                    launch_mlp_forward(reinterpret_cast<const float *>(feat), sur_y, rows, c->d_wpk,
-                                       reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
-                                       (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), c->stream);
-            }
+            if (sur) launch_network_pass(c, xa, sur_y, nblocks, &ctr->arena_next, xf_grid, c->stream);
             if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
             if (form == RT_FP64)
                 launch_transfer_fp64(xa, coef, xf_grid, c->stream);

@@ -114,7 +114,8 @@ void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s)
 void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s);
 void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s);
 void launch_unpol(const XferArgs &a, int grid, cudaStream_t s);  // Stokes I only, FP32
-void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s);
+void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s,
+                        const unsigned long long *used_blocks = nullptr);
 void launch_x2_table(const GridModel &g, double *table, float *table_f, cudaStream_t s);
 // out[7]: sum I, Q, U, V, flux [Jy], net LP, net CP; out holds 8 + 4 kStatBlocks doubles
 constexpr int kStatBlocks = 608;

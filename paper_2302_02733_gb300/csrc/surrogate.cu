@@ -17,7 +17,6 @@ using namespace prt;
 namespace prt {
 int mlp_init_attributes();
 void launch_mlp_pack(const float *th, void *wpk, void *tpk, cudaStream_t s);
-void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s);
 void launch_mlp_grad(const float *x, const float *t, long long n, long long ntot, const void *wpk, const void *tpk,
                      float *grad, float *loss, unsigned *err, cudaStream_t s);
 void launch_mlp_adam(float *th, float *m, float *v, float *grad, float lr, float b1, float b2, float eps, float c1,

@@ -77,3 +77,32 @@ def test_render_config_checks(rt):
     assert polrt.rt_get_render_config(ctx) == {"geo_blocks_per_sm": 1, "xfer_blocks_per_sm": 2, "chunks": 8}
     polrt.rt_set_render_config(ctx, 0, 0, 0)
     assert polrt.rt_get_render_config(ctx) == {"geo_blocks_per_sm": 0, "xfer_blocks_per_sm": 0, "chunks": 0}
+
+
+def test_overlapped_surrogate_is_identical(rt, synth, torus_grid):
+    """The surrogate form through the overlapped shape: per chunk the features pass, the
+    tensor-core network pass (its row count read on the device) and the transfer, in each
+    workspace half. A fixed random network is enough: the check is that the shape does not
+    change the image."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=20.0, nx=160, ny=128)
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    polrt.rt_set_camera(ctx, cam)
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g, kappa=4.5))
+    rng = np.random.default_rng(5)
+    theta = (0.05 * rng.standard_normal(polrt.RT_MLP_PARAMS)).astype(np.float32)
+    # targets near -30 (coefficients about e^-30 of their prefactors, as for cool electrons),
+    # so the FP32 image stays finite
+    norm = polrt.mlp_norm([-5.0, 1e-3, -6.0, 3.2], [40.0, 1.5707963, 4.0, 8.0], [-30.0] * 8, [0.01] * 8)
+    polrt.rt_mlp_set_params(ctx, theta, norm)
+    try:
+        ref, st0, _, c0 = render(polrt, ctx, polrt.RT_SURROGATE, cam, (0, 0, 1))
+        assert c0["chunks"] == 1 and torch.isfinite(ref).all() and ref[..., 0].max() > 0
+        for cfg in ((1, 0, 4), (0, 0, 3)):
+            out, st, _, c = render(polrt, ctx, polrt.RT_SURROGATE, cam, cfg)
+            assert c["chunks"] == cfg[2]
+            assert torch.equal(out, ref) and torch.equal(st, st0), cfg
+            assert c["points"] == c0["points"] and c["steps"] == c0["steps"]
+    finally:
+        polrt.rt_set_render_config(ctx, 0, 0, 0)
