@@ -500,7 +500,7 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
                      : 1;
         if (chunks >= 2 && geo_b == 0) geo_b = 1;
     }
-    const bool ovl = chunks >= 2 && nrays >= 2;
+    bool ovl = chunks >= 2 && nrays >= 2;
     // the overlapped form holds two chunks at a time, each half with its own counters
     long long ws_rays = nrays;
     if (ovl)
@@ -509,7 +509,12 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     int rv = ensure_workspace(c, ws_rays, per_ray);
     if (rv) return rv;
     long long K = 1;
-    if (ovl && (K = overlap_chunks(c, nrays, chunks, per_ray)) < 0) return RT_ERR_NOMEM;
+    // a workspace too small for kMaxChunks overlapped chunks (a caller's, or a nearly full
+    // device) renders in one pass of each kernel per chunk instead
+    if (ovl && (K = overlap_chunks(c, nrays, chunks, per_ray)) < 0) {
+        ovl = false;
+        K = 1;
+    }
 
     // ray order: longest first once a full render of this camera has recorded its step counts
     const int *ray_list = list;

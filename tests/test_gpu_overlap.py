@@ -106,3 +106,25 @@ def test_overlapped_surrogate_is_identical(rt, synth, torus_grid):
             assert c["points"] == c0["points"] and c["steps"] == c0["steps"]
     finally:
         polrt.rt_set_render_config(ctx, 0, 0, 0)
+
+
+def test_small_caller_workspace_falls_back_to_one_pass(rt, synth, torus_grid):
+    """An overlapped shape that a caller's workspace cannot hold in at most 64 chunks renders
+    in one pass of each kernel per chunk instead, with the same image."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=20.0, nx=160, ny=128)
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    polrt.rt_set_camera(ctx, cam)
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
+    ref, st0, _, _ = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 1))
+    # about 1% of the image's rays: 100 sequential chunks, or 200 overlapped ones (over 64)
+    ws = torch.empty(polrt.rt_workspace_hint(ctx) // 100, dtype=torch.uint8, device="cuda")
+    polrt.rt_set_workspace(ctx, ws)
+    try:
+        out, st, _, c = render(polrt, ctx, polrt.RT_MIXED, cam, (1, 0, 8))
+        assert c["chunks"] >= 64 and c["n_overflow"] == 0
+        assert torch.equal(out, ref) and torch.equal(st, st0)
+    finally:
+        polrt.rt_set_workspace(ctx, None)
+        polrt.rt_set_render_config(ctx, 0, 0, 0)
