@@ -216,7 +216,7 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
 def surrogate_leg(polrt, ctx, prims_dev, g, dev, torch, size):
     """Kappa electrons (kappa drawn from U(3, 8) with a fixed seed) on the torus grid: train the
     surrogate on 2^20 quadrature points in the box of the image's features (below), time the
-    RT_SURROGATE image at size^2, judge it against the quadrature image at 128^2, and time both
+    RT_SURROGATE image at size^2, check it against the quadrature image at 128^2, and time both
     forms at 256^2."""
     import math
 
@@ -292,7 +292,7 @@ def surrogate_leg(polrt, ctx, prims_dev, g, dev, torch, size):
             "value": size * size / (m / 1e3), "unit": "pixels/s", "ms_per_image": m,
             "training": {"samples": n, "steps": steps, "batch": 8192, "seconds": train_s,
                          "final_loss": float(curve[-100:].mean())},
-            "judge_128": {"flux_rel_err": abs(fs / fq - 1), "lp": [lq, ls], "cp": [cq, cs]},
+            "vs_quadrature_128": {"flux_rel_err": abs(fs / fq - 1), "lp": [lq, ls], "cp": [cq, cs]},
             "speedup_256_vs_quadrature": t256["quadrature"] / t256["surrogate"]}
 
 

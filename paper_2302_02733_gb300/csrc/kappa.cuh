@@ -1,7 +1,8 @@
 // Synchrotron coefficients of kappa-distributed (or Maxwell-Juttner) electrons by quadrature
 // over the distribution: the nonthermal models of the paper's Section 2.1, integrated
 // numerically as its outlook (Section 4) proposes. This is the accurate path: it makes the
-// surrogate's training set and judges (and stands in for) the surrogate.
+// surrogate's training set, is the reference the surrogate is checked against, and stands in
+// for it outside its box.
 //
 // Definitions, in an isotropic distribution N(g) (g the Lorentz factor, p = sqrt(g^2 - 1)):
 //   kappa:  N = n C g p (1 + (g - 1)/(kappa w))^-(kappa+1), w = (kappa - 3) Theta / kappa;

@@ -1,5 +1,5 @@
 """Images with kappa electrons on the torus grid: the quadrature path against the oracle, and
-the surrogate form against the quadrature path (the judge).
+the surrogate form against the quadrature path (its reference).
 
 - FP64 form (coefficients by quadrature at every emitting point) against the oracle on a 12x12
   image: per pixel within 1e-6 (the two quadratures use different node densities and agree to
@@ -109,7 +109,7 @@ def test_surrogate_image_against_quadrature(rt, synth, torus_grid):
     curve = np.zeros(20000, dtype=np.float32)
     polrt.rt_mlp_train(ctx, xs, tn, 20000, 8192, 2e-3, 33, curve)
     print(f"training loss {curve[:10].mean():.3e} -> {curve[-100:].mean():.3e}")
-    # the judge: quadrature image (mixed form) against the surrogate image
+    # the reference: quadrature image (mixed form) against the surrogate image
     q, cq = render(polrt, ctx, cam, polrt.RT_MIXED)
     s, cs = render(polrt, ctx, cam, polrt.RT_SURROGATE)
     e = rel_err(s, q)

@@ -158,7 +158,7 @@ def test_trained_surrogate_against_quadrature(rt, ora):
     train_s = time.perf_counter() - t0
     print(f"training: {steps} steps in {train_s:.2f} s, loss {curve[:10].mean():.3e} -> {curve[-100:].mean():.3e}")
     assert curve[-100:].mean() < 1e-2 * curve[:10].mean()
-    # judge on fresh points inside the box
+    # check on fresh points inside the box
     pts = physical(box_points(4096, 21))
     d_in = torch.from_numpy(pts).cuda()
     q = torch.zeros((len(pts), 8), dtype=torch.float64, device="cuda")

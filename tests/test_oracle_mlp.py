@@ -1,5 +1,5 @@
 """The FP64 reference of the surrogate network (oracle/mlp.py): its hand-written backward pass
-against central finite differences of its loss (the reference the GPU gradients are judged by),
+against central finite differences of its loss (the reference the GPU gradients are checked against),
 and its target variables against the thermal fits they are built from."""
 import math
 
