@@ -516,22 +516,10 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         K = 1;
     }
 
-    // ray order: longest first once a full render of this camera has recorded its step counts
-    const int *ray_list = list;
-    uint16_t *steps_out = nullptr;
-    if (!list) {
-        rv = prepare_order(c, cam, npix_img);
-        if (rv) return rv;
-        steps_out = c->d_steps;
-        if (c->have_steps) {
-            if (c->order_K != (int)K) {
-                launch_order_build(c->d_steps, npix_img, (int)K, c->d_ohist, c->d_order, c->stream);
-                CK(cudaGetLastError());
-                c->order_K = (int)K;
-            }
-            ray_list = c->d_order;
-        }
-    }
+    // one-pass shape: as many rays per chunk as the workspace holds; the Kseq chunks take the
+    // rays in the same round-robin layout as the overlapped ones (chunk k from k (n / Kseq) +
+    // min(k, n % Kseq)), so that with the longest-first order every chunk holds the same mix
+    // of lengths and none outgrows the arena's per-ray budget
     const size_t per_block = kBlockBytes + (sur ? (size_t)kBlockStates * 48 : 0);
     char *base = (char *)c->ws;
     Counters *ctr = (Counters *)base;
@@ -539,6 +527,25 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     size_t room = c->ws_bytes - off - 3 * kAlign;
     long long chunk = std::min<long long>(nrays, (long long)(room / per_ray));
     if (chunk < 1) return RT_ERR_NOMEM;
+    const long long Kseq = (nrays + chunk - 1) / chunk;
+
+    // ray order: longest first once a full render of this camera has recorded its step counts
+    const int *ray_list = list;
+    uint16_t *steps_out = nullptr;
+    if (!list) {
+        rv = prepare_order(c, cam, npix_img);
+        if (rv) return rv;
+        steps_out = c->d_steps;
+        const long long Kord = ovl ? K : Kseq;
+        if (c->have_steps) {
+            if (c->order_K != Kord) {
+                launch_order_build(c->d_steps, npix_img, (int)Kord, c->d_ohist, c->d_order, c->stream);
+                CK(cudaGetLastError());
+                c->order_K = Kord;
+            }
+            ray_list = c->d_order;
+        }
+    }
     RayRecord *rec = (RayRecord *)(base + off);
     off = align_up(off + sizeof(RayRecord) * chunk);
     long long nblocks = (long long)((c->ws_bytes - off - 3 * kAlign) / per_block);
@@ -591,9 +598,10 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         c->last_was_overlap = true;
     } else {
         CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
-        c->last_chunks = (int)((nrays + chunk - 1) / chunk);
-        for (long long o = 0; o < nrays; o += chunk) {
-            long long n = std::min(chunk, nrays - o);
+        c->last_chunks = (int)Kseq;
+        const long long base_n = nrays / Kseq, extra = nrays % Kseq;
+        for (long long k = 0; k < Kseq; k++) {
+            const long long o = k * base_n + std::min(k, extra), n = base_n + (k < extra ? 1 : 0);
             CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), c->stream));  // queues + arena
             GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n, o};
             ga.pix_list = ray_list;
@@ -602,10 +610,10 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
             xa.pix_list = ray_list;
             xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
             if (sur) set_surrogate_args(c, xa, feat, sur_y);
-            if (o == 0) CK(cudaEventRecord(c->ev[0], c->stream));
+            if (k == 0) CK(cudaEventRecord(c->ev[0], c->stream));
             launch_geodesic(ga, geo_grid, c->stream);
             if (sur) launch_network_pass(c, xa, sur_y, nblocks, &ctr->arena_next, xf_grid, c->stream);
-            if (o == 0) CK(cudaEventRecord(c->ev[1], c->stream));
+            if (k == 0) CK(cudaEventRecord(c->ev[1], c->stream));
             if (form == RT_FP64)
                 launch_transfer_fp64(xa, coef, xf_grid, c->stream);
             else if (form == RT_UNPOL)

@@ -67,9 +67,18 @@ __device__ __forceinline__ void ray_start(const Camera &c, int ix, int iy, doubl
     for (int k = 0; k < 4; k++) y[3 + k] = -e[0][k] + s[0] * e[1][k] + s[1] * e[2][k] + s[2] * e[3][k];
 }
 
+// The camera constants a geodesic step and its stop test read. The batched kernel, whose
+// cameras live in a global job table, keeps them in registers for the life of a ray.
+struct StepCam {
+    double a, eps, r_stop, r_cam;
+    int nmax;
+};
+__device__ __forceinline__ StepCam step_cam(const Camera &c) { return StepCam{c.a, c.eps, c.r_stop, c.r_cam, c.nmax}; }
+
 // One step from y: yn, the step h, and whether it crossed the polar axis (then theta is
-// reflected, phi advanced by pi and K^theta reversed).
-__device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const Camera &c, const double y[7],
+// reflected, phi advanced by pi and K^theta reversed). C is Camera or StepCam.
+template <class C>
+__device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const C &c, const double y[7],
                                          double yn[7], double &h) {
     h = step_size(c.eps, y);
     rk4_step(tab, c.a, h, y, yn);
@@ -90,7 +99,8 @@ __device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const C
 }
 
 // Stop test after n steps, in order: non-finite, horizon, escape, step limit; 0 to go on.
-__device__ __forceinline__ uint8_t geo_stop(const Camera &c, const double y[7], int n) {
+template <class C>
+__device__ __forceinline__ uint8_t geo_stop(const C &c, const double y[7], int n) {
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < 7; k++) bad |= (__double2hiint(y[k]) & 0x7ff00000) == 0x7ff00000;  // inf or NaN

@@ -95,9 +95,10 @@ __device__ __forceinline__ void publish(const PipeArgs &p, long long ray, const 
     atomicExch(p.ready + pos, (int)ray);
 }
 
-__device__ __forceinline__ void pipe_geodesic(const PipeArgs &p) {
+__device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *tab) {
     const unsigned long long nb = (unsigned long long)p.pool.nblocks;
     double y[7];
+    StepCam sc{};  // the current ray's camera constants
     long long ray = -1, tk = -1;  // tk: pool ticket whose block has not come yet
     int job = 0, n = 0, blk = -1, slot = 0;
     bool live = false, drained = false, cancel = false;
@@ -114,6 +115,7 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p) {
                 int ix, iy;
                 ray_pixel(ray - p.jobs[job].ray_begin, c.nx, c.ny, ix, iy);
                 ray_start(c, ix, iy, y);
+                sc = step_cam(c);
                 n = 0;
                 blk = -1;
                 slot = kBlockStates;
@@ -172,17 +174,16 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p) {
         }
         backoff = 256;
         if (!go) continue;
-        const Camera &c = p.jobs[job].cam;
         uint8_t status = 0;
         for (int k = 0; k < p.step_tile; k++) {
             double h, yn[7];
-            bool refl = geo_step(p.sctab, c, y, yn, h);
+            bool refl = geo_step(tab, sc, y, yn, h);
             save_state(p.pool, blk, slot, y, refl ? -h : h);
             slot++;
             n++;
 #pragma unroll
             for (int i = 0; i < 7; i++) y[i] = yn[i];
-            status = geo_stop(c, y, n);
+            status = geo_stop(sc, y, n);
             if (status || slot > kBlockStates - 2) break;
         }
         if (status) {
@@ -294,10 +295,12 @@ __device__ __forceinline__ void pipe_transfer(const PipeArgs &p, const R *sgw) {
 template <typename R, typename OutT>
 __global__ void __launch_bounds__(kPipeThreads, sizeof(R) == 4 ? 2 : 1) pipe_kernel(PipeArgs p) {
     __shared__ R sgw[32];
+    __shared__ double tab[3 * kSinTab];  // the geodesic's sin/cos table
     fill_bessel_weights(sgw);
+    for (int i = threadIdx.x; i < 3 * kSinTab; i += blockDim.x) tab[i] = p.sctab[i];
     __syncthreads();
     if ((int)(threadIdx.x >> 5) < p.geo_warps)
-        pipe_geodesic(p);
+        pipe_geodesic(p, tab);
     else
         pipe_transfer<R, OutT>(p, sgw);
 }

@@ -63,7 +63,7 @@ struct rt_ctx {
     long long order_cap = 0;      // pixels the two arrays hold
     double order_key[8] = {};     // camera and integrator the steps belong to
     bool have_steps = false;
-    int order_K = 0;              // chunks d_order is dealt to; 0: not built
+    long long order_K = 0;        // chunks d_order is dealt to; 0: not built
     float last_ms_geo = 0.f, last_ms_xfer = 0.f;
     bool last_was_overlap = false;
     int last_chunks = 0;
