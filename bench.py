@@ -206,11 +206,22 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
         steps = c["steps"]
     m = statistics.mean(ms)
     fp64 = steps * GEO_FLOP_PER_STEP / (m / 1e3) / 1e12
-    return {"workload": "image library: 96 images, N in {128,256,512}, torus grid, mixed form", "images": 96,
-            "pixels": npix, "value": npix / (m / 1e3), "unit": "pixels/s", "ms_per_batch": m,
-            "launch": "one persistent kernel per batch, replayed from a CUDA graph",
-            "shape": polrt.rt_get_batch_config(ctx, polrt.RT_MIXED),
-            "geodesic_fp64_tflops": fp64, "geodesic_fp64_frac": fp64 / FP64_PEAK_TFLOPS}
+    shape = polrt.rt_get_batch_config(ctx, polrt.RT_MIXED)
+    launch = {polrt.RT_BATCH_PERSISTENT: "one persistent kernel per batch, replayed from a CUDA graph",
+              polrt.RT_BATCH_CHUNKS: "the images' rays as one ray space, overlapped chunks of two kernels"}
+    res = {"workload": "image library: 96 images, N in {128,256,512}, torus grid, mixed form", "images": 96,
+           "pixels": npix, "value": npix / (m / 1e3), "unit": "pixels/s", "ms_per_batch": m,
+           "launch": launch[shape["mode"]], "shape": shape,
+           "geodesic_fp64_tflops": fp64, "geodesic_fp64_frac": fp64 / FP64_PEAK_TFLOPS}
+    # the other mode at the autotuner's best shape for it, for comparison
+    other = polrt.RT_BATCH_PERSISTENT if shape["mode"] == polrt.RT_BATCH_CHUNKS else polrt.RT_BATCH_CHUNKS
+    g, t, b = (shape["geo_warps"] or 4), (shape["step_tile"] or 1), (shape["blocks_per_sm"] or 2)
+    polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, g, t, b, other)
+    polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
+    polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
+    mo = polrt.rt_last_counters(ctx)["ms_total"]
+    res["other_mode"] = {"launch": launch[other], "value": npix / (mo / 1e3), "ms_per_batch": mo}
+    return res
 
 
 def surrogate_leg(polrt, ctx, prims_dev, g, dev, torch, size):

@@ -326,27 +326,35 @@ typedef struct {
     void *out_depth;   /* optional device nx*ny*2 depths (see rt_render_depths), or NULL */
 } rt_job;
 
-/* Launch shape of the batched kernel. Each block has 8 warps: geo_warps of them integrate
- * geodesics and the rest run the transfer. step_tile is the number of RK4 steps a lane takes
- * between its queue and pool checks. blocks_per_sm is the number of resident blocks per SM
- * (the grid is that times the SM count). ms is the time the autotuner measured for this shape
- * (0 when set by hand). */
+/* Launch shape of the batched form. mode 0 (RT_BATCH_PERSISTENT) is one persistent launch,
+ * captured in a CUDA graph: each block has 8 warps, geo_warps of them integrate geodesics and
+ * the rest run the transfer; step_tile is the number of RK4 steps a lane takes between its
+ * queue and pool checks; blocks_per_sm is the number of resident blocks per SM (the grid is
+ * that times the SM count). mode 1 (RT_BATCH_CHUNKS) treats the rays of all images as one ray
+ * space and runs it like one large image in the overlapped shape of rt_set_render_config
+ * (chunks of about 2^17 rays, at most 64; the geodesic of one chunk beside the transfer of the
+ * previous), on the context's stream and without a graph; geo_warps, step_tile and
+ * blocks_per_sm are then ignored. ms is the time the autotuner measured for this shape (0
+ * when set by hand). */
 typedef struct {
-    int geo_warps;      /* 1..7 */
-    int step_tile;      /* 1..16 */
-    int blocks_per_sm;  /* 1..(the kernel's occupancy limit) */
+    int geo_warps;      /* 1..7 (mode 0) */
+    int step_tile;      /* 1..16 (mode 0) */
+    int blocks_per_sm;  /* 1..(the kernel's occupancy limit) (mode 0) */
     float ms;
+    int mode;           /* RT_BATCH_PERSISTENT or RT_BATCH_CHUNKS */
 } rt_batch_config;
+enum { RT_BATCH_PERSISTENT = 0, RT_BATCH_CHUNKS = 1 };
 
-/* Render njobs images in one persistent launch. Rays of all images share one work queue. Path
- * blocks come from a bounded pool that the transfer frees as it walks, so memory does not grow
- * with the batch. The launch (with its set-up) is captured once into a CUDA graph and replayed
- * while the form, the image count and the total ray count stay the same. The first call for a
- * form runs the autotuner (rt_batch_autotune) on this batch unless a shape was set by hand, and
- * so does a call whose batch has over 4x more or 4x fewer rays than the tuned one. Results
- * equal rt_render's for each image. Synchronizes; RT_ERR_WORKSPACE if a ray had to be given
- * up for lack of pool blocks (its pixel is zero, status RT_RAY_OVERFLOW); RT_ERR_STALL if a
- * bounded wait ran out. At most 2^31 - 1 rays in total. */
+/* Render njobs images: mode 0 in one persistent launch, where rays of all images share one work
+ * queue and path blocks come from a bounded pool that the transfer frees as it walks, so memory
+ * does not grow with the batch; the launch (with its set-up) is captured once into a CUDA graph
+ * and replayed while the form, the image count and the total ray count stay the same. Mode 1
+ * as described above. The first call for a form runs the autotuner (rt_batch_autotune, which
+ * times both modes) on this batch unless a shape was set by hand, and so does a call whose
+ * batch has over 4x more or 4x fewer rays than the tuned one. Results equal rt_render's for
+ * each image. Synchronizes; RT_ERR_WORKSPACE if a ray had to be given up for lack of path
+ * blocks (its pixel is zero, status RT_RAY_OVERFLOW); RT_ERR_STALL if a bounded wait ran out.
+ * At most 2^31 - 1 rays in total. */
 int rt_render_batch(rt_ctx *ctx, int form, const rt_job *jobs, int njobs);
 
 /* Time the candidate launch shapes on a calibration batch (the leading images of `jobs`,

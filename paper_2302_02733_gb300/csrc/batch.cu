@@ -166,8 +166,20 @@ int finish(rt_ctx *c, long long nrays) {
 }
 
 bool valid_cfg(const rt_ctx *c, int form, const rt_batch_config &b) {
-    return b.geo_warps >= 1 && b.geo_warps <= kPipeThreads / 32 - 1 && b.step_tile >= 1 && b.step_tile <= 16 &&
-           b.blocks_per_sm >= 1 && b.blocks_per_sm <= c->pipe_bps[fidx(form)];
+    if (b.mode == RT_BATCH_CHUNKS) return true;
+    return b.mode == RT_BATCH_PERSISTENT && b.geo_warps >= 1 && b.geo_warps <= kPipeThreads / 32 - 1 &&
+           b.step_tile >= 1 && b.step_tile <= 16 && b.blocks_per_sm >= 1 && b.blocks_per_sm <= c->pipe_bps[fidx(form)];
+}
+
+// Mode 1: the job table's images as one ray space through the overlapped two-kernel shape.
+int render_chunks(rt_ctx *c, int form, int njobs, long long nrays) {
+    BK(cudaMemcpyAsync(c->d_jobs, c->h_jobs, sizeof(JobDev) * njobs, cudaMemcpyHostToDevice, c->stream));
+    int rv = render_jobs_overlap(c, form, c->d_jobs, c->h_jobs, njobs, nrays);
+    c->last_was_batch = true;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]) == cudaSuccess) c->last_ms_total = ms;
+    cudaGetLastError();
+    return rv;
 }
 
 int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config *best) {
@@ -226,7 +238,16 @@ int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config
             if (rv) return rv;
         }
     }
-    if (top.geo_warps == 0) return RT_ERR_STALL;
+    // the overlapped two-kernel shape on the same images
+    {
+        int r = render_chunks(c, form, k, rays);
+        if (r == RT_OK) r = render_chunks(c, form, k, rays);  // the first call allocates
+        if (r == RT_OK && (top.geo_warps == 0 || c->last_ms_total < top.ms))
+            top = rt_batch_config{top.geo_warps, top.step_tile, top.blocks_per_sm, c->last_ms_total, RT_BATCH_CHUNKS};
+        else if (r != RT_OK && r != RT_ERR_NOMEM)
+            return r;
+    }
+    if (top.geo_warps == 0 && top.mode != RT_BATCH_CHUNKS) return RT_ERR_STALL;
     c->bcfg[fidx(form)] = top;
     c->bcal_rays[fidx(form)] = nrays;
     if (best) *best = top;
@@ -292,7 +313,8 @@ int rt_render_batch(rt_ctx *c, int form, const rt_job *jobs, int njobs) {
     // tune on first use, and again when the batch is far larger or smaller than the one the
     // shape was tuned on (a shape set by hand is kept)
     long long cal = c->bcal_rays[fidx(form)];
-    if (c->bcfg[fidx(form)].geo_warps == 0 || (cal > 0 && (nrays > 4 * cal || 4 * nrays < cal))) {
+    const bool tuned = c->bcfg[fidx(form)].geo_warps != 0 || c->bcfg[fidx(form)].mode == RT_BATCH_CHUNKS;
+    if (!tuned || (cal > 0 && (nrays > 4 * cal || 4 * nrays < cal))) {
         rv = autotune(c, form, jobs, njobs, nullptr);
         if (rv) return rv;
     }
@@ -300,6 +322,7 @@ int rt_render_batch(rt_ctx *c, int form, const rt_job *jobs, int njobs) {
     rv = ensure_buffers(c, njobs, nrays);
     if (rv) return rv;
     fill_jobs(c, jobs, njobs);
+    if (cfg.mode == RT_BATCH_CHUNKS) return render_chunks(c, form, njobs, nrays);
     long long key[8] = {form + 1,         njobs,          nrays, cfg.geo_warps, cfg.step_tile, cfg.blocks_per_sm,
                         c->pool.nblocks, c->jobs_cap};
     if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {

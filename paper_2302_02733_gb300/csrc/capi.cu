@@ -374,7 +374,7 @@ static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks, si
 
 static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, const Model &mod, const int *list,
                           uint16_t *steps_out, long long nrays, long long K, void *d_out, uint8_t *d_status,
-                          void *d_depth, int geo_grid, int xf_grid) {
+                          void *d_depth, int geo_grid, int xf_grid, const JobDev *jobs = nullptr, int njobs = 0) {
     const bool sur = form == RT_SURROGATE;
     // per arena block: the states and the prev link, and for the surrogate form the network's
     // inputs and outputs of each state (16 + 32 bytes)
@@ -422,9 +422,13 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
         GeoArgs ga{cam, c->d_sctab, ar[h], rec[h], ctr[h], n, o};
         ga.pix_list = list;
         ga.steps_out = steps_out;
+        ga.jobs = jobs;
+        ga.njobs = njobs;
         XferArgs xa{cam, mod, ar[h], rec[h], ctr[h], n, o, d_out, d_status, d_depth};
         xa.pix_list = list;
         xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+        xa.jobs = jobs;
+        xa.njobs = njobs;
         if (sur) set_surrogate_args(c, xa, feat[h], sur_y[h]);
         CK(cudaEventRecord(gs[i], sg));
         launch_geodesic(ga, geo_grid, sg);
@@ -463,6 +467,32 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     c->last_blocks_total = ar[0].nblocks;
     return RT_OK;
 }
+
+}  // extern "C"
+
+// The batched form in the overlapped two-kernel shape: the rays of njobs images (the job table
+// d_jobs on the device, h_jobs its host copy, ray_begin filled) form one ray space, chunked and
+// overlapped like one large image, on the context's stream. Thermal electrons, RT_FP64 or
+// RT_MIXED. Synchronizes; the counters describe the whole batch.
+int render_jobs_overlap(rt_ctx *c, int form, const JobDev *d_jobs, const JobDev *h_jobs, int njobs, long long nrays) {
+    const size_t per_ray = kPerRayBytes;
+    const int chunks = (int)std::min<long long>(rt_ctx::kMaxChunks, std::max<long long>(2, nrays >> 17));
+    long long ws_rays = 2 * ((nrays + chunks - 1) / chunks) +
+                        2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
+    int rv = ensure_workspace(c, ws_rays, per_ray);
+    if (rv) return rv;
+    long long K = overlap_chunks(c, nrays, chunks, per_ray);
+    if (K < 0) return RT_ERR_NOMEM;
+    const int geo_grid = c->nsm, xf_grid = c->nsm * (form == RT_FP64 ? c->fp64_bps : c->mixed_bps);
+    rv = render_overlap(c, form, 0, h_jobs[0].cam, h_jobs[0].model, nullptr, nullptr, nrays, K, nullptr, nullptr,
+                        nullptr, geo_grid, xf_grid, d_jobs, njobs);
+    if (rv) return rv;
+    c->last_rays = nrays;
+    c->last_was_overlap = true;
+    return c->h_ctr->n_status[kOverflow] > 0 ? RT_ERR_WORKSPACE : RT_OK;
+}
+
+extern "C" {
 
 static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, void *depth, const int *list = nullptr,
                        long long nlist = 0) {

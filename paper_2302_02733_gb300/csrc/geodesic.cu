@@ -11,6 +11,9 @@ namespace prt {
 
 static_assert(kSinTabBytes == 3 * kSinTab * sizeof(double), "sin/cos table size");
 
+// JOBS: the rays run over a table of images (p.jobs), each with its own camera; otherwise over
+// the one image of p.cam.
+template <bool JOBS>
 __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
     // the sin/cos table in shared memory: the RK4 stages read it at data-dependent indices, and
     // through the texture path those reads queued behind the transfer's gathers
@@ -18,6 +21,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
     for (int i = threadIdx.x; i < 3 * kSinTab; i += blockDim.x) tab[i] = p.sctab[i];
     __syncthreads();
     const Camera &c = p.cam;
+    StepCam sc{};  // JOBS: the current ray's camera constants
     double y[7];
     long long ray = -1;
     int n = 0, blk = -1, slot = kBlockStates, pix = 0;
@@ -30,9 +34,17 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             if (t < (unsigned long long)p.nrays) {
                 ray = (long long)t;
                 int ix, iy;
-                map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
-                pix = iy * c.nx + ix;
-                ray_start(c, ix, iy, y);
+                if (JOBS) {
+                    const long long gid = ray + p.ray_offset;
+                    const JobDev &J = p.jobs[find_job(p.jobs, p.njobs, gid)];
+                    ray_pixel(gid - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
+                    ray_start(J.cam, ix, iy, y);
+                    sc = step_cam(J.cam);
+                } else {
+                    map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
+                    pix = iy * c.nx + ix;
+                    ray_start(c, ix, iy, y);
+                }
                 n = 0;
                 blk = -1;
                 slot = kBlockStates;
@@ -45,7 +57,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
         if (!live) continue;
 
         double h, yn[7];
-        bool refl = geo_step(tab, c, y, yn, h);
+        bool refl = JOBS ? geo_step(tab, sc, y, yn, h) : geo_step(tab, c, y, yn, h);
         // save state n with the step taken from it; then n+1 becomes current
         uint8_t status = 0;
         for (int pass = 0; pass < 2; pass++) {
@@ -72,7 +84,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
                 n++;
 #pragma unroll
                 for (int k = 0; k < 7; k++) y[k] = yn[k];
-                status = geo_stop(c, y, n);
+                status = JOBS ? geo_stop(sc, y, n) : geo_stop(c, y, n);
             }
         }
         if (status) {
@@ -82,7 +94,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             rec.nstates = ok ? n + 1 : 0;
             rec.status = status;
             p.rec[ray] = rec;
-            if (p.steps_out) p.steps_out[pix] = (uint16_t)min(n, 65535);
+            if (!JOBS && p.steps_out) p.steps_out[pix] = (uint16_t)min(n, 65535);
             my_steps += (unsigned long long)n;
             atomicAdd(&p.ctr->n_status[status], 1u);
             live = false;
@@ -108,12 +120,15 @@ void launch_sincos_table(double *tab, cudaStream_t s) {
 }
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s) {
-    geodesic_kernel<<<grid, kGeoThreads, 0, s>>>(a);
+    if (a.jobs)
+        geodesic_kernel<true><<<grid, kGeoThreads, 0, s>>>(a);
+    else
+        geodesic_kernel<false><<<grid, kGeoThreads, 0, s>>>(a);
 }
 
 int geodesic_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, geodesic_kernel, kGeoThreads, 0) != cudaSuccess) n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, geodesic_kernel<false>, kGeoThreads, 0) != cudaSuccess) n = 1;
     return n > 0 ? n : 1;
 }
 

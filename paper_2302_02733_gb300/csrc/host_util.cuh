@@ -137,3 +137,7 @@ namespace prt {
 // Release the batched form's buffers, graph and stream (rt_destroy).
 void free_batch(rt_ctx *c);
 }  // namespace prt
+
+// capi.cu: the batched form through the overlapped two-kernel shape
+int render_jobs_overlap(rt_ctx *c, int form, const prt::JobDev *d_jobs, const prt::JobDev *h_jobs, int njobs,
+                        long long nrays);

@@ -34,19 +34,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Image of a global ray id: the last job whose first ray is <= ray.
-__device__ __forceinline__ int find_job(const JobDev *jobs, int njobs, long long ray) {
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&jobs[mid].ray_begin) <= ray)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 // Return a block to the ring at the next tail position. The slot is written only once the
 // ticket of the previous lap has taken its value (that ticket exists: the ring never holds
 // more than nblocks free blocks), and only after this lane's accesses to the block.

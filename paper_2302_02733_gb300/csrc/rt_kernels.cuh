@@ -7,6 +7,8 @@ namespace prt {
 constexpr int kGeoThreads = 128;
 constexpr int kXferThreads = 128;
 
+struct JobDev;
+
 struct GeoArgs {
     Camera cam;
     const double *sctab;  // (theta, sin, cos) table of the FP64 geodesic, 1024 entries
@@ -17,6 +19,8 @@ struct GeoArgs {
     long long ray_offset; // global id of the chunk's first ray
     const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering, ray order)
     uint16_t *steps_out;  // optional: per pixel (row-major), the ray's RK4 step count (capped at 65535)
+    const JobDev *jobs;   // optional: a table of images; global ray ids then run over all of them
+    int njobs;
 };
 
 struct XferArgs {
@@ -40,6 +44,8 @@ struct XferArgs {
     float4 *feat_raw;     // or (rt_render_features) raw inputs of the emitting points, compacted
     long long feat_cap;
     const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering)
+    const JobDev *jobs;   // optional: a table of images (see GeoArgs)
+    int njobs;
 };
 
 // ---- batched rendering: many images in one persistent launch ----------------------------
@@ -52,6 +58,19 @@ struct JobDev {
     uint8_t *status;      // optional [ny][nx]
     void *depth;          // optional [ny][nx][2]
 };
+
+// Image of a global ray id: the last job whose first ray is <= ray.
+__device__ __forceinline__ int find_job(const JobDev *jobs, int njobs, long long ray) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&jobs[mid].ray_begin) <= ray)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 // A bounded pool of path blocks with a free ring, so the memory of a batch does not grow
 // with its ray count: blocks return to the ring as the transfer walks past them.

@@ -4,7 +4,12 @@
 namespace prt {
 void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s) {
     switch (coef) {
-        case 0: transfer_kernel<double, double, 0><<<grid, kXferThreads, 0, s>>>(a); break;
+        case 0:
+            if (a.jobs)
+                transfer_kernel<double, double, 0, true><<<grid, kXferThreads, 0, s>>>(a);
+            else
+                transfer_kernel<double, double, 0><<<grid, kXferThreads, 0, s>>>(a);
+            break;
         case 1: transfer_kernel<double, double, 1><<<grid, kXferThreads, 0, s>>>(a); break;
         default: break;
     }

@@ -393,23 +393,34 @@ __device__ __forceinline__ void fill_bessel_weights(R *sgw) {
     }
 }
 
-template <typename R, typename OutT, int CM = 0>
+// JOBS: the rays run over a table of images (p.jobs), each with its own camera, model and
+// outputs; otherwise over the one image of p.cam, p.model, p.out.
+template <typename R, typename OutT, int CM = 0, bool JOBS = false>
 __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer_kernel(XferArgs p) {
     __shared__ R sgw[32];
     fill_bessel_weights(sgw);
     __syncthreads();
-    const Camera &c = p.cam;
     long long ray = -1;
-    int blk = -1, slot = 0, n = 0, rstat = 0;
+    int blk = -1, slot = 0, n = 0, rstat = 0, job = 0;
     bool live = false, drained = false;
     XLane<R> Ln;
     unsigned long long my_pts = 0, my_emit = 0;
+    // this ray's image: pixel, and (JOBS) the job's camera, model and outputs
+    auto pixel = [&](int &ix, int &iy) {
+        if (JOBS) {
+            const JobDev &J = p.jobs[job];
+            ray_pixel(ray + p.ray_offset - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
+        } else {
+            map_pixel(p.pix_list, ray + p.ray_offset, p.cam.nx, p.cam.ny, ix, iy);
+        }
+    };
     for (;;) {
         bool want = !live && !drained;
         unsigned long long t = warp_pop(&p.ctr->xfer_next, want);
         if (want) {
             if (t < (unsigned long long)p.nrays) {
                 ray = (long long)t;
+                if (JOBS) job = find_job(p.jobs, p.njobs, ray + p.ray_offset);
                 RayRecord rec = p.rec[ray];
                 rstat = rec.status;
                 if (rec.nstates >= 2) {
@@ -420,10 +431,13 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
                     live = true;
                 } else {
                     int ix, iy;
-                    map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
+                    pixel(ix, iy);
+                    const Camera &c = JOBS ? p.jobs[job].cam : p.cam;
+                    void *out = JOBS ? p.jobs[job].out : p.out, *depth = JOBS ? p.jobs[job].depth : p.depth;
+                    uint8_t *status = JOBS ? p.jobs[job].status : p.status;
                     long long pix = (long long)iy * c.nx + ix;
-                    xfer_zero<OutT>(pix, p.out, p.depth);
-                    if (p.status) p.status[pix] = (uint8_t)rstat;
+                    xfer_zero<OutT>(pix, out, depth);
+                    if (status) status[pix] = (uint8_t)rstat;
                 }
             } else {
                 drained = true;
@@ -441,13 +455,17 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
         const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
         double4_32a q0 = src[0], q1 = src[1];
         KS<R> m;
-        if (xfer_point<R, CM>(c, p.model, q0, q1, sgw, Ln, m, &p, (long long)blk * kBlockStates + slot)) my_emit++;
+        const Camera &c = JOBS ? p.jobs[job].cam : p.cam;
+        const Model &mdl = JOBS ? p.jobs[job].model : p.model;
+        if (xfer_point<R, CM>(c, mdl, q0, q1, sgw, Ln, m, &p, (long long)blk * kBlockStates + slot)) my_emit++;
         my_pts++;
         if (n == 0) {
             int ix, iy;
-            map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
-            xfer_finish<R, OutT>(c, m, ix, iy, Ln, p.out, p.depth);
-            if (p.status) p.status[(long long)iy * c.nx + ix] = (uint8_t)rstat;
+            pixel(ix, iy);
+            void *out = JOBS ? p.jobs[job].out : p.out, *depth = JOBS ? p.jobs[job].depth : p.depth;
+            uint8_t *status = JOBS ? p.jobs[job].status : p.status;
+            xfer_finish<R, OutT>(c, m, ix, iy, Ln, out, depth);
+            if (status) status[(long long)iy * c.nx + ix] = (uint8_t)rstat;
             live = false;
         }
     }

@@ -5,7 +5,12 @@
 namespace prt {
 void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s) {
     switch (coef) {
-        case 0: transfer_kernel<float, float, 0><<<grid, kXferThreads, 0, s>>>(a); break;
+        case 0:
+            if (a.jobs)
+                transfer_kernel<float, float, 0, true><<<grid, kXferThreads, 0, s>>>(a);
+            else
+                transfer_kernel<float, float, 0><<<grid, kXferThreads, 0, s>>>(a);
+            break;
         case 1: transfer_kernel<float, float, 1><<<grid, kXferThreads, 0, s>>>(a); break;
         case 2: transfer_kernel<float, float, 2><<<grid, kXferThreads, 0, s>>>(a); break;
         default: break;

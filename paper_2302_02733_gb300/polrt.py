@@ -68,7 +68,11 @@ class rt_job(C.Structure):
 
 
 class rt_batch_config(C.Structure):
-    _fields_ = [("geo_warps", C.c_int), ("step_tile", C.c_int), ("blocks_per_sm", C.c_int), ("ms", C.c_float)]
+    _fields_ = [("geo_warps", C.c_int), ("step_tile", C.c_int), ("blocks_per_sm", C.c_int), ("ms", C.c_float),
+                ("mode", C.c_int)]
+
+
+RT_BATCH_PERSISTENT, RT_BATCH_CHUNKS = 0, 1
 
 
 _lib = None
@@ -349,8 +353,8 @@ def rt_batch_autotune(ctx, form: int, jobs) -> dict:
     return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
 
 
-def rt_set_batch_config(ctx, form: int, geo_warps: int, step_tile: int, blocks_per_sm: int):
-    b = rt_batch_config(geo_warps, step_tile, blocks_per_sm, 0.0)
+def rt_set_batch_config(ctx, form: int, geo_warps: int, step_tile: int, blocks_per_sm: int, mode: int = 0):
+    b = rt_batch_config(geo_warps, step_tile, blocks_per_sm, 0.0, mode)
     _check(lib().rt_set_batch_config(ctx, form, C.byref(b)), "rt_set_batch_config")
 
 

@@ -149,3 +149,46 @@ def test_image_library_96(rt, ora, synth, torus_grid):
     print(f"library96 vs oracle: p50 {np.median(e):.2e} p99 {np.percentile(e, 99):.2e} max {e.max():.2e}; "
           f"full-image flux errors {max(ferrs):.2e}")
     assert np.percentile(e, 99) <= 5e-4 and max(ferrs) <= 1e-4
+
+
+def test_chunk_mode_equals_single_renders(rt, synth, torus_grid):
+    """Mode 1 (RT_BATCH_CHUNKS): the images' rays as one ray space through the overlapped
+    two-kernel shape. Each image equals its rt_render image, with status codes and depth maps:
+    bit for bit in the mixed form, within 1e-12 in the FP64 form (as the persistent mode; the
+    job-table kernels are separate instantiations, whose FP64 contractions may round apart)."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    prims_dev = torch.from_numpy(prims).cuda()
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    spec = small_jobs(synth)
+    try:
+        for form, dt in ((polrt.RT_FP64, torch.float64), (polrt.RT_MIXED, torch.float32)):
+            polrt.rt_set_batch_config(ctx, form, 0, 0, 0, polrt.RT_BATCH_CHUNKS)
+            polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g))
+            outs = [torch.full((c.ny, c.nx, 4), float("nan"), dtype=dt, device="cuda") for c, _, _ in spec]
+            sts = [torch.zeros((c.ny, c.nx), dtype=torch.uint8, device="cuda") for c, _, _ in spec]
+            deps = [torch.zeros((c.ny, c.nx, 2), dtype=dt, device="cuda") for c, _, _ in spec]
+            jobs = polrt.make_jobs((c, mu, rh, o, s, d) for (c, mu, rh), o, s, d in zip(spec, outs, sts, deps))
+            polrt.rt_render_batch(ctx, form, jobs)
+            cnt = polrt.rt_last_counters(ctx)
+            assert cnt["rays"] == sum(c.nx * c.ny for c, _, _ in spec) and cnt["n_overflow"] == 0
+            assert cnt["ms_total"] > 0 and polrt.rt_get_batch_config(ctx, form)["mode"] == polrt.RT_BATCH_CHUNKS
+            for (c, mu, rh), o, s, d in zip(spec, outs, sts, deps):
+                g1 = dataclasses.replace(g, M_unit=mu, R_high=rh)
+                polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g1))
+                polrt.rt_set_camera(ctx, c)
+                ref = torch.zeros_like(o)
+                rst = torch.zeros_like(s)
+                rdep = torch.zeros_like(d)
+                polrt.rt_render_depths(ctx, form, ref, rdep, rst)
+                assert torch.equal(s, rst), (form, c.nx, c.incl_deg)
+                if form == polrt.RT_MIXED:
+                    assert torch.equal(o, ref) and torch.equal(d, rdep), (c.nx, c.incl_deg)
+                else:
+                    a, b = o.cpu().numpy(), ref.cpu().numpy()
+                    assert rel_err(a, b).max() <= 1e-12, (c.nx, c.incl_deg, rel_err(a, b).max())
+                    dd, dr = d.cpu().numpy(), rdep.cpu().numpy()
+                    assert np.abs(dd - dr).max() <= 1e-12 * max(np.abs(dr).max(), 1e-300)
+    finally:
+        for form in (polrt.RT_FP64, polrt.RT_MIXED):
+            polrt.rt_set_batch_config(ctx, form, 4, 1, 1)
