@@ -110,6 +110,8 @@ int rt_destroy(rt_ctx *c) {
     cudaFree(c->d_steps);
     cudaFree(c->d_order);
     cudaFree(c->d_ohist);
+    cudaFree(c->d_bsteps);
+    cudaFree(c->d_border);
     if (c->ws_owned) cudaFree(c->ws);
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
@@ -484,12 +486,57 @@ int render_jobs_overlap(rt_ctx *c, int form, const JobDev *d_jobs, const JobDev 
     long long K = overlap_chunks(c, nrays, chunks, per_ray);
     if (K < 0) return RT_ERR_NOMEM;
     const int geo_grid = c->nsm, xf_grid = c->nsm * (form == RT_FP64 ? c->fp64_bps : c->mixed_bps);
-    rv = render_overlap(c, form, 0, h_jobs[0].cam, h_jobs[0].model, nullptr, nullptr, nrays, K, nullptr, nullptr,
+    // longest first, as for one image, once a batch of the same cameras has recorded its steps
+    unsigned long long key = 1469598103934665603ull;  // FNV-1a over the cameras and integrator
+    auto mix = [&](const void *v, size_t n) {
+        for (size_t i = 0; i < n; i++) key = (key ^ ((const unsigned char *)v)[i]) * 1099511628211ull;
+    };
+    for (int j = 0; j < njobs; j++) {
+        const Camera &cj = h_jobs[j].cam;
+        const double f[6] = {cj.a, cj.r_cam, cj.theta_o, cj.fov, cj.eps, (double)cj.nmax};
+        const int d[2] = {cj.nx, cj.ny};
+        mix(f, sizeof(f));
+        mix(d, sizeof(d));
+    }
+    if (key != c->bkey || nrays > c->border_cap) {
+        c->bkey = key;
+        c->have_bsteps = false;
+        c->border_K = 0;
+    }
+    if (nrays > c->border_cap) {
+        cudaFree(c->d_bsteps);
+        cudaFree(c->d_border);
+        c->d_bsteps = nullptr;
+        c->d_border = nullptr;
+        c->border_cap = 0;
+        if (cudaMalloc(&c->d_bsteps, sizeof(uint16_t) * nrays) != cudaSuccess ||
+            cudaMalloc(&c->d_border, sizeof(int) * nrays) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ERR_NOMEM;
+        }
+        c->border_cap = nrays;
+    }
+    if (!c->d_ohist && cudaMalloc(&c->d_ohist, sizeof(unsigned) * kOrderBuckets) != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_NOMEM;
+    }
+    const int *list = nullptr;
+    if (c->have_bsteps) {
+        if (c->border_K != K) {
+            launch_order_build(c->d_bsteps, nrays, (int)K, c->d_ohist, c->d_border, c->stream);
+            CK(cudaGetLastError());
+            c->border_K = K;
+        }
+        list = c->d_border;
+    }
+    rv = render_overlap(c, form, 0, h_jobs[0].cam, h_jobs[0].model, list, c->d_bsteps, nrays, K, nullptr, nullptr,
                         nullptr, geo_grid, xf_grid, d_jobs, njobs);
     if (rv) return rv;
     c->last_rays = nrays;
     c->last_was_overlap = true;
-    return c->h_ctr->n_status[kOverflow] > 0 ? RT_ERR_WORKSPACE : RT_OK;
+    if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
+    c->have_bsteps = true;
+    return RT_OK;
 }
 
 extern "C" {

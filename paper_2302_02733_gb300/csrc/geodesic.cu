@@ -34,12 +34,13 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             if (t < (unsigned long long)p.nrays) {
                 ray = (long long)t;
                 int ix, iy;
-                if (JOBS) {
-                    const long long gid = ray + p.ray_offset;
+                if (JOBS) {  // the ray's global id (through the order list, if any) and image
+                    const long long gid = p.pix_list ? p.pix_list[ray + p.ray_offset] : ray + p.ray_offset;
                     const JobDev &J = p.jobs[find_job(p.jobs, p.njobs, gid)];
                     ray_pixel(gid - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
                     ray_start(J.cam, ix, iy, y);
                     sc = step_cam(J.cam);
+                    pix = (int)gid;
                 } else {
                     map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
                     pix = iy * c.nx + ix;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             rec.nstates = ok ? n + 1 : 0;
             rec.status = status;
             p.rec[ray] = rec;
-            if (!JOBS && p.steps_out) p.steps_out[pix] = (uint16_t)min(n, 65535);
+            if (p.steps_out) p.steps_out[pix] = (uint16_t)min(n, 65535);  // by pixel, or (JOBS) by global id
             my_steps += (unsigned long long)n;
             atomicAdd(&p.ctr->n_status[status], 1u);
             live = false;

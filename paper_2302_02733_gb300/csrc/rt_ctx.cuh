@@ -64,6 +64,12 @@ struct rt_ctx {
     double order_key[8] = {};     // camera and integrator the steps belong to
     bool have_steps = false;
     long long order_K = 0;        // chunks d_order is dealt to; 0: not built
+    // the same for the batched form's mode 1, by global ray id over the job table
+    uint16_t *d_bsteps = nullptr;
+    int *d_border = nullptr;
+    long long border_cap = 0, border_K = 0;
+    unsigned long long bkey = 0;  // hash of the cameras and integrator the steps belong to
+    bool have_bsteps = false;
     float last_ms_geo = 0.f, last_ms_xfer = 0.f;
     bool last_was_overlap = false;
     int last_chunks = 0;

@@ -19,8 +19,8 @@ struct GeoArgs {
     long long ray_offset; // global id of the chunk's first ray
     const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering, ray order)
     uint16_t *steps_out;  // optional: per pixel (row-major), the ray's RK4 step count (capped at 65535)
-    const JobDev *jobs;   // optional: a table of images; global ray ids then run over all of them
-    int njobs;
+    const JobDev *jobs;   // optional: a table of images; global ray ids then run over all of them, the
+    int njobs;            // order list holds global ray ids and steps_out is indexed by them
 };
 
 struct XferArgs {

@@ -406,10 +406,11 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
     XLane<R> Ln;
     unsigned long long my_pts = 0, my_emit = 0;
     // this ray's image: pixel, and (JOBS) the job's camera, model and outputs
+    auto gid_of = [&](long long r) { return p.pix_list ? (long long)p.pix_list[r + p.ray_offset] : r + p.ray_offset; };
     auto pixel = [&](int &ix, int &iy) {
         if (JOBS) {
             const JobDev &J = p.jobs[job];
-            ray_pixel(ray + p.ray_offset - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
+            ray_pixel(gid_of(ray) - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
         } else {
             map_pixel(p.pix_list, ray + p.ray_offset, p.cam.nx, p.cam.ny, ix, iy);
         }
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
         if (want) {
             if (t < (unsigned long long)p.nrays) {
                 ray = (long long)t;
-                if (JOBS) job = find_job(p.jobs, p.njobs, ray + p.ray_offset);
+                if (JOBS) job = find_job(p.jobs, p.njobs, gid_of(ray));
                 RayRecord rec = p.rec[ray];
                 rstat = rec.status;
                 if (rec.nstates >= 2) {

@@ -170,6 +170,9 @@ def test_chunk_mode_equals_single_renders(rt, synth, torus_grid):
             deps = [torch.zeros((c.ny, c.nx, 2), dtype=dt, device="cuda") for c, _, _ in spec]
             jobs = polrt.make_jobs((c, mu, rh, o, s, d) for (c, mu, rh), o, s, d in zip(spec, outs, sts, deps))
             polrt.rt_render_batch(ctx, form, jobs)
+            first = [o.clone() for o in outs]
+            polrt.rt_render_batch(ctx, form, jobs)  # the same cameras: rays longest first this time
+            assert all(torch.equal(a, b) for a, b in zip(first, outs))
             cnt = polrt.rt_last_counters(ctx)
             assert cnt["rays"] == sum(c.nx * c.ny for c, _, _ in spec) and cnt["n_overflow"] == 0
             assert cnt["ms_total"] > 0 and polrt.rt_get_batch_config(ctx, form)["mode"] == polrt.RT_BATCH_CHUNKS
