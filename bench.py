@@ -221,6 +221,13 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
     polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
     mo = polrt.rt_last_counters(ctx)["ms_total"]
     res["other_mode"] = {"launch": launch[other], "value": npix / (mo / 1e3), "ms_per_batch": mo}
+    # the same library unpolarized (the fitting loop's form; always mode 1)
+    uouts = [torch.empty((j.n, j.n), dtype=torch.float32, device=dev) for j in table]
+    ujobs = polrt.make_jobs((c, j.M_unit, j.R_high, o, None, None) for c, j, o in zip(cams, table, uouts))
+    polrt.rt_render_batch(ctx, polrt.RT_UNPOL, ujobs)
+    polrt.rt_render_batch(ctx, polrt.RT_UNPOL, ujobs)
+    mu = polrt.rt_last_counters(ctx)["ms_total"]
+    res["unpolarized"] = {"launch": launch[polrt.RT_BATCH_CHUNKS], "value": npix / (mu / 1e3), "ms_per_batch": mu}
     return res
 
 

@@ -321,7 +321,8 @@ typedef struct {
     rt_camera cam;     /* resolution, inclination, frequency, ... of this image */
     double M_unit;     /* grid models: this image's mass unit [g]; <= 0 keeps the loaded value */
     double R_high;     /* grid models: this image's R_high; <= 0 keeps the loaded value */
-    void *out_iquv;    /* device buffer, nx*ny*4 values of the form's type, layout as rt_render */
+    void *out_iquv;    /* device buffer, nx*ny*4 values of the form's type, layout as rt_render
+                        * (RT_UNPOL: nx*ny floats of I) */
     uint8_t *status;   /* optional device nx*ny codes, or NULL */
     void *out_depth;   /* optional device nx*ny*2 depths (see rt_render_depths), or NULL */
 } rt_job;
@@ -345,7 +346,8 @@ typedef struct {
 } rt_batch_config;
 enum { RT_BATCH_PERSISTENT = 0, RT_BATCH_CHUNKS = 1 };
 
-/* Render njobs images: mode 0 in one persistent launch, where rays of all images share one work
+/* Render njobs images (form RT_FP64, RT_MIXED or RT_UNPOL; RT_UNPOL always in mode 1, with
+ * out_iquv holding nx*ny floats of I and out_depth NULL): mode 0 in one persistent launch, where rays of all images share one work
  * queue and path blocks come from a bounded pool that the transfer frees as it walks, so memory
  * does not grow with the batch; the launch (with its set-up) is captured once into a CUDA graph
  * and replayed while the form, the image count and the total ray count stay the same. Mode 1

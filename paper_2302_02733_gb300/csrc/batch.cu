@@ -26,7 +26,7 @@ constexpr long long kCalibRays = 1ll << 20; // rays in the autotuner's calibrati
 int fidx(int form) { return form == RT_FP64 ? 0 : 1; }
 
 int check_jobs(const rt_ctx *c, int form, const rt_job *jobs, int njobs, long long *nrays) {
-    if (!c || !jobs || njobs < 1 || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
+    if (!c || !jobs || njobs < 1 || (form != RT_FP64 && form != RT_MIXED && form != RT_UNPOL)) return RT_ERR_INVALID;
     if (!c->have_model) return RT_ERR_NOT_READY;
     if (c->model.edf != RT_EDF_THERMAL) return RT_ERR_INVALID;  // the batched form renders thermal electrons
     long long tot = 0;
@@ -35,7 +35,7 @@ int check_jobs(const rt_ctx *c, int form, const rt_job *jobs, int njobs, long lo
         if (rv) return rv;
         if (!jobs[i].out_iquv || !is_device_ptr(jobs[i].out_iquv)) return RT_ERR_INVALID;
         if (jobs[i].status && !is_device_ptr(jobs[i].status)) return RT_ERR_INVALID;
-        if (jobs[i].out_depth && !is_device_ptr(jobs[i].out_depth)) return RT_ERR_INVALID;
+        if (jobs[i].out_depth && (form == RT_UNPOL || !is_device_ptr(jobs[i].out_depth))) return RT_ERR_INVALID;
         tot += (long long)jobs[i].cam.nx * jobs[i].cam.ny;
     }
     if (tot > INT_MAX) return RT_ERR_SIZE;
@@ -61,7 +61,7 @@ int realloc_dev(T **p, size_t n) {
     return RT_OK;
 }
 
-int ensure_buffers(rt_ctx *c, int njobs, long long nrays) {
+int ensure_jobs(rt_ctx *c, int njobs) {
     if (njobs > c->jobs_cap) {
         drop_graph(c);
         if (c->h_jobs) cudaFreeHost(c->h_jobs);
@@ -75,6 +75,12 @@ int ensure_buffers(rt_ctx *c, int njobs, long long nrays) {
         }
         c->jobs_cap = njobs;
     }
+    return RT_OK;
+}
+
+int ensure_buffers(rt_ctx *c, int njobs, long long nrays) {
+    int rv = ensure_jobs(c, njobs);
+    if (rv) return rv;
     if (nrays > c->brays_cap) {
         drop_graph(c);
         c->brays_cap = 0;
@@ -288,6 +294,7 @@ void free_batch(rt_ctx *c) {
 extern "C" {
 
 int rt_batch_autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config *best) {
+    if (form == RT_UNPOL) return RT_ERR_INVALID;  // no launch shape to tune: always mode 1
     return autotune(c, form, jobs, njobs, best);
 }
 
@@ -310,6 +317,12 @@ int rt_render_batch(rt_ctx *c, int form, const rt_job *jobs, int njobs) {
     int rv = check_jobs(c, form, jobs, njobs, &nrays);
     if (rv) return rv;
     BK(cudaSetDevice(c->device));
+    if (form == RT_UNPOL) {  // the unpolarized form has no persistent kernel: always mode 1
+        rv = ensure_jobs(c, njobs);
+        if (rv) return rv;
+        fill_jobs(c, jobs, njobs);
+        return render_chunks(c, form, njobs, nrays);
+    }
     // tune on first use, and again when the batch is far larger or smaller than the one the
     // shape was tuned on (a shape set by hand is kept)
     long long cal = c->bcal_rays[fidx(form)];

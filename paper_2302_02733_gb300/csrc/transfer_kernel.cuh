@@ -543,22 +543,47 @@ __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
 // (the ray's fluid-frame direction is -K - w u, b is spatial in that frame), j_I and a_I, and the
 // exact step I <- I e^-tau + (j ds / w^3) (1 - e^-tau)/tau, added as the increment
 // (J - tau I) (1 - e^-tau)/tau with TwoSum compensation. Output: one value per pixel.
-template <typename R>
+template <typename R, bool JOBS = false>
 __global__ void __launch_bounds__(kXferThreads, 4) unpol_kernel(XferArgs p) {
     typedef Mth<R> F;
-    const Camera &c = p.cam;
-    const R a = pick<R>(c.a, c.f_a), nu_obs = pick<R>(c.nu_obs, c.f_nu_obs), L = pick<R>(c.L_unit, c.f_L_unit);
+    // the ray's camera constants: p.cam's, or (JOBS) its image's
+    R a = pick<R>(p.cam.a, p.cam.f_a), nu_obs = pick<R>(p.cam.nu_obs, p.cam.f_nu_obs),
+      L = pick<R>(p.cam.L_unit, p.cam.f_L_unit);
     long long ray = -1;
-    int blk = -1, slot = 0, n = 0, rstat = 0;
+    int blk = -1, slot = 0, n = 0, rstat = 0, job = 0;
     bool live = false, drained = false;
     R I = 0, Ilo = 0;
     unsigned long long my_pts = 0, my_emit = 0;
+    auto gid_of = [&](long long r) { return p.pix_list ? (long long)p.pix_list[r + p.ray_offset] : r + p.ray_offset; };
+    // this ray's pixel index and its image's outputs
+    auto target = [&](long long &pix, R *&out, uint8_t *&status) {
+        int ix, iy;
+        if (JOBS) {
+            const JobDev &J = p.jobs[job];
+            ray_pixel(gid_of(ray) - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
+            pix = (long long)iy * J.cam.nx + ix;
+            out = reinterpret_cast<R *>(J.out);
+            status = J.status;
+        } else {
+            map_pixel(p.pix_list, ray + p.ray_offset, p.cam.nx, p.cam.ny, ix, iy);
+            pix = (long long)iy * p.cam.nx + ix;
+            out = reinterpret_cast<R *>(p.out);
+            status = p.status;
+        }
+    };
     for (;;) {
         bool want = !live && !drained;
         unsigned long long t = warp_pop(&p.ctr->xfer_next, want);
         if (want) {
             if (t < (unsigned long long)p.nrays) {
                 ray = (long long)t;
+                if (JOBS) {
+                    job = find_job(p.jobs, p.njobs, gid_of(ray));
+                    const Camera &cj = p.jobs[job].cam;
+                    a = pick<R>(cj.a, cj.f_a);
+                    nu_obs = pick<R>(cj.nu_obs, cj.f_nu_obs);
+                    L = pick<R>(cj.L_unit, cj.f_L_unit);
+                }
                 RayRecord rec = p.rec[ray];
                 rstat = rec.status;
                 if (rec.nstates >= 2) {
@@ -568,11 +593,12 @@ __global__ void __launch_bounds__(kXferThreads, 4) unpol_kernel(XferArgs p) {
                     I = Ilo = R(0);
                     live = true;
                 } else {
-                    int ix, iy;
-                    map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
-                    long long pix = (long long)iy * c.nx + ix;
-                    reinterpret_cast<R *>(p.out)[pix] = R(0);
-                    if (p.status) p.status[pix] = (uint8_t)rstat;
+                    long long pix;
+                    R *out;
+                    uint8_t *status;
+                    target(pix, out, status);
+                    out[pix] = R(0);
+                    if (status) status[pix] = (uint8_t)rstat;
                 }
             } else {
                 drained = true;
@@ -593,10 +619,11 @@ __global__ void __launch_bounds__(kXferThreads, 4) unpol_kernel(XferArgs p) {
         KS<R> m;
         m.eval(a, r, th);
         Plasma<R> pl;
-        if (p.model.kind == 1)
-            adaf_plasma(p.model.adaf, a, m, r, pl);
+        const Model &mdl = JOBS ? p.jobs[job].model : p.model;
+        if (mdl.kind == 1)
+            adaf_plasma(mdl.adaf, a, m, r, pl);
         else
-            grid_plasma(p.model.grid, m, q0.x, q0.y, q0.z, pl);
+            grid_plasma(mdl.grid, m, q0.x, q0.y, q0.z, pl);
         if (pl.valid) {
             R w = m.dot(K, pl.u);
             R kp[4], bn[4];
@@ -618,11 +645,12 @@ __global__ void __launch_bounds__(kXferThreads, 4) unpol_kernel(XferArgs p) {
         }
         my_pts++;
         if (n == 0) {
-            int ix, iy;
-            map_pixel(p.pix_list, ray + p.ray_offset, c.nx, c.ny, ix, iy);
-            long long pix = (long long)iy * c.nx + ix;
-            reinterpret_cast<R *>(p.out)[pix] = I + Ilo;
-            if (p.status) p.status[pix] = (uint8_t)rstat;
+            long long pix;
+            R *out;
+            uint8_t *status;
+            target(pix, out, status);
+            out[pix] = I + Ilo;
+            if (status) status[pix] = (uint8_t)rstat;
             live = false;
         }
     }

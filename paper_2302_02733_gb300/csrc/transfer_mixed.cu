@@ -17,7 +17,10 @@ void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s
     }
 }
 void launch_unpol(const XferArgs &a, int grid, cudaStream_t s) {
-    unpol_kernel<float><<<grid, kXferThreads, 0, s>>>(a);
+    if (a.jobs)
+        unpol_kernel<float, true><<<grid, kXferThreads, 0, s>>>(a);
+    else
+        unpol_kernel<float><<<grid, kXferThreads, 0, s>>>(a);
 }
 void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s) {
     sur_features_pass<float><<<grid, kXferThreads, 0, s>>>(a);

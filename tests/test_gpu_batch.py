@@ -195,3 +195,38 @@ def test_chunk_mode_equals_single_renders(rt, synth, torus_grid):
     finally:
         for form in (polrt.RT_FP64, polrt.RT_MIXED):
             polrt.rt_set_batch_config(ctx, form, 4, 1, 1)
+
+
+def test_unpolarized_batch_equals_single_renders(rt, synth, torus_grid):
+    """The fitting loop's form: many unpolarized images in one batch (always mode 1). Each
+    image matches its rt_render(RT_UNPOL) image within 1e-5 per pixel, and the first call (pixel
+    order) equals the next (rays longest first) bit for bit. The job-table kernel reads the
+    camera constants per ray instead of from its parameters, and its FP32 contractions round
+    apart from the single-image kernel's by about 1e-6."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    prims_dev = torch.from_numpy(prims).cuda()
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g))
+    spec = small_jobs(synth)
+    outs = [torch.full((c.ny, c.nx), float("nan"), dtype=torch.float32, device="cuda") for c, _, _ in spec]
+    sts = [torch.zeros((c.ny, c.nx), dtype=torch.uint8, device="cuda") for c, _, _ in spec]
+    jobs = polrt.make_jobs((c, mu, rh, o, s, None) for (c, mu, rh), o, s in zip(spec, outs, sts))
+    polrt.rt_render_batch(ctx, polrt.RT_UNPOL, jobs)
+    first = [o.clone() for o in outs]
+    polrt.rt_render_batch(ctx, polrt.RT_UNPOL, jobs)
+    assert all(torch.equal(a, b) for a, b in zip(first, outs))
+    assert polrt.rt_last_counters(ctx)["rays"] == sum(c.nx * c.ny for c, _, _ in spec)
+    for (c, mu, rh), o, s in zip(spec, outs, sts):
+        polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, dataclasses.replace(g, M_unit=mu, R_high=rh)))
+        polrt.rt_set_camera(ctx, c)
+        ref = torch.zeros_like(o)
+        rst = torch.zeros_like(s)
+        polrt.rt_render(ctx, polrt.RT_UNPOL, ref, rst)
+        a, b = o.double().cpu().numpy(), ref.double().cpu().numpy()
+        err = np.abs(a - b) / np.maximum(b, 1e-8 * max(b.max(), 1e-300))
+        print(f"unpolarized batch vs single, {c.nx}^2 i={c.incl_deg}: max rel err {err.max():.2e}, "
+              f"bit-exact {bool(torch.equal(o, ref))}")
+        assert torch.isfinite(o).all() and torch.equal(s, rst) and err.max() <= 1e-5, (c.nx, c.incl_deg)
+    with pytest.raises(polrt.PolrtError):
+        polrt.rt_batch_autotune(ctx, polrt.RT_UNPOL, jobs)
