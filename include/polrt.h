@@ -299,7 +299,7 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
  * render of the same camera and integrator takes its rays longest first (dealt round-robin to
  * the chunks), so that no launch ends waiting for a few long photon-ring rays. The image is the
  * same either way (every ray takes the same arithmetic); only the time differs. Shapes that
- * exceed the kernels' occupancy or chunks above 64 return RT_ERR_INVALID. */
+ * exceed the kernels' occupancy or chunks above 256 return RT_ERR_INVALID. */
 typedef struct {
     int geo_blocks_per_sm;
     int xfer_blocks_per_sm;
@@ -333,7 +333,8 @@ typedef struct {
  * queue and pool checks; blocks_per_sm is the number of resident blocks per SM (the grid is
  * that times the SM count). mode 1 (RT_BATCH_CHUNKS) treats the rays of all images as one ray
  * space and runs it like one large image in the overlapped shape of rt_set_render_config
- * (chunks of about 2^17 rays, at most 64; the geodesic of one chunk beside the transfer of the
+ * (chunks of about 2^17 rays, 2 to 64 of them, up to 256 when the workspace is short; a batch
+ * that needs more runs in mode 0; the geodesic of one chunk beside the transfer of the
  * previous), on the context's stream and without a graph; geo_warps, step_tile and
  * blocks_per_sm are then ignored. ms is the time the autotuner measured for this shape (0
  * when set by hand). */

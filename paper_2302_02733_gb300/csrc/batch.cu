@@ -331,11 +331,18 @@ int rt_render_batch(rt_ctx *c, int form, const rt_job *jobs, int njobs) {
         rv = autotune(c, form, jobs, njobs, nullptr);
         if (rv) return rv;
     }
-    const rt_batch_config cfg = c->bcfg[fidx(form)];
+    rt_batch_config cfg = c->bcfg[fidx(form)];
     rv = ensure_buffers(c, njobs, nrays);
     if (rv) return rv;
     fill_jobs(c, jobs, njobs);
-    if (cfg.mode == RT_BATCH_CHUNKS) return render_chunks(c, form, njobs, nrays);
+    if (cfg.mode == RT_BATCH_CHUNKS) {
+        rv = render_chunks(c, form, njobs, nrays);
+        // a batch too large for mode 1's workspace (two chunks of at most 1/kMaxChunks of its
+        // rays) runs in the persistent kernel, whose pool bounds its memory
+        if (rv != RT_ERR_NOMEM) return rv;
+        cfg.mode = RT_BATCH_PERSISTENT;
+        if (!valid_cfg(c, form, cfg)) cfg = rt_batch_config{4, 1, c->pipe_bps[fidx(form)], 0.f, RT_BATCH_PERSISTENT};
+    }
     long long key[8] = {form + 1,         njobs,          nrays, cfg.geo_warps, cfg.step_tile, cfg.blocks_per_sm,
                         c->pool.nblocks, c->jobs_cap};
     if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {

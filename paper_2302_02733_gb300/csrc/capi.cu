@@ -478,7 +478,7 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
 // RT_MIXED. Synchronizes; the counters describe the whole batch.
 int render_jobs_overlap(rt_ctx *c, int form, const JobDev *d_jobs, const JobDev *h_jobs, int njobs, long long nrays) {
     const size_t per_ray = kPerRayBytes;
-    const int chunks = (int)std::min<long long>(rt_ctx::kMaxChunks, std::max<long long>(2, nrays >> 17));
+    const int chunks = (int)std::min<long long>(64, std::max<long long>(2, nrays >> 17));
     long long ws_rays = 2 * ((nrays + chunks - 1) / chunks) +
                         2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
     int rv = ensure_workspace(c, ws_rays, per_ray);
@@ -586,7 +586,7 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     int rv = ensure_workspace(c, ws_rays, per_ray);
     if (rv) return rv;
     long long K = 1;
-    // a workspace too small for kMaxChunks overlapped chunks (a caller's, or a nearly full
+    // a workspace too small for kMaxChunks (256) overlapped chunks (a caller's, or a nearly full
     // device) renders in one pass of each kernel per chunk instead
     if (ovl && (K = overlap_chunks(c, nrays, chunks, per_ray)) < 0) {
         ovl = false;

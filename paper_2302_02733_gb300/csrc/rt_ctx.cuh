@@ -48,7 +48,7 @@ struct rt_ctx {
 
     // overlapped rt_render: geodesic of chunk i + 1 on ostream[0] beside the transfer of chunk i
     // on ostream[1]; per chunk the events geodesic start/end, transfer start/end
-    static constexpr int kMaxChunks = 64;
+    static constexpr int kMaxChunks = 256;
     rt_render_config rcfg{};
     cudaStream_t ostream[2] = {nullptr, nullptr};
     cudaEvent_t oev[4 * kMaxChunks] = {};

@@ -70,7 +70,7 @@ def test_overlapped_render_is_identical(rt, synth, torus_grid):
 
 def test_render_config_checks(rt):
     polrt, ctx = rt
-    for bad in ((0, 0, 65), (0, 0, -1), (99, 0, 0), (0, 99, 0), (-1, 0, 0)):
+    for bad in ((0, 0, 257), (0, 0, -1), (99, 0, 0), (0, 99, 0), (-1, 0, 0)):
         with pytest.raises(polrt.PolrtError):
             polrt.rt_set_render_config(ctx, *bad)
     polrt.rt_set_render_config(ctx, 1, 2, 8)
@@ -109,7 +109,7 @@ def test_overlapped_surrogate_is_identical(rt, synth, torus_grid):
 
 
 def test_small_caller_workspace_falls_back_to_one_pass(rt, synth, torus_grid):
-    """An overlapped shape that a caller's workspace cannot hold in at most 64 chunks renders
+    """An overlapped shape that a caller's workspace cannot hold in at most 256 chunks renders
     in one pass of each kernel per chunk instead, with the same image."""
     polrt, ctx = rt
     prims, g = torus_grid
@@ -118,12 +118,12 @@ def test_small_caller_workspace_falls_back_to_one_pass(rt, synth, torus_grid):
     polrt.rt_set_camera(ctx, cam)
     polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
     ref, st0, _, _ = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 1))
-    # about 1% of the image's rays: 100 sequential chunks, or 200 overlapped ones (over 64)
-    ws = torch.empty(polrt.rt_workspace_hint(ctx) // 100, dtype=torch.uint8, device="cuda")
+    # about 1/400 of the image's rays: 400 sequential chunks, or 800 overlapped ones (over 256)
+    ws = torch.empty(polrt.rt_workspace_hint(ctx) // 400, dtype=torch.uint8, device="cuda")
     polrt.rt_set_workspace(ctx, ws)
     try:
         out, st, _, c = render(polrt, ctx, polrt.RT_MIXED, cam, (1, 0, 8))
-        assert c["chunks"] >= 64 and c["n_overflow"] == 0
+        assert c["chunks"] >= 256 and c["n_overflow"] == 0
         assert torch.equal(out, ref) and torch.equal(st, st0)
     finally:
         polrt.rt_set_workspace(ctx, None)
