@@ -208,7 +208,7 @@ int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config
     // first the number of geodesic warps at step tile 1, then the step tile at the best of
     // them; each shape is timed twice and keeps its faster time (one launch is noisy)
     int maxb = c->pipe_bps[fidx(form)];
-    rt_batch_config top{0, 0, 0, 0.f};
+    rt_batch_config top{0, 0, 0, 0.f, RT_BATCH_PERSISTENT};
     bool warm = false;
     auto trial = [&](rt_batch_config cand) -> int {
         if (!warm) {  // one untimed launch first
@@ -234,13 +234,13 @@ int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config
         return RT_OK;
     };
     for (int g : {2, 3, 4, 5, 6}) {
-        rv = trial(rt_batch_config{g, 1, maxb, 0.f});
+        rv = trial(rt_batch_config{g, 1, maxb, 0.f, RT_BATCH_PERSISTENT});
         if (rv) return rv;
     }
     if (top.geo_warps > 0) {
         const int g = top.geo_warps;
         for (int t : {2, 4}) {
-            rv = trial(rt_batch_config{g, t, maxb, 0.f});
+            rv = trial(rt_batch_config{g, t, maxb, 0.f, RT_BATCH_PERSISTENT});
             if (rv) return rv;
         }
     }
