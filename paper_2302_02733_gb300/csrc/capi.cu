@@ -112,6 +112,7 @@ int rt_destroy(rt_ctx *c) {
     cudaFree(c->d_ohist);
     cudaFree(c->d_bsteps);
     cudaFree(c->d_border);
+    cudaFree(c->d_probe);
     if (c->ws_owned) cudaFree(c->ws);
     cudaFree(c->d_stage);
     cudaFree(c->d_stage_status);
@@ -363,6 +364,38 @@ static int prepare_order(rt_ctx *c, const Camera &cam, long long npix) {
     return RT_OK;
 }
 
+// Predicted step counts for a new camera: trace the ray through the centre of every
+// kProbeStride x kProbeStride block (1/64 of the rays) with the one-pass carving of the
+// workspace, record their steps, and give every other pixel its block's count. Skipped when
+// the workspace's first chunk cannot hold the probe.
+constexpr int kProbeStride = 8;
+static int probe_steps(rt_ctx *c, const Camera &cam, Counters *ctr, RayRecord *rec, long long cap, const Arena &ar) {
+    const long long np = (long long)((cam.nx + kProbeStride - 1) / kProbeStride) *
+                         ((cam.ny + kProbeStride - 1) / kProbeStride);
+    if (np > cap) return RT_OK;
+    if (np > c->probe_cap) {
+        cudaFree(c->d_probe);
+        c->d_probe = nullptr;
+        c->probe_cap = 0;
+        if (cudaMalloc(&c->d_probe, sizeof(int) * np) != cudaSuccess) {
+            cudaGetLastError();
+            return RT_ERR_NOMEM;
+        }
+        c->probe_cap = np;
+    }
+    launch_probe_list(c->d_probe, cam.nx, cam.ny, kProbeStride, c->stream);
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
+    GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, np, 0};
+    ga.pix_list = c->d_probe;
+    ga.steps_out = c->d_steps;
+    launch_geodesic(ga, c->nsm * c->geo_bps, c->stream);
+    launch_steps_fill(c->d_steps, cam.nx, cam.ny, kProbeStride, c->stream);
+    CK(cudaGetLastError());
+    c->have_steps = true;
+    c->order_K = 0;
+    return RT_OK;
+}
+
 // Chunks of an overlapped render of nrays rays: at least `chunks`, more when a workspace half
 // cannot hold that many rays; -1 when that would need more than kMaxChunks.
 static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks, size_t per_ray) {
@@ -606,23 +639,6 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     if (chunk < 1) return RT_ERR_NOMEM;
     const long long Kseq = (nrays + chunk - 1) / chunk;
 
-    // ray order: longest first once a full render of this camera has recorded its step counts
-    const int *ray_list = list;
-    uint16_t *steps_out = nullptr;
-    if (!list) {
-        rv = prepare_order(c, cam, npix_img);
-        if (rv) return rv;
-        steps_out = c->d_steps;
-        const long long Kord = ovl ? K : Kseq;
-        if (c->have_steps) {
-            if (c->order_K != Kord) {
-                launch_order_build(c->d_steps, npix_img, (int)Kord, c->d_ohist, c->d_order, c->stream);
-                CK(cudaGetLastError());
-                c->order_K = Kord;
-            }
-            ray_list = c->d_order;
-        }
-    }
     RayRecord *rec = (RayRecord *)(base + off);
     off = align_up(off + sizeof(RayRecord) * chunk);
     long long nblocks = (long long)((c->ws_bytes - off - 3 * kAlign) / per_block);
@@ -637,6 +653,29 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         feat = (float4 *)(base + off);
         off = align_up(off + (size_t)nblocks * kBlockStates * sizeof(float4));
         sur_y = (float *)(base + off);
+    }
+
+    // ray order: longest first once a render of this camera has recorded its step counts, or,
+    // for a new camera of 2^18 rays or more, as a probe of one ray per 8 x 8 block predicts them
+    const int *ray_list = list;
+    uint16_t *steps_out = nullptr;
+    if (!list) {
+        rv = prepare_order(c, cam, npix_img);
+        if (rv) return rv;
+        steps_out = c->d_steps;
+        const long long Kord = ovl ? K : Kseq;
+        if (!c->have_steps && nrays >= (1ll << 18)) {
+            rv = probe_steps(c, cam, ctr, rec, chunk, ar);
+            if (rv) return rv;
+        }
+        if (c->have_steps) {
+            if (c->order_K != Kord) {
+                launch_order_build(c->d_steps, npix_img, (int)Kord, c->d_ohist, c->d_order, c->stream);
+                CK(cudaGetLastError());
+                c->order_K = Kord;
+            }
+            ray_list = c->d_order;
+        }
     }
 
     // outputs: device directly, or staged

@@ -47,6 +47,38 @@ __global__ void order_scatter_kernel(const uint16_t *steps, long long n, int K, 
     }
 }
 
+// The probe of a new camera: the pixel at the centre of each S x S block (clipped to the image).
+__device__ __forceinline__ int probe_pixel(int bx, int by, int nx, int ny, int S) {
+    return min(S * by + S / 2, ny - 1) * nx + min(S * bx + S / 2, nx - 1);
+}
+
+__global__ void probe_list_kernel(int *list, int nx, int ny, int S) {
+    const int px = (nx + S - 1) / S, py = (ny + S - 1) / S;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)px * py;
+         i += (long long)gridDim.x * blockDim.x)
+        list[i] = probe_pixel((int)(i % px), (int)(i / px), nx, ny, S);
+}
+
+// every other pixel takes the step count of its block's probe (which keeps its own)
+__global__ void steps_fill_kernel(uint16_t *steps, int nx, int ny, int S) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < (long long)nx * ny;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(p % nx), y = (int)(p / nx);
+        const int q = probe_pixel(x / S, y / S, nx, ny, S);
+        if (q != p) steps[p] = steps[q];
+    }
+}
+
+void launch_probe_list(int *list, int nx, int ny, int S, cudaStream_t s) {
+    long long n = (long long)((nx + S - 1) / S) * ((ny + S - 1) / S);
+    probe_list_kernel<<<(int)std::min<long long>((n + 255) / 256, 1024), 256, 0, s>>>(list, nx, ny, S);
+}
+
+void launch_steps_fill(uint16_t *steps, int nx, int ny, int S, cudaStream_t s) {
+    long long n = (long long)nx * ny;
+    steps_fill_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(steps, nx, ny, S);
+}
+
 void launch_order_build(const uint16_t *steps, long long n, int K, unsigned *hist, int *order, cudaStream_t s) {
     int grid = (int)std::min<long long>((n + 255) / 256, 1024);
     cudaMemsetAsync(hist, 0, kOrderBuckets * sizeof(unsigned), s);

@@ -64,6 +64,8 @@ struct rt_ctx {
     double order_key[8] = {};     // camera and integrator the steps belong to
     bool have_steps = false;
     long long order_K = 0;        // chunks d_order is dealt to; 0: not built
+    int *d_probe = nullptr;       // the probe's pixel list (a new camera's predicted order)
+    long long probe_cap = 0;
     // the same for the batched form's mode 1, by global ray id over the job table
     uint16_t *d_bsteps = nullptr;
     int *d_border = nullptr;

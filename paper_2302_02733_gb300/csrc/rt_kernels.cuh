@@ -126,6 +126,10 @@ void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
 // hist: kOrderBuckets unsigned of scratch.
 constexpr int kOrderBuckets = 1024;
 void launch_order_build(const uint16_t *steps, long long n, int K, unsigned *hist, int *order, cudaStream_t s);
+// The probe of a new camera: list[i] = the pixel at the centre of S x S block i (row-major over
+// blocks, clipped to the image); then every pixel takes its block's probe's step count.
+void launch_probe_list(int *list, int nx, int ny, int S, cudaStream_t s);
+void launch_steps_fill(uint16_t *steps, int nx, int ny, int S, cudaStream_t s);
 void launch_sincos_table(double *tab, cudaStream_t s);
 constexpr size_t kSinTabBytes = 1024 * 3 * sizeof(double);
 // coef: 0 thermal fits, 1 kappa quadrature at every emitting point, 2 surrogate outputs

@@ -128,3 +128,19 @@ def test_small_caller_workspace_falls_back_to_one_pass(rt, synth, torus_grid):
     finally:
         polrt.rt_set_workspace(ctx, None)
         polrt.rt_set_render_config(ctx, 0, 0, 0)
+
+
+def test_probe_order_for_a_new_camera(rt, synth, torus_grid):
+    """A new camera of 2^18 rays or more is first probed (one ray per 8 x 8 block) to predict
+    the longest-first order; the image equals that of the next render, which uses the exact
+    step counts the first one recorded."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=33.0, nx=512, ny=512)  # a camera no other test renders
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    polrt.rt_set_camera(ctx, cam)
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
+    first, st1, _, c1 = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 0))
+    second, st2, _, c2 = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 0))
+    assert torch.isfinite(first).all() and torch.equal(first, second) and torch.equal(st1, st2)
+    assert c1["steps"] == c2["steps"] and c1["rays"] == 512 * 512 and c1["n_overflow"] == 0
