@@ -27,6 +27,8 @@ struct Mth<double> {
     static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
     static __device__ __forceinline__ double log_(double x) { return log(x); }
     static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+    static __device__ __forceinline__ double log2_(double x) { return log2(x); }
+    static __device__ __forceinline__ double exp2_(double x) { return exp2(x); }
     static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
     static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
@@ -50,6 +52,8 @@ struct Mth<float> {
     static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
     static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float log2_(float x) { return log2f(x); }
+    static __device__ __forceinline__ float exp2_(float x) { return exp2f(x); }
     static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
     static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
@@ -139,6 +143,26 @@ __device__ __forceinline__ void bessel_k012_scaled(R z, const R *gw, R &k0, R &k
 }
 
 // ------------------------------------------------------------------------------------------
+// Shcherbakov's (2008) correction of rho_Q,
+//   f(X) = 2.011 e^{-X^1.035/4.7} - cos(X/2) e^{-X^1.2/2.73} - 0.011 e^{-X/47.2}
+//          + [X > 1] (0.011 e^{-X/47.2} - 2^{-1/3} 3^{-23/6} 1e4 pi X^{-8/3}) (1 + tanh(10 ln(X/120)))/2,
+// with the three powers from one log2 X, and (1 + tanh y)/2 = 1 - 1/(e^{2y} + 1) where
+// e^{2y} = (X/120)^20 (which may overflow to infinity: the form stays exact there).
+template <typename R>
+__device__ __forceinline__ R shcherbakov_fX(R X) {
+    typedef Mth<R> F;
+    const R lX = F::log2_(X);  // -inf at X = 0, where the powers are 0
+    const R eX = F::exp_(-X / R(47.2));
+    R f = R(2.011) * F::exp_(-F::exp2_(R(1.035) * lX) / R(4.7)) -
+          F::cos_(R(0.5) * X) * F::exp_(-F::exp2_(R(1.2) * lX) / R(2.73)) - R(0.011) * eX;
+    if (X > R(1)) {
+        const R t = F::exp2_(R(20) * (lX - R(6.9068905956085187)));  // (X/120)^20; log2 120
+        f += (R(0.011) * eX - R(369.6934286909082) * F::exp2_(R(-8.0 / 3.0) * lX)) * (R(1) - R(1) / (t + R(1)));
+    }
+    return f;
+}
+
+// ------------------------------------------------------------------------------------------
 // Thermal synchrotron coefficients in the fluid frame (cgs).
 // Emission: the Dexter (2016) fits with nu_c = (3/2) nu_B sin(th) Theta^2, x = nu/nu_c:
 //   j_I = n e^2 nu/(2 sqrt3 c Theta^2) 2.5651 (1 + 1.92 x^-1/3 + 0.9977 x^-2/3) e^{-1.8899 x^1/3},
@@ -175,12 +199,7 @@ __device__ __forceinline__ void thermal_coeffs(R ne, R Te, R B, R nu, R sth, R c
     } else {  // K_n(z)/K_2(z) -> 1 as z -> infinity
         k0 = k1 = k2 = R(1);
     }
-    R f = R(2.011) * F::exp_(-F::pow_(X, R(1.035)) / R(4.7)) -
-          F::cos_(R(0.5) * X) * F::exp_(-F::pow_(X, R(1.2)) / R(2.73)) - R(0.011) * F::exp_(-X / R(47.2));
-    if (X > R(1))
-        f += (R(0.011) * F::exp_(-X / R(47.2)) -
-              R(369.6934286909082) * F::pow_(X, R(-8.0 / 3.0))) *  // 2^-1/3 3^-23/6 1e4 pi
-             R(0.5) * (R(1) + F::tanh_(R(10) * F::log_(X / R(120))));
+    R f = shcherbakov_fX(X);
     R gX = R(1) - R(0.11) * F::log1p_(R(0.035) * X);
     out[6] = cQ2 * ne * rb * rb / nu * sth * sth * f * (k1 / k2 + R(6) * Te);
     out[7] = R(2) * cQ2 * ne * rb / nu * cth * (k0 / k2) * gX;

@@ -163,11 +163,7 @@ __device__ __forceinline__ SurPrefR<R> sur_prefactors_r(R ne, R Te, R B, R nu, R
     p.Pa = cQ2 * ne / (R(4.0 * 1.7320508075688772) * nu * Te * Te * Te);
     p.PaV = p.Pa * cot;
     R X = Te * F::sqrt_(R(1.4142135623730951) * as * R(1e3) * rb);
-    R f = R(2.011) * F::exp_(-F::pow_(X, R(1.035)) / R(4.7)) -
-          F::cos_(R(0.5) * X) * F::exp_(-F::pow_(X, R(1.2)) / R(2.73)) - R(0.011) * F::exp_(-X / R(47.2));
-    if (X > R(1))
-        f += (R(0.011) * F::exp_(-X / R(47.2)) - R(369.6934286909082) * F::pow_(X, R(-8.0 / 3.0))) * R(0.5) *
-             (R(1) + F::tanh_(R(10) * F::log_(X / R(120))));
+    R f = shcherbakov_fX(X);
     p.PrQ = cQ2 * ne * rb * rb / nu * sth * sth * f;
     p.PrV = R(2) * cQ2 * ne * rb / nu * ac * (R(1) - R(0.11) * F::log1p_(R(0.035) * X));
     p.sgn = cth < R(0) ? R(-1) : R(1);
