@@ -299,7 +299,7 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
  * render of the same camera and integrator takes its rays longest first (dealt round-robin to
  * the chunks), so that no launch ends waiting for a few long photon-ring rays. The first render
  * of a new camera of 2^18 rays or more predicts the counts from a probe of one ray per 8 x 8
- * block. The image is the
+ * block; the next render rebuilds the order from the counts the first one recorded. The image is the
  * same either way (every ray takes the same arithmetic); only the time differs. Shapes that
  * exceed the kernels' occupancy or chunks above 256 return RT_ERR_INVALID. */
 typedef struct {

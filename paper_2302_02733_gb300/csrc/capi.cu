@@ -340,6 +340,7 @@ static int prepare_order(rt_ctx *c, const Camera &cam, long long npix) {
     if (memcmp(key, c->order_key, sizeof(key)) != 0) {
         memcpy(c->order_key, key, sizeof(key));
         c->have_steps = false;
+        c->steps_probed = false;
         c->order_K = 0;
     }
     if (npix > c->order_cap) {
@@ -349,6 +350,7 @@ static int prepare_order(rt_ctx *c, const Camera &cam, long long npix) {
         c->d_order = nullptr;
         c->order_cap = 0;
         c->have_steps = false;
+        c->steps_probed = false;
         c->order_K = 0;
         if (cudaMalloc(&c->d_steps, sizeof(uint16_t) * npix) != cudaSuccess ||
             cudaMalloc(&c->d_order, sizeof(int) * npix) != cudaSuccess) {
@@ -392,6 +394,7 @@ static int probe_steps(rt_ctx *c, const Camera &cam, Counters *ctr, RayRecord *r
     launch_steps_fill(c->d_steps, cam.nx, cam.ny, kProbeStride, c->stream);
     CK(cudaGetLastError());
     c->have_steps = true;
+    c->steps_probed = true;
     c->order_K = 0;
     return RT_OK;
 }
@@ -751,7 +754,13 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     c->last_rays = nrays;
     c->last_was_batch = false;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
-    if (steps_out) c->have_steps = true;  // every ray of this camera recorded its steps
+    if (steps_out) {  // every ray of this camera recorded its steps
+        c->have_steps = true;
+        if (c->steps_probed) {  // the order came from the probe: rebuild it from the counts
+            c->steps_probed = false;
+            c->order_K = 0;
+        }
+    }
     return RT_OK;
 }
 

@@ -66,6 +66,7 @@ struct rt_ctx {
     long long order_K = 0;        // chunks d_order is dealt to; 0: not built
     int *d_probe = nullptr;       // the probe's pixel list (a new camera's predicted order)
     long long probe_cap = 0;
+    bool steps_probed = false;    // d_steps holds the probe's predictions, not recorded counts
     // the same for the batched form's mode 1, by global ray id over the job table
     uint16_t *d_bsteps = nullptr;
     int *d_border = nullptr;
