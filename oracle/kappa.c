@@ -16,7 +16,8 @@
  *    F and G are the single-electron synchrotron functions (Rybicki & Lightman 6.31-6.32); the
  *    circular kernel H and its factor 4/3 are fixed by the thermal limit: with the
  *    Maxwell-Juttner distribution these integrals are exactly those that the thermal fits
- *    approximate (checked in the tests).
+ *    approximate. All three are the leading order in 1/gamma of the exact sum over cyclotron
+ *    harmonics (the Schott series), which the tests evaluate for both distributions.
  *  - absorption for every Stokes component from the emission kernel k_S (j_S = int N k_S):
  *      a_S = -(1 / (2 nu^2 m)) int k_S g^2 d/dg (N / g^2) dg     (Rybicki & Lightman 6.50),
  *    which reduces to Kirchhoff's law (Rayleigh-Jeans) for Maxwell-Juttner electrons.

@@ -15,10 +15,10 @@
  * The paper leaves every formula to its method paper, which is not available here. Each
  * function states the reading it implements. Every reading is listed in the design notes.
  *
- * Parity unpinned: the normalisation of the circularly polarized emissivity j_V and the
- * Shcherbakov correction functions of the rotativities away from their X -> 0 limit. Both
- * are transcriptions of published fits, and nothing in this repository pins them
- * independently. The absolute flux scale follows from the model constants.
+ * Parity unpinned: the Shcherbakov correction functions of the rotativities away from their
+ * X -> 0 limit, a transcription of a published fit that nothing in this repository pins
+ * independently. The absolute flux scale follows from the model constants. (The emissivities,
+ * j_V included, are pinned by the exact sum over cyclotron harmonics.)
  */
 #ifndef PR_ORACLE_H
 #define PR_ORACLE_H
