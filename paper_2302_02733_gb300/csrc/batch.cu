@@ -78,6 +78,15 @@ int ensure_jobs(rt_ctx *c, int njobs) {
     return RT_OK;
 }
 
+void free_pool(rt_ctx *c) {
+    cudaFree(c->pool.states);
+    cudaFree(c->pool.prev);
+    cudaFree(c->pool.fill);
+    cudaFree(c->pool.ring);
+    c->pool = Pool{};
+    cudaGetLastError();
+}
+
 int ensure_buffers(rt_ctx *c, int njobs, long long nrays) {
     int rv = ensure_jobs(c, njobs);
     if (rv) return rv;
@@ -108,7 +117,7 @@ int ensure_buffers(rt_ctx *c, int njobs, long long nrays) {
         Pool &P = c->pool;
         if (realloc_dev(&P.states, (size_t)nb * kBlockStates) || realloc_dev(&P.prev, (size_t)nb) ||
             realloc_dev(&P.fill, (size_t)nb) || realloc_dev(&P.ring, (size_t)nb)) {
-            free_batch(c);
+            free_pool(c);  // the part that was allocated; the next call tries again
             return RT_ERR_NOMEM;
         }
         P.nblocks = (int)nb;
@@ -269,10 +278,7 @@ void free_batch(rt_ctx *c) {
     if (c->h_jobs) cudaFreeHost(c->h_jobs);
     cudaFree(c->d_brec);
     cudaFree(c->d_ready);
-    cudaFree(c->pool.states);
-    cudaFree(c->pool.prev);
-    cudaFree(c->pool.fill);
-    cudaFree(c->pool.ring);
+    free_pool(c);
     cudaFree(c->d_pctr);
     if (c->h_pctr) cudaFreeHost(c->h_pctr);
     c->d_jobs = c->h_jobs = nullptr;
@@ -280,7 +286,6 @@ void free_batch(rt_ctx *c) {
     c->d_brec = nullptr;
     c->d_ready = nullptr;
     c->brays_cap = 0;
-    c->pool = Pool{};
     c->d_pctr = c->h_pctr = nullptr;
     for (int i = 0; i < 3; i++)
         if (c->bev[i]) cudaEventDestroy(c->bev[i]);

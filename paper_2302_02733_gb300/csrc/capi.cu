@@ -158,7 +158,8 @@ int rt_set_camera(rt_ctx *c, const rt_camera *cam) {
 
 int rt_load_model(rt_ctx *c, const rt_model_params *p) {
     if (!c || !p) return RT_ERR_INVALID;
-    CK(cudaSetDevice(c->device));
+    if (p->edf != RT_EDF_THERMAL && !(p->edf == RT_EDF_KAPPA && p->kappa > 3.0 && p->kappa < 100.0))
+        return RT_ERR_INVALID;
     if (p->kind == RT_MODEL_ADAF) {
         const rt_adaf_params &a = p->adaf;
         if (!(a.n0 > 0) || !(a.T0 > 0) || !(a.beta > 0) || !(a.Ti_over_Te >= 0) || !(a.r_out > 0))
@@ -168,6 +169,15 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
         if (g.n1 < 2 || g.n2 < 2 || g.n3 < 1 || !g.prims || !(g.r_in > 0) || !(g.r_out > g.r_in) ||
             !(g.M_unit > 0) || !(g.gamma_ad > 1.0) || !(g.poly_alpha > 0) || !(g.poly_xt > 0))
             return RT_ERR_INVALID;
+    } else {
+        return RT_ERR_INVALID;
+    }
+    CK(cudaSetDevice(c->device));
+    if (p->kind == RT_MODEL_GRID) {
+        const rt_grid_params &g = p->grid;
+        // the grid's device buffers change from here on: until they all hold the new grid there
+        // is no model (a failure leaves none, rather than the old description over new buffers)
+        c->have_model = false;
         size_t bytes = (size_t)g.n1 * g.n2 * g.n3 * 8 * sizeof(float);
         if (bytes != c->prims_bytes) {
             cudaFree(c->d_prims);
@@ -215,11 +225,7 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
         launch_x2_table(gm, c->d_x2, c->d_x2f, c->stream);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->stream));
-    } else {
-        return RT_ERR_INVALID;
     }
-    if (p->edf != RT_EDF_THERMAL && !(p->edf == RT_EDF_KAPPA && p->kappa > 3.0 && p->kappa < 100.0))
-        return RT_ERR_INVALID;
     c->model = *p;
     c->model.grid.prims = nullptr;  // the device copy is used from here on
     c->have_model = true;
@@ -864,6 +870,7 @@ int rt_kappa_coeffs(rt_ctx *c, const double *in, long long n, double *out) {
     double *d_out = out;
     void *tmp = nullptr;
     bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+    cudaError_t e = cudaSuccess;
     if (!in_dev || !out_dev) {
         if (cudaMalloc(&tmp, (size_t)n * 14 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
@@ -871,13 +878,15 @@ int rt_kappa_coeffs(rt_ctx *c, const double *in, long long n, double *out) {
         }
         if (!in_dev) {
             d_in = (const double *)tmp;
-            CK(cudaMemcpyAsync((void *)d_in, in, (size_t)n * 6 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            e = cudaMemcpyAsync((void *)d_in, in, (size_t)n * 6 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         }
         if (!out_dev) d_out = (double *)tmp + 6 * n;
     }
-    KappaTables T{c->d_syn, c->d_gl, c->d_gl + 8};
-    launch_kappa_quad(T, d_in, d_out, n, c->nsm * 8, c->stream);
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        KappaTables T{c->d_syn, c->d_gl, c->d_gl + 8};
+        launch_kappa_quad(T, d_in, d_out, n, c->nsm * 8, c->stream);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && !out_dev)
         e = cudaMemcpyAsync(out, d_out, (size_t)n * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

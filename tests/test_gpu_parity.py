@@ -285,3 +285,23 @@ def test_invalid_arguments(rt, synth):
     bad = polrt.rt_camera(1.2, 60.0, 1000.0, 2.3e11, 40.0, 8, 8, 1e40, 1e22)
     assert L.rt_set_camera(ctx, polrt.C.byref(bad)) == polrt.RT_ERR_INVALID
     assert L.rt_render(ctx, 7, None, None) == polrt.RT_ERR_INVALID
+
+
+def test_rejected_model_leaves_the_loaded_one(rt, synth, torus_grid, small_grid):
+    """A model rejected for its arguments (here kappa electrons with kappa outside (3, 100))
+    changes nothing on the device: the grid loaded before it renders the same image, although
+    the rejected grid has other dimensions."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=20.0, nx=32, ny=24)
+    rc, ref, st0, _ = gpu_render(rt, cam, polrt.grid_model(torch.from_numpy(prims).cuda(), g), polrt.RT_MIXED)
+    assert rc == 0
+    sprims, sg = small_grid
+    sp = torch.from_numpy(sprims).cuda()
+    bad = polrt.grid_model(sp, sg)
+    bad.edf, bad.kappa = polrt.RT_EDF_KAPPA, 2.0
+    assert polrt.lib().rt_load_model(ctx, polrt.C.byref(bad)) == polrt.RT_ERR_INVALID
+    out = torch.full((cam.ny, cam.nx, 4), float("nan"), dtype=torch.float32, device="cuda")
+    st = torch.zeros((cam.ny, cam.nx), dtype=torch.uint8, device="cuda")
+    assert polrt.rt_render(ctx, polrt.RT_MIXED, out, st, check=False) == 0
+    assert np.array_equal(out.cpu().numpy().astype(np.float64), ref) and np.array_equal(st.cpu().numpy(), st0)
