@@ -150,7 +150,10 @@ int rt_set_stream(rt_ctx *ctx, void *stream);
  * Grid primitives are copied to a context-owned device buffer. Synchronizes on the copy. */
 int rt_load_model(rt_ctx *ctx, const rt_model_params *p);
 
-/* Camera: spin, inclination, distance, frequency, field of view and resolution. */
+/* Camera: spin, inclination, distance, frequency, field of view and resolution. Copied.
+ * RT_ERR_INVALID for |a| >= 1, an inclination outside (0, 180) degrees, a size, frequency,
+ * field of view, mass or distance that is not positive, or r_cam <= 2 r_h; RT_ERR_SIZE for
+ * more than 2^31 - 1 pixels. */
 int rt_set_camera(rt_ctx *ctx, const rt_camera *cam);
 
 /* Geodesic step control: h = eps / (|K^r|/r + |K^th|/max(min(th, pi - th), 0.01) + |K^ph|),
@@ -268,7 +271,8 @@ int rt_surrogate_coeffs(rt_ctx *ctx, const double *in, long long n, double *out,
  * smallest feature of interest. out (and
  * status, optional) are device buffers in rt_render's layout for form RT_FP64, RT_MIXED or
  * RT_UNPOL; every pixel is written. *rays_traced (optional) receives the number of rays
- * traced. Synchronizes. */
+ * traced. Rays that overflow the path arena are marked RT_RAY_OVERFLOW as in rt_render; the
+ * refinement still completes and the call then returns RT_ERR_WORKSPACE. Synchronizes. */
 int rt_render_adaptive(rt_ctx *ctx, int form, void *out, uint8_t *status, int base_step, double tol,
                        long long *rays_traced);
 

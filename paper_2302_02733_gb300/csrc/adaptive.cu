@@ -171,6 +171,7 @@ int rt_render_adaptive(rt_ctx *c, int form, void *out, uint8_t *status, int base
     unsigned *count = (unsigned *)scal;
     unsigned long long *imax = scal + 1;
     int rv = RT_OK;
+    int overflow = RT_OK;  // RT_ERR_WORKSPACE once a level's rays overflowed the arena
     long long traced = 0;
     cudaStream_t s = c->stream;
     int grid = c->nsm * 4;
@@ -187,6 +188,7 @@ int rt_render_adaptive(rt_ctx *c, int form, void *out, uint8_t *status, int base
             return RT_ERR_CUDA;
         int r = render_pixel_list(c, form, out, st, list, n);
         if (r != RT_OK && r != RT_ERR_WORKSPACE) return r;
+        if (r) overflow = r;
         traced += n;
         imax_kernel<T><<<grid, 256, 0, s>>>(img, nc, state, npix, imax);
         // every lattice block starts active
@@ -212,6 +214,7 @@ int rt_render_adaptive(rt_ctx *c, int form, void *out, uint8_t *status, int base
             if (n > 0) {
                 r = render_pixel_list(c, form, out, st, list, n);
                 if (r != RT_OK && r != RT_ERR_WORKSPACE) return r;
+                if (r) overflow = r;
                 traced += n;
             }
             if (cudaMemsetAsync(count, 0, sizeof(unsigned), s) != cudaSuccess) return RT_ERR_CUDA;
@@ -225,6 +228,7 @@ int rt_render_adaptive(rt_ctx *c, int form, void *out, uint8_t *status, int base
             if (n > 0) {
                 r = render_pixel_list(c, form, out, st, list, n);
                 if (r != RT_OK && r != RT_ERR_WORKSPACE) return r;
+                if (r) overflow = r;
                 traced += n;
             }
             cur = 1 - cur;
@@ -232,6 +236,7 @@ int rt_render_adaptive(rt_ctx *c, int form, void *out, uint8_t *status, int base
         return RT_OK;
     };
     rv = form == RT_FP64 ? step(0.0) : step(0.0f);
+    if (rv == RT_OK) rv = overflow;  // the refinement went on; the overflowed rays are marked
     cudaFree(buf);
     cudaGetLastError();
     if (rays_traced) *rays_traced = traced;

@@ -96,7 +96,7 @@ int ensure_buffers(rt_ctx *c, int njobs, long long nrays) {
         if (realloc_dev(&c->d_brec, (size_t)nrays) || realloc_dev(&c->d_ready, (size_t)nrays)) return RT_ERR_NOMEM;
         c->brays_cap = nrays;
     }
-    if (!c->d_pctr) {
+    if (!c->d_pctr || !c->h_pctr) {
         if (realloc_dev(&c->d_pctr, 1)) return RT_ERR_NOMEM;
         if (cudaMallocHost(&c->h_pctr, sizeof(PipeCounters)) != cudaSuccess) {
             cudaGetLastError();

@@ -30,7 +30,7 @@ inline int check_camera(const rt_camera &cam) {
         return RT_ERR_INVALID;
     double rh = 1.0 + std::sqrt(1.0 - cam.a * cam.a);
     if (!(cam.r_cam > 2.0 * rh)) return RT_ERR_INVALID;
-    if ((long long)cam.nx * cam.ny > (1ll << 31)) return RT_ERR_SIZE;
+    if ((long long)cam.nx * cam.ny > 2147483647ll) return RT_ERR_SIZE;  // pixels are indexed by int
     return RT_OK;
 }
 

@@ -206,6 +206,15 @@ int ensure_mlp(rt_ctx *c) {
     size_t pb = kMlpParams * sizeof(float);
     if (cudaMalloc(&c->d_theta, 4 * pb) != cudaSuccess || cudaMalloc(&c->d_wpk, kPkWBytes) != cudaSuccess ||
         cudaMalloc(&c->d_tpk, kPkTBytes) != cudaSuccess || cudaMalloc(&c->d_mlpaux, kAuxBytes) != cudaSuccess) {
+        // all or nothing: d_theta is what later calls test
+        cudaFree(c->d_theta);
+        cudaFree(c->d_wpk);
+        cudaFree(c->d_tpk);
+        cudaFree(c->d_mlpaux);
+        c->d_theta = nullptr;
+        c->d_wpk = nullptr;
+        c->d_tpk = nullptr;
+        c->d_mlpaux = nullptr;
         cudaGetLastError();
         return RT_ERR_NOMEM;
     }

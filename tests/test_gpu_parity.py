@@ -284,6 +284,8 @@ def test_invalid_arguments(rt, synth):
     assert L.rt_set_camera(ctx, polrt.C.byref(bad)) == polrt.RT_ERR_INVALID
     bad = polrt.rt_camera(1.2, 60.0, 1000.0, 2.3e11, 40.0, 8, 8, 1e40, 1e22)
     assert L.rt_set_camera(ctx, polrt.C.byref(bad)) == polrt.RT_ERR_INVALID
+    big = polrt.rt_camera(0.9375, 60.0, 1000.0, 2.3e11, 40.0, 65536, 32768, 1e40, 1e22)  # 2^31 pixels
+    assert L.rt_set_camera(ctx, polrt.C.byref(big)) == polrt.RT_ERR_SIZE
     assert L.rt_render(ctx, 7, None, None) == polrt.RT_ERR_INVALID
 
 
