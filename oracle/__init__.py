@@ -67,6 +67,7 @@ def lib():
         L.ora_camera_ray.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, _D, _D]
         L.ora_trace_geodesic.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, C.c_int, _D, _I]
         L.ora_trace_geodesic.restype = C.c_int
+        L.ora_transport_vector.argtypes = [C.c_double, _D, C.c_int, _D, _D]
         L.ora_fmks_theta.argtypes = [C.POINTER(Model), C.c_double, C.c_double, _D, _D]
         L.ora_fmks_theta.restype = C.c_double
         L.ora_fmks_x2.argtypes = [C.POINTER(Model), C.c_double, C.c_double]
@@ -206,6 +207,17 @@ def trace_geodesic(cam: Camera, px: float, py: float):
     stat = C.c_int(0)
     n = L.ora_trace_geodesic(C.byref(cam), px, py, maxst, _dp(st), C.byref(stat))
     return st[: n + 1].copy(), stat.value
+
+
+def transport_vector(a, states, f):
+    """The vector f at the last saved state carried back along the path to every state, as
+    the transfer carries each index of the coherency tensor; rows follow the states."""
+    st = np.ascontiguousarray(states, dtype=np.float64)
+    M = st.shape[0] - 1
+    fv = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros((M + 1, 4))
+    lib().ora_transport_vector(a, _dp(st), M, _dp(fv), _dp(out))
+    return out
 
 
 def metric(a, r, th):

@@ -698,6 +698,44 @@ static void heun_propagator(double h, double T1[4][4], double T0[4][4], double P
         }
 }
 
+/* The propagator of the vector transport over the segment from saved point n+1 (s1) to point
+ * n (sn). A segment that crossed the polar axis saved point n+1 reflected (theta -> -theta or
+ * 2 pi - theta, phi + pi, K^theta -> -K^theta); it is taken back to the chart of point n, and
+ * *flip tells the caller to change the sign of the theta components of what it transports. */
+static void segment_propagator(double a, const double *sn, const double *s1, double P[4][4], int *flip) {
+    double h = fabs(sn[8]);
+    double th1 = s1[2], K1[4] = {s1[4], s1[5], s1[6], s1[7]};
+    *flip = sn[8] < 0.0;
+    if (*flip) {
+        th1 = (sn[2] < 0.5 * O_PI) ? -th1 : 2.0 * O_PI - th1;
+        K1[2] = -K1[2];
+    }
+    double T1[4][4], T0[4][4];
+    tmat(a, s1[1], th1, K1, T1);
+    tmat(a, sn[1], sn[2], sn + 4, T0);
+    heun_propagator(h, T1, T0, P);
+}
+
+/* A real vector f given at the far end of a saved path (point M), transported to every saved
+ * point in turn exactly as the transfer transports each index of N. out holds M + 1 rows of
+ * 4 components, row n at point n (row M = f). For the pins of the transport. */
+void ora_transport_vector(double a, const double *states, int M, const double f[4], double *out) {
+    for (int i = 0; i < 4; i++) out[M * 4 + i] = f[i];
+    for (int n = M - 1; n >= 0; n--) {
+        const double *sn = states + n * 9, *s1 = states + (n + 1) * 9;
+        double P[4][4], v[4];
+        int flip;
+        segment_propagator(a, sn, s1, P, &flip);
+        for (int i = 0; i < 4; i++) v[i] = out[(n + 1) * 4 + i];
+        if (flip) v[2] = -v[2];
+        for (int i = 0; i < 4; i++) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; k++) acc += P[i][k] * v[k];
+            out[n * 4 + i] = acc;
+        }
+    }
+}
+
 /* Each index of N^{mu nu} is transported as a vector: N <- P N P^T. */
 static void congruence(double P[4][4], cplx N[4][4]) {
     cplx X[4][4];
@@ -823,18 +861,13 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
         const double *sn = st + n * 9, *s1 = st + (n + 1) * 9;
         double h = fabs(sn[8]);
         /* transport N from point n+1 to point n */
-        double th1 = s1[2], K1[4] = {s1[4], s1[5], s1[6], s1[7]};
-        if (sn[8] < 0.0) {
-            th1 = (sn[2] < 0.5 * O_PI) ? -th1 : 2.0 * O_PI - th1;
-            K1[2] = -K1[2];
+        double P[4][4];
+        int flip;
+        segment_propagator(a, sn, s1, P, &flip);
+        if (flip)
             for (int i = 0; i < 4; i++)
                 for (int j = 0; j < 4; j++)
                     if ((i == 2) != (j == 2)) N[i][j] = -N[i][j];
-        }
-        double T1[4][4], T0[4][4], P[4][4];
-        tmat(a, s1[1], th1, K1, T1);
-        tmat(a, sn[1], sn[2], sn + 4, T0);
-        heun_propagator(h, T1, T0, P);
         congruence(P, N);
         /* radiative step at point n */
         double pl[12];

@@ -65,6 +65,9 @@ void ora_camera_ray(const ora_camera *cam, double px, double py, double x[4], do
 /* states[n*9]: t r th ph Kt Kr Kth Kph h (h<0 marks a pole reflection on that step) */
 int ora_trace_geodesic(const ora_camera *cam, double px, double py, int maxstates,
                        double *states, int *status);
+/* the transfer's transport of one index of N: a vector f at saved point M carried back to
+ * points M-1..0; out[(M+1)*4], row n at point n */
+void ora_transport_vector(double a, const double *states, int M, const double f[4], double *out);
 
 /* plasma */
 double ora_fmks_theta(const ora_model *m, double X1, double X2, double *dth1, double *dth2);
