@@ -68,6 +68,7 @@ def lib():
         L.ora_trace_geodesic.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, C.c_int, _D, _I]
         L.ora_trace_geodesic.restype = C.c_int
         L.ora_transport_vector.argtypes = [C.c_double, _D, C.c_int, _D, _D]
+        L.ora_camera_stokes.argtypes = [C.POINTER(Camera), C.c_double, C.c_double, _D, _D, _D]
         L.ora_fmks_theta.argtypes = [C.POINTER(Model), C.c_double, C.c_double, _D, _D]
         L.ora_fmks_theta.restype = C.c_double
         L.ora_fmks_x2.argtypes = [C.POINTER(Model), C.c_double, C.c_double]
@@ -218,6 +219,16 @@ def transport_vector(a, states, f):
     out = np.zeros((M + 1, 4))
     lib().ora_transport_vector(a, _dp(st), M, _dp(fv), _dp(out))
     return out
+
+
+def camera_stokes(cam: Camera, px, py, N):
+    """(I, Q, U, V) that the transfer's camera reads from the coherency tensor N (4 x 4,
+    real or complex) for the pixel at image coordinates (px, py)."""
+    N = np.asarray(N, dtype=np.complex128)
+    re, im = np.ascontiguousarray(N.real), np.ascontiguousarray(N.imag)
+    S = np.zeros(4)
+    lib().ora_camera_stokes(C.byref(cam), px, py, _dp(re), _dp(im), _dp(S))
+    return S
 
 
 def metric(a, r, th):

@@ -844,6 +844,40 @@ static void N_from_stokes(const double e1[4], const double e2[4], const double S
             N[m][n] = n11 * e1[m] * e1[n] + n22 * e2[m] * e2[n] + n12 * e1[m] * e2[n] + n21 * e2[m] * e1[n];
 }
 
+/* The camera's reading of N for the pixel at image coordinates (px, py): Stokes on the image
+ * basis x ~ e_phi, y ~ -e_theta of the camera frame, each projected normal to the ray. */
+static void camera_stokes(const ora_camera *cam, double px, double py, cplx N[4][4], double S[4]) {
+    double e[4][4], s[3];
+    camera_frame(cam, e);
+    sky_dir(cam, px, py, s);
+    double xh[3] = {0.0 - s[2] * s[0], 0.0 - s[2] * s[1], 1.0 - s[2] * s[2]};
+    double nx = sqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
+    for (int i = 0; i < 3; i++) xh[i] /= nx;
+    double yh[3] = {0.0 + s[1] * s[0], -1.0 + s[1] * s[1], 0.0 + s[1] * s[2]};
+    double yx = yh[0] * xh[0] + yh[1] * xh[1] + yh[2] * xh[2];
+    for (int i = 0; i < 3; i++) yh[i] -= yx * xh[i];
+    double ny = sqrt(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
+    for (int i = 0; i < 3; i++) yh[i] /= ny;
+    double X[4], Y[4];
+    for (int mm = 0; mm < 4; mm++) {
+        X[mm] = xh[0] * e[1][mm] + xh[1] * e[2][mm] + xh[2] * e[3][mm];
+        Y[mm] = yh[0] * e[1][mm] + yh[1] * e[2][mm] + yh[2] * e[3][mm];
+    }
+    double g[16];
+    ora_metric_ks(cam->a, cam->r_cam, cam->incl_deg * O_PI / 180.0, g);
+    stokes_from_N(g, X, Y, N, S);
+}
+
+/* camera_stokes for a caller's N^{mu nu} (real and imaginary parts, row-major 4 x 4). For the
+ * pins of the camera's Stokes basis. */
+void ora_camera_stokes(const ora_camera *cam, double px, double py, const double Nre[16], const double Nim[16],
+                       double S[4]) {
+    cplx N[4][4];
+    for (int m = 0; m < 4; m++)
+        for (int n = 0; n < 4; n++) N[m][n] = Nre[m * 4 + n] + I * Nim[m * 4 + n];
+    camera_stokes(cam, px, py, N, S);
+}
+
 typedef struct {
     double st[4], minpol;
     double tau, phi; /* optical depth sum alpha_I ds and Faraday depth sum rho_V ds */
@@ -908,26 +942,8 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
         }
         N_from_stokes(e1, e2, S, N);
     }
-    /* camera: Stokes on the image basis x ~ e_phi, y ~ -e_theta, projected normal to the ray */
-    double e[4][4], s[3];
-    camera_frame(cam, e);
-    sky_dir(cam, px, py, s);
-    double xh[3] = {0.0 - s[2] * s[0], 0.0 - s[2] * s[1], 1.0 - s[2] * s[2]};
-    double nx = sqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
-    for (int i = 0; i < 3; i++) xh[i] /= nx;
-    double yh[3] = {0.0 + s[1] * s[0], -1.0 + s[1] * s[1], 0.0 + s[1] * s[2]};
-    double yx = yh[0] * xh[0] + yh[1] * xh[1] + yh[2] * xh[2];
-    for (int i = 0; i < 3; i++) yh[i] -= yx * xh[i];
-    double ny = sqrt(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
-    for (int i = 0; i < 3; i++) yh[i] /= ny;
-    double X[4], Y[4];
-    for (int mm = 0; mm < 4; mm++) {
-        X[mm] = xh[0] * e[1][mm] + xh[1] * e[2][mm] + xh[2] * e[3][mm];
-        Y[mm] = yh[0] * e[1][mm] + yh[1] * e[2][mm] + yh[2] * e[3][mm];
-    }
-    double g[16], S[4];
-    ora_metric_ks(a, st[1], st[2], g);
-    stokes_from_N(g, X, Y, N, S);
+    double S[4];
+    camera_stokes(cam, px, py, N, S);
     pix_out o = {{S[0], S[1], S[2], S[3]}, minpol, tau, phi};
     return o;
 }

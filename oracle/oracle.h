@@ -68,6 +68,10 @@ int ora_trace_geodesic(const ora_camera *cam, double px, double py, int maxstate
 /* the transfer's transport of one index of N: a vector f at saved point M carried back to
  * points M-1..0; out[(M+1)*4], row n at point n */
 void ora_transport_vector(double a, const double *states, int M, const double f[4], double *out);
+/* the transfer's camera reading of N^{mu nu} (Nre + i Nim, row-major) for pixel (px, py):
+ * S = (I, Q, U, V) on the image basis x ~ e_phi, y ~ -e_theta */
+void ora_camera_stokes(const ora_camera *cam, double px, double py, const double Nre[16], const double Nim[16],
+                       double S[4]);
 
 /* plasma */
 double ora_fmks_theta(const ora_model *m, double X1, double X2, double *dth1, double *dth2);

@@ -1,5 +1,6 @@
 """Pins of the oracle's transport of the coherency tensor, through the vector transport it
-applies to each index (oracle/oracle.c, the transfer's own segment propagator).
+applies to each index (oracle/oracle.c, the transfer's own segment propagator), and of the
+camera's reading of it (the transfer's own camera_stokes).
 
 Along a null geodesic k of the Kerr metric, a parallel-transported vector f keeps f.f and f.k,
 and the Walker-Penrose quantity (Walker & Penrose 1970; in this form Connors, Piran & Stark
@@ -121,3 +122,37 @@ def test_walker_penrose_detects_a_sign_slip(ora, synth):
         worst = max(worst, abs(walker_penrose(a, st[n, 1], st[n, 2], st[n, 4:8], f) - k0) / abs(k0))
         T1 = T0
     assert worst > 0.5, worst
+
+
+def wrap_half_turn(d):
+    """An angle difference taken modulo pi into [-pi/2, pi/2)."""
+    return (d + math.pi / 2) % math.pi - math.pi / 2
+
+
+@pytest.mark.parametrize("a,incl", [(A_SPIN, 60.0), (A_SPIN, 20.0), (0.0, 60.0), (-0.7, 75.0)])
+def test_camera_polarization_angle_matches_connors_piran_stark(ora, synth, a, incl):
+    """The camera's Stokes basis and Q/U convention, through the transfer's own camera reading
+    (oracle camera_stokes). A unit vector f is placed in the screen deep in the field (the
+    closest approach of an escaping ray, the far end of one that falls in) and carried to the
+    camera. The reading of N = f f^T gives the angle chi = atan2(U, Q) / 2 from the image's x axis
+    toward its y axis. Connors, Piran & Stark (1980) give the same angle at infinity from the
+    Walker-Penrose constant and the image coordinates (alpha, beta) = (x, y):
+        E_alpha = (beta k2 - nu k1) / (beta^2 + nu^2),  E_beta = (beta k1 + nu k2) / (beta^2 + nu^2),
+        nu = -(alpha + a sin(i)),  kappa = k1 + i k2.
+    The camera sits at r = 1e4 M, so the two agree to about M / r. A swapped or flipped image
+    axis, or a wrong sign of Q or U, misses by up to pi/2."""
+    cam = ora.camera(synth.Camera(a=a, incl_deg=incl, r_cam=1.0e4), eps=0.025, nmax=200000)
+    for al, be in ((6.0, 2.0), (-5.0, 3.0), (3.0, -6.0), (0.5, 7.0), (-7.5, -1.0), (12.0, 9.0)):
+        st, status = ora.trace_geodesic(cam, al, be)
+        assert status in (ora.ESCAPE, ora.HORIZON)
+        n0 = int(np.argmin(st[:, 1])) if status == ora.ESCAPE else len(st) - 1
+        f = screen_vector(ora, a, st[n0, :4], st[n0, 4:8], 0.4)
+        fs = ora.transport_vector(a, st[: n0 + 1], f)
+        kap = walker_penrose(a, st[n0, 1], st[n0, 2], -st[n0, 4:8], f)  # forward momentum
+        nu = -(al + a * math.sin(math.radians(incl)))
+        Ea = (be * kap.imag - nu * kap.real) / (be * be + nu * nu)
+        Eb = (be * kap.real + nu * kap.imag) / (be * be + nu * nu)
+        S = ora.camera_stokes(cam, al, be, np.outer(fs[0], fs[0]))
+        assert abs(math.hypot(S[1], S[2]) / S[0] - 1.0) < 1e-9 and abs(S[3]) < 1e-12 * S[0]
+        d = wrap_half_turn(0.5 * math.atan2(S[2], S[1]) - math.atan2(Eb, Ea))
+        assert abs(d) < 2e-3, (al, be, status, d)
