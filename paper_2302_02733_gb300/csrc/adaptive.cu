@@ -90,9 +90,10 @@ __global__ void decide_kernel(T *img, int nc, const uint8_t *st, int nx, int ny,
         if (!active[b]) continue;
         Block k = block_at(b, nbx, s, nx, ny);
         int bi = (int)(b % nbx), bj = (int)(b / nbx), h = s / 2;
-        int c00 = k.j0 * nx + k.i0, c10 = k.j0 * nx + k.i1, c01 = k.j1 * nx + k.i0, c11 = k.j1 * nx + k.i1;
+        // pixel indices fit an int; times nc they need not
+        long long c00 = k.j0 * nx + k.i0, c10 = k.j0 * nx + k.i1, c01 = k.j1 * nx + k.i0, c11 = k.j1 * nx + k.i1;
         bool centre = k.im >= 0 && k.jm >= 0;
-        int cc = centre ? k.jm * nx + k.im : c00;
+        long long cc = centre ? k.jm * nx + k.im : c00;
         bool refine = st && (st[c00] != st[c10] || st[c00] != st[c01] || st[c00] != st[c11] || st[c00] != st[cc]);
         for (int q = 0; q < nc && !refine; q++) {
             double a = img[nc * c00 + q], bb = img[nc * c10 + q], c = img[nc * c01 + q], d = img[nc * c11 + q];
@@ -123,7 +124,7 @@ __global__ void decide_kernel(T *img, int nc, const uint8_t *st, int nx, int ny,
         } else {
             for (int j = k.j0; j <= k.j1; j++)
                 for (int i = k.i0; i <= k.i1; i++) {
-                    int p = j * nx + i;
+                    long long p = j * nx + i;
                     if (atomicCAS(state + p, kUntouched, kFilled) != kUntouched) continue;
                     double fx = (double)(i - k.i0) / (k.i1 - k.i0), fy = (double)(j - k.j0) / (k.j1 - k.j0);
                     for (int q = 0; q < nc; q++) {
