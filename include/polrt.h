@@ -155,6 +155,9 @@ int rt_load_model(rt_ctx *ctx, const rt_model_params *p);
  * field of view, mass or distance that is not positive, or r_cam <= 2 r_h; RT_ERR_SIZE for
  * more than 2^31 - 1 pixels. */
 int rt_set_camera(rt_ctx *ctx, const rt_camera *cam);
+/* The current camera, copied to *cam (which the caller owns); RT_ERR_NOT_READY before the
+ * first rt_set_camera. Callers size their image buffers from it. */
+int rt_get_camera(const rt_ctx *ctx, rt_camera *cam);
 
 /* Geodesic step control: h = eps / (|K^r|/r + |K^th|/max(min(th, pi - th), 0.01) + |K^ph|),
  * classic RK4, at most nmax steps per ray. Defaults: eps = 0.05, nmax = 20000. */

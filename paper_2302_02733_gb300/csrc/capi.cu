@@ -140,6 +140,13 @@ int rt_set_stream(rt_ctx *c, void *stream) {
     return RT_OK;
 }
 
+int rt_get_camera(const rt_ctx *c, rt_camera *cam) {
+    if (!c || !cam) return RT_ERR_INVALID;
+    if (!c->have_cam) return RT_ERR_NOT_READY;
+    *cam = c->cam;
+    return RT_OK;
+}
+
 int rt_set_integrator(rt_ctx *c, double eps, int nmax) {
     if (!c || !(eps > 0.0) || !(eps < 1.0) || nmax < 1) return RT_ERR_INVALID;
     c->eps = eps;

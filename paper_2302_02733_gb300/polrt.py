@@ -1,7 +1,9 @@
 """Thin Python binding of the polrt C ABI (include/polrt.h): argument marshalling only.
 
 Every function keeps the C name. Buffers may be torch tensors (on the GPU or the host) or
-numpy arrays; their data pointers are passed through unchanged. The CUDA library must have
+numpy arrays; their data pointers are passed through unchanged, once the buffer is known to
+hold what the call reads or writes (the C calls take bare pointers; the sizes follow from the
+camera or the row count). The CUDA library must have
 been built in-tree (``paper_2302_02733_gb300.build.build()``). Without it this module raises:
 there is no CPU fallback.
 """
@@ -95,6 +97,7 @@ def lib():
         L.rt_set_stream.argtypes = [_VP, _VP]
         L.rt_load_model.argtypes = [_VP, C.POINTER(rt_model_params)]
         L.rt_set_camera.argtypes = [_VP, C.POINTER(rt_camera)]
+        L.rt_get_camera.argtypes = [_VP, C.POINTER(rt_camera)]
         L.rt_set_integrator.argtypes = [_VP, C.c_double, C.c_int]
         L.rt_set_workspace.argtypes = [_VP, _VP, C.c_size_t]
         L.rt_workspace_min_bytes.restype = C.c_size_t
@@ -156,6 +159,46 @@ def _ptr(buf):
     raise TypeError(f"unsupported buffer type {type(buf)}")
 
 
+def _bytes_of(buf):
+    """(total bytes, bytes per element) of a torch tensor or numpy array."""
+    if hasattr(buf, "element_size"):
+        return buf.numel() * buf.element_size(), buf.element_size()
+    return buf.nbytes, buf.itemsize
+
+
+def _need(buf, count: int, itemsize: int, what: str):
+    """Refuse a buffer (None passes) with elements of another size than itemsize, or fewer
+    than count of them: the library would read or write past its end."""
+    if buf is None:
+        return
+    have, isz = _bytes_of(buf)
+    if isz != itemsize or have < count * itemsize:
+        raise ValueError(f"{what}: needs {count} elements of {itemsize} bytes, has {have // max(isz, 1)} of {isz}")
+
+
+def _image_layout(form: int):
+    """(values per pixel, bytes per value) of an image of this form; None for a form the
+    library rejects itself."""
+    return {RT_FP64: (4, 8), RT_MIXED: (4, 4), RT_SURROGATE: (4, 4), RT_UNPOL: (1, 4)}.get(form)
+
+
+def _check_images(ctx, form: int, out, status=None, depth=None, vis=None, cam=None):
+    """The image-sized buffers of a call on the current camera (or cam) hold one image."""
+    lay = _image_layout(form)
+    if lay is None:
+        return
+    if cam is None:
+        cam = rt_camera()
+        if lib().rt_get_camera(ctx, C.byref(cam)) != RT_OK:
+            return  # no camera yet: the call reports that itself
+    npix = cam.nx * cam.ny
+    ncomp, esz = lay
+    _need(out, npix * ncomp, esz, "image buffer")
+    _need(status, npix, 1, "status buffer")
+    _need(depth, npix * 2, esz, "depth buffer")
+    _need(vis, npix, 2 * esz, "visibility buffer")
+
+
 def rt_create(device: int = 0, stream=None) -> int:
     h = _VP()
     _check(lib().rt_create(C.byref(h), device, stream), "rt_create")
@@ -181,6 +224,12 @@ def rt_set_camera(ctx, cam):
     _check(lib().rt_set_camera(ctx, C.byref(_camera(cam))), "rt_set_camera")
 
 
+def rt_get_camera(ctx) -> rt_camera:
+    cam = rt_camera()
+    _check(lib().rt_get_camera(ctx, C.byref(cam)), "rt_get_camera")
+    return cam
+
+
 def rt_set_integrator(ctx, eps: float = 0.05, nmax: int = 20000):
     _check(lib().rt_set_integrator(ctx, eps, nmax), "rt_set_integrator")
 
@@ -204,6 +253,7 @@ def grid_model(prims, g, kappa: float = 0.0) -> rt_model_params:
     shape = tuple(prims.shape)
     if len(shape) != 4 or shape[3] != 8:
         raise ValueError("prims must be [n1][n2][n3][8]")
+    _need(prims, shape[0] * shape[1] * shape[2] * 8, 4, "prims (float32)")
     m = rt_model_params()
     m.kind = RT_MODEL_GRID
     m.grid = rt_grid_params(shape[0], shape[1], shape[2], g.r_in, g.r_out, g.hslope, g.poly_xt, g.poly_alpha,
@@ -216,8 +266,11 @@ def rt_set_workspace(ctx, buf, nbytes: int | None = None):
     if buf is None:
         _check(lib().rt_set_workspace(ctx, None, 0), "rt_set_workspace")
         return
+    have = _bytes_of(buf)[0]
     if nbytes is None:
-        nbytes = buf.numel() * buf.element_size() if hasattr(buf, "numel") else buf.nbytes
+        nbytes = have
+    elif nbytes > have:
+        raise ValueError(f"workspace: {nbytes} bytes declared, buffer holds {have}")
     _check(lib().rt_set_workspace(ctx, _ptr(buf), nbytes), "rt_set_workspace")
 
 
@@ -232,6 +285,7 @@ def rt_workspace_hint(ctx) -> int:
 
 
 def rt_render(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
+    _check_images(ctx, form, out_iquv, status)
     rc = lib().rt_render(ctx, form, _ptr(out_iquv), _ptr(status))
     if check:
         _check(rc, "rt_render")
@@ -240,6 +294,7 @@ def rt_render(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
 
 def rt_render_depths(ctx, form: int, out_iquv, out_depth, status=None, check: bool = True) -> int:
     """rt_render plus the per-pixel optical and Faraday depths [ny][nx][2]."""
+    _check_images(ctx, form, out_iquv, status, out_depth)
     rc = lib().rt_render_depths(ctx, form, _ptr(out_iquv), _ptr(status), _ptr(out_depth))
     if check:
         _check(rc, "rt_render_depths")
@@ -248,6 +303,9 @@ def rt_render_depths(ctx, form: int, out_iquv, out_depth, status=None, check: bo
 
 def rt_kappa_coeffs(ctx, inp, out):
     """inp: [n, 6] float64 (ne, Theta_e, B, nu, theta_B, kappa); out: [n, 8] float64."""
+    n = int(inp.shape[0])
+    _need(inp, 6 * n, 8, "inp")
+    _need(out, 8 * n, 8, "out")
     _check(lib().rt_kappa_coeffs(ctx, _ptr(inp), int(inp.shape[0]), _ptr(out)), "rt_kappa_coeffs")
 
 
@@ -262,36 +320,57 @@ def mlp_norm(lo, hi, y_mean=None, y_std=None) -> rt_mlp_norm:
 
 
 def rt_mlp_set_params(ctx, theta, norm: rt_mlp_norm):
+    _need(theta, RT_MLP_PARAMS, 4, "theta")
     _check(lib().rt_mlp_set_params(ctx, _ptr(theta), C.byref(norm)), "rt_mlp_set_params")
 
 
 def rt_mlp_get_params(ctx, theta=None) -> rt_mlp_norm:
     n = rt_mlp_norm()
+    _need(theta, RT_MLP_PARAMS, 4, "theta")
     _check(lib().rt_mlp_get_params(ctx, _ptr(theta), C.byref(n)), "rt_mlp_get_params")
     return n
 
 
 def rt_mlp_forward(ctx, x, y):
+    n = int(x.shape[0])
+    _need(x, 4 * n, 4, "x")
+    _need(y, 8 * n, 4, "y")
     _check(lib().rt_mlp_forward(ctx, _ptr(x), int(x.shape[0]), _ptr(y)), "rt_mlp_forward")
 
 
 def rt_mlp_grad(ctx, x, t, grad) -> float:
+    n = int(x.shape[0])
+    _need(x, 4 * n, 4, "x")
+    _need(t, 8 * n, 4, "t")
+    _need(grad, RT_MLP_PARAMS, 4, "grad")
     loss = C.c_float(0)
     _check(lib().rt_mlp_grad(ctx, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grad), C.byref(loss)), "rt_mlp_grad")
     return loss.value
 
 
 def rt_mlp_train(ctx, x, t, steps: int, batch: int, lr: float, seed: int, loss_curve=None):
+    n = int(x.shape[0])
+    _need(x, 4 * n, 4, "x")
+    _need(t, 8 * n, 4, "t")
+    _need(loss_curve, steps, 4, "loss_curve")
     _check(lib().rt_mlp_train(ctx, _ptr(x), _ptr(t), int(x.shape[0]), steps, batch, lr, seed, _ptr(loss_curve)),
            "rt_mlp_train")
 
 
 def rt_surrogate_dataset(ctx, box, n: int, seed: int, x, y, valid):
+    _need(x, 4 * n, 4, "x")
+    _need(y, 8 * n, 4, "y")
+    _need(valid, n, 4, "valid (int32)")
     b = (C.c_float * 8)(*[float(v) for v in box])
     _check(lib().rt_surrogate_dataset(ctx, b, n, seed, _ptr(x), _ptr(y), _ptr(valid)), "rt_surrogate_dataset")
 
 
 def rt_surrogate_fit(ctx, x, y, valid, t, lo, hi) -> rt_mlp_norm:
+    n = int(x.shape[0])
+    _need(x, 4 * n, 4, "x")
+    _need(y, 8 * n, 4, "y")
+    _need(valid, n, 4, "valid (int32)")
+    _need(t, 8 * n, 4, "t")
     """Baseline fit and standardised residual targets; returns the filled rt_mlp_norm."""
     n = mlp_norm(lo, hi)
     _check(lib().rt_surrogate_fit(ctx, _ptr(x), _ptr(y), _ptr(valid), int(x.shape[0]), _ptr(t), C.byref(n)),
@@ -301,6 +380,7 @@ def rt_surrogate_fit(ctx, x, y, valid, t, lo, hi) -> rt_mlp_norm:
 
 def rt_render_adaptive(ctx, form: int, out, status=None, base_step: int = 8, tol: float = 1e-3) -> int:
     """Adaptive render into device buffers; returns the number of rays traced."""
+    _check_images(ctx, form, out, status)
     n = C.c_longlong(0)
     _check(lib().rt_render_adaptive(ctx, form, _ptr(out), _ptr(status), base_step, tol, C.byref(n)),
            "rt_render_adaptive")
@@ -309,17 +389,23 @@ def rt_render_adaptive(ctx, form: int, out, status=None, base_step: int = 8, tol
 
 def rt_image_visibilities(ctx, img, form: int, stokes: int, vis):
     """vis: complex buffer [ny][nx] (complex128 for RT_FP64, complex64 otherwise)."""
+    _check_images(ctx, form, img, vis=vis)
     _check(lib().rt_image_visibilities(ctx, _ptr(img), form, stokes, _ptr(vis)), "rt_image_visibilities")
 
 
 def rt_render_features(ctx, feat) -> int:
     """feat: device float32 [cap, 4]; returns the number of emitting points."""
+    _need(feat, 4 * int(feat.shape[0]), 4, "feat")
     n = C.c_longlong(0)
     _check(lib().rt_render_features(ctx, _ptr(feat), int(feat.shape[0]), C.byref(n)), "rt_render_features")
     return n.value
 
 
 def rt_surrogate_coeffs(ctx, inp, out, inside=None):
+    n = int(inp.shape[0])
+    _need(inp, 6 * n, 8, "inp")
+    _need(out, 8 * n, 8, "out")
+    _need(inside, n, 1, "inside")
     _check(lib().rt_surrogate_coeffs(ctx, _ptr(inp), int(inp.shape[0]), _ptr(out), _ptr(inside)),
            "rt_surrogate_coeffs")
 
@@ -329,6 +415,7 @@ def make_jobs(items) -> C.Array:
     rt_set_camera, buffers device tensors (status and out_depth may be None)."""
     items = list(items)
     arr = (rt_job * len(items))()
+    arr._buffers = [it[3:] for it in items]  # kept alive with the pointers; sizes checked per form
     for j, (cam, mu, rh, out, st, dep) in zip(arr, items):
         j.cam = _camera(cam)
         j.M_unit = mu
@@ -339,8 +426,15 @@ def make_jobs(items) -> C.Array:
     return arr
 
 
+def _check_jobs(ctx, form: int, jobs):
+    """Every job's buffers (recorded by make_jobs) hold one image of its camera."""
+    for j, (out, st, dep) in zip(jobs, getattr(jobs, "_buffers", ())):
+        _check_images(ctx, form, out, st, dep, cam=j.cam)
+
+
 def rt_render_batch(ctx, form: int, jobs, check: bool = True) -> int:
     """Render every job of an rt_job array (see make_jobs) in one persistent launch."""
+    _check_jobs(ctx, form, jobs)
     rc = lib().rt_render_batch(ctx, form, jobs, len(jobs))
     if check:
         _check(rc, "rt_render_batch")
@@ -348,6 +442,7 @@ def rt_render_batch(ctx, form: int, jobs, check: bool = True) -> int:
 
 
 def rt_batch_autotune(ctx, form: int, jobs) -> dict:
+    _check_jobs(ctx, form, jobs)
     b = rt_batch_config()
     _check(lib().rt_batch_autotune(ctx, form, jobs, len(jobs), C.byref(b)), "rt_batch_autotune")
     return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
@@ -377,6 +472,7 @@ def rt_get_render_config(ctx) -> dict:
 
 def rt_render_static(ctx, form: int, out_iquv, status=None, check: bool = True) -> int:
     """rt_render with the scratch in the library's static device array (no allocation)."""
+    _check_images(ctx, form, out_iquv, status)
     rc = lib().rt_render_static(ctx, form, _ptr(out_iquv), _ptr(status))
     if check:
         _check(rc, "rt_render_static")
@@ -388,6 +484,7 @@ def rt_render_static_max_pixels() -> int:
 
 
 def rt_image_stats(ctx, iquv, form: int):
+    _check_images(ctx, form, iquv)
     f, lp, cp = C.c_double(0), C.c_double(0), C.c_double(0)
     _check(lib().rt_image_stats(ctx, _ptr(iquv), form, C.byref(f), C.byref(lp), C.byref(cp)), "rt_image_stats")
     return f.value, lp.value, cp.value
