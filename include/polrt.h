@@ -22,6 +22,12 @@
  *     rt_destroy.
  *   - Units: geometry in M = GM/c^2 (G = c = 1); intensities in cgs
  *     (erg s^-1 cm^-2 Hz^-1 sr^-1); flux in Jy.
+ *   - A context is not thread safe: it holds the camera, the model, the workspace and the
+ *     pinned counters of its last call. Threads that share one must serialize their calls.
+ *     Separate contexts, on one device or several, are independent, except for
+ *     rt_render_static's shared array.
+ *   - A rejected call (RT_ERR_INVALID, RT_ERR_NOT_READY, RT_ERR_SIZE) leaves the context as
+ *     it was.
  */
 #ifndef POLRT_H
 #define POLRT_H
