@@ -910,7 +910,6 @@ static pix_out transfer(const ora_camera *cam, const ora_model *m, const double 
         double g[16];
         ora_metric_ks(a, sn[1], sn[2], g);
         const double *K = sn + 4, *u = pl + 4, *b = pl + 8;
-        double k[4] = {-K[0], -K[1], -K[2], -K[3]};
         double w = dot4(g, K, u); /* = -k.u = nu_fluid / nu_obs */
         double e0[4], e1[4], e2[4], e3[4];
         double thB = fluid_tetrad(g, K, u, b, e0, e1, e2, e3);
