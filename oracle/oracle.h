@@ -15,10 +15,15 @@
  * The paper leaves every formula to its method paper, which is not available here. Each
  * function states the reading it implements. Every reading is listed in the design notes.
  *
- * Parity unpinned: the Shcherbakov correction functions of the rotativities away from their
- * X -> 0 limit, a transcription of a published fit that nothing in this repository pins
- * independently. The absolute flux scale follows from the model constants. (The emissivities,
- * j_V included, are pinned by the exact sum over cyclotron harmonics.)
+ * Parity unpinned:
+ *  - the Shcherbakov correction functions of the rotativities away from their X -> 0 limit,
+ *    a transcription of a published fit that nothing in this repository pins independently;
+ *  - the kappa rotativities (kappa.c), a reading that is exact for Maxwell-Juttner electrons
+ *    only;
+ *  - the depth maps' normalisation: sums of the exponents of the pinned constant-coefficient
+ *    step, which converge with the step, but no closed form fixes a pixel's value;
+ *  - the absolute flux scale, which follows from the model constants.
+ * The emissivities, j_V included, are pinned by the exact sum over cyclotron harmonics.
  */
 #ifndef PR_ORACLE_H
 #define PR_ORACLE_H
