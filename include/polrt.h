@@ -178,7 +178,8 @@ size_t rt_workspace_min_bytes(void);
 int rt_workspace_hint(const rt_ctx *ctx, size_t *bytes);
 
 /* Render the IQUV image: out_iquv holds nx*ny*4 values, row-major [iy][ix][I,Q,U,V]
- * (double for RT_FP64, float for RT_MIXED), host or device. Row iy = 0 is the bottom
+ * (double for RT_FP64, float for RT_MIXED and RT_SURROGATE; RT_UNPOL writes nx*ny floats of
+ * I alone), host or device. Row iy = 0 is the bottom
  * (image y = -FOV/2); x runs along +e_phi and y along -e_theta of the camera. Stokes Q is
  * positive for E along x, and V > 0 for right-handed light in the IEEE/IAU sense. status:
  * optional nx*ny uint8 per-pixel codes (host or device), or NULL. The rays are processed in
