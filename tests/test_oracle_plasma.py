@@ -144,3 +144,37 @@ def test_adaf_plasma(ora, synth):
         assert np.isclose(pl[1], KB * Te / (ME * C * C), rtol=1e-13)
         assert np.isclose(pl[2] ** 2 / (8 * np.pi), pl[0] * KB * Te * (1 + p.Ti_over_Te) / p.beta, rtol=1e-12)
     assert ora.plasma(cam, m, np.array([0.0, 1001.0, 1.0, 0.0]))[3] == 0.0
+
+
+@pytest.mark.parametrize("scale,r,th", [(1.0, 7.0, 1.1), (0.3, 18.0, 2.3)])
+def test_grid_field_and_temperature_by_hand(ora, synth, scale, r, th):
+    """A static fluid (U = 0) in a uniform FMKS field, worked by hand at one point.
+    - The field's KS components follow from the FMKS Jacobian: B^r = r B^1,
+      B^theta = (dtheta/dX1) B^1 + (dtheta/dX2) B^2, B^phi = B^3.
+    - For the normal observer (u_i = 0), b^t = 0 and b^i = alpha B^i.
+    - B = |b| c sqrt(4 pi rho_unit).
+    - beta = 2 (gamma - 1) u / b^2, so R = R_high beta^2/(1 + beta^2) + R_low/(1 + beta^2).
+    - Theta_e = (m_p/m_e)(gamma - 1) u / (rho (1 + R)).
+    The two cases put beta on either side of one, where both terms of R count."""
+    g = synth.GridParams(n1=8, n2=8, n3=4, M_unit=3e18, R_high=20.0).resolved()
+    vals = np.array([2.0, 0.05, 0.0, 0.0, 0.0, 0.012 * scale, 0.02 * scale, 0.03 * scale], dtype=np.float32)
+    m = ora.grid_model(np.broadcast_to(vals, (8, 8, 4, 8)).copy(), g)
+    cam = ora.camera(synth.Camera())
+    pl = ora.plasma(cam, m, np.array([0.0, r, th, 0.4]))
+    assert pl[3] == 1.0
+    v = vals.astype(np.float64)
+    X1 = np.log(r)
+    th_back, d1, d2 = ora.fmks_theta(m, X1, ora.fmks_x2(m, X1, th))
+    assert abs(th_back - th) < 1e-12
+    gm = ora.metric(cam.a, r, th)
+    alpha = 1.0 / np.sqrt(-np.linalg.inv(gm)[0, 0])
+    b = alpha * np.array([0.0, r * v[5], d1 * v[5] + d2 * v[6], v[7]])
+    b2 = b @ gm @ b
+    MP, ME, G, C = 1.67262192369e-24, 9.1093837015e-28, 6.67430e-8, 2.99792458e10
+    L = G * cam.M_bh_g / C ** 2
+    beta = 2.0 * (g.gamma_ad - 1.0) * v[1] / b2
+    R = g.R_high * beta ** 2 / (1 + beta ** 2) + g.R_low / (1 + beta ** 2)
+    assert 0.2 < beta < 5.0 and 1.5 < R < 19.0
+    assert np.allclose(pl[8:12], b, rtol=1e-12, atol=1e-15)
+    assert np.isclose(pl[2], np.sqrt(b2) * C * np.sqrt(4 * np.pi * g.M_unit / L ** 3), rtol=1e-12)
+    assert np.isclose(pl[1], MP / ME * (g.gamma_ad - 1) * v[1] / (v[0] * (1 + R)), rtol=1e-12)
