@@ -139,6 +139,8 @@ def test_adaf_plasma(ora, synth):
         assert np.isclose(ul[0], -1.0, rtol=1e-10)
         assert np.isclose(ul[3], p.f_kep * lK * np.sin(th) ** 2, rtol=1e-9, atol=1e-12)
         assert u[1] < 0   # inflow
+        # the field has no theta component (B^i along (1, 0, 1/r)) and u^theta = 0, so b^theta = 0
+        assert u[2] == 0.0 and abs(b[2]) <= 1e-14 * np.abs(b).max()
         assert np.isclose(pl[0], p.n0 * r ** -1.5, rtol=1e-13)
         Te = p.T0 / r
         assert np.isclose(pl[1], KB * Te / (ME * C * C), rtol=1e-13)
