@@ -18,7 +18,7 @@ _SO = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 HORIZON, ESCAPE, NMAX, NAN = 1, 2, 3, 4
-MODEL_ADAF, MODEL_GRID = 1, 2
+MODEL_ADAF, MODEL_GRID, MODEL_SPHERE = 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -48,7 +48,9 @@ class Model(C.Structure):
                 ("prims", C.POINTER(C.c_float)),
                 ("M_unit", C.c_double), ("R_high", C.c_double), ("R_low", C.c_double),
                 ("sigma_cut", C.c_double), ("gamma_ad", C.c_double),
-                ("edf", C.c_int), ("kappa", C.c_double), ("unpol_test", C.c_int)]
+                ("edf", C.c_int), ("kappa", C.c_double), ("unpol_test", C.c_int),
+                ("sph_R", C.c_double), ("sph_ne", C.c_double), ("sph_Te", C.c_double), ("sph_B", C.c_double),
+                ("sph_smooth", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -138,6 +140,16 @@ def grid_model(prims: np.ndarray, g, kappa: float = 0.0) -> ModelHandle:
     m.M_unit, m.R_high, m.R_low, m.sigma_cut, m.gamma_ad = g.M_unit, g.R_high, g.R_low, g.sigma_cut, g.gamma_ad
     m.edf, m.kappa = (EDF_KAPPA, kappa) if kappa > 3.0 else (EDF_THERMAL, 0.0)
     return ModelHandle(m, prims)
+
+
+def sphere_model(R: float, ne: float, Te: float, B: float, smooth: bool = False) -> ModelHandle:
+    """A static sphere (Theta_e and B [G] constant for r < R; n_e [cm^-3] constant, or with
+    smooth=True ne (1 - r^2/R^2)^2; fluid at rest, field along d_phi): a test model whose image
+    has a closed form, not a model of the paper."""
+    m = Model()
+    m.kind = MODEL_SPHERE
+    m.sph_R, m.sph_ne, m.sph_Te, m.sph_B, m.sph_smooth = R, ne, Te, B, int(smooth)
+    return ModelHandle(m)
 
 
 def render_pixels(cam: Camera, model: ModelHandle, ix, iy, pert: int = 0, nthreads: int = 0,

@@ -498,9 +498,40 @@ static void grid_plasma(const ora_camera *cam, const ora_model *m, const double 
     }
 }
 
+/* Static sphere, for the pins of the camera-to-flux chain and of the depth maps: a model whose
+ * image has a closed form (it is not one of the paper's models). Inside r < R the temperature
+ * and field strength are constant and the density is constant or, with sph_smooth, falls as
+ * (1 - r^2/R^2)^2 to zero at the surface (so that sums along a ray converge without an edge
+ * term); the fluid is at rest, u = d_t / |d_t| (outside the ergoregion), and the field
+ * direction is d_phi made normal to u. */
+static void sphere_plasma(const ora_camera *cam, const ora_model *m, const double x[4], double out[12]) {
+    memset(out, 0, 12 * sizeof(double));
+    if (!(x[1] < m->sph_R)) return;
+    double g[16];
+    ora_metric_ks(cam->a, x[1], x[2], g);
+    if (!(g[0] < 0.0)) return;
+    double u[4] = {1.0 / sqrt(-g[0]), 0.0, 0.0, 0.0};
+    double ph[4] = {0.0, 0.0, 0.0, 1.0};
+    double pu = dot4(g, ph, u);
+    double b[4];
+    for (int i = 0; i < 4; i++) b[i] = ph[i] + pu * u[i];
+    double nb = sqrt(dot4(g, b, b));
+    double q = 1.0 - x[1] * x[1] / (m->sph_R * m->sph_R);
+    out[0] = m->sph_smooth ? m->sph_ne * q * q : m->sph_ne;
+    out[1] = m->sph_Te;
+    out[2] = m->sph_B;
+    out[3] = 1.0;
+    for (int i = 0; i < 4; i++) {
+        out[4 + i] = u[i];
+        out[8 + i] = b[i] / nb;
+    }
+}
+
 void ora_plasma(const ora_camera *cam, const ora_model *m, const double x[4], double out[12]) {
     if (m->kind == ORA_MODEL_ADAF)
         adaf_plasma(cam, m, x, out);
+    else if (m->kind == ORA_MODEL_SPHERE)
+        sphere_plasma(cam, m, x, out);
     else
         grid_plasma(cam, m, x, out);
 }

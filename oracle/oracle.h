@@ -15,15 +15,16 @@
  * The paper leaves every formula to its method paper, which is not available here. Each
  * function states the reading it implements. Every reading is listed in the design notes.
  *
- * Parity unpinned:
- *  - the Shcherbakov correction functions of the rotativities away from their X -> 0 limit,
- *    a transcription of a published fit that nothing in this repository pins independently;
- *  - the kappa rotativities (kappa.c), a reading that is exact for Maxwell-Juttner electrons
- *    only;
- *  - the depth maps' normalisation: sums of the exponents of the pinned constant-coefficient
- *    step, which converge with the step, but no closed form fixes a pixel's value;
- *  - the absolute flux scale, which follows from the model constants.
- * The emissivities, j_V included, are pinned by the exact sum over cyclotron harmonics.
+ * Parity unpinned (the values below follow from published model constants or from a reading,
+ * and nothing independent fixes them; every other function has a pin in tests/):
+ *  - the middle range of the Shcherbakov correction functions of the rotativities: the fit is
+ *    pinned at X -> 0 (cold-plasma rates) and at large X (its closed-form X^(-8/3) asymptote),
+ *    and between them it is the transcription of a published fit;
+ *  - the kappa rotativities (kappa.c) as a reading: their distribution averages are pinned by an
+ *    independent quadrature, but the reading itself is exact for Maxwell-Juttner electrons only;
+ *  - the absolute flux scale of the ADAF and grid models, which follows from the model constants.
+ * The emissivities, j_V included, are pinned by the exact sum over cyclotron harmonics; the
+ * camera-to-flux chain and the depth maps by the closed-form image of a static sphere.
  */
 #ifndef PR_ORACLE_H
 #define PR_ORACLE_H
@@ -32,7 +33,7 @@ extern "C" {
 #endif
 
 enum { ORA_HORIZON = 1, ORA_ESCAPE = 2, ORA_NMAX = 3, ORA_NAN = 4 };
-enum { ORA_MODEL_ADAF = 1, ORA_MODEL_GRID = 2 };
+enum { ORA_MODEL_ADAF = 1, ORA_MODEL_GRID = 2, ORA_MODEL_SPHERE = 3 };
 enum { ORA_EDF_THERMAL = 0, ORA_EDF_KAPPA = 1 };
 
 typedef struct {
@@ -57,6 +58,11 @@ typedef struct {
     double kappa;
     /* test switch: keep only j_I and a_I in the polarized transfer (for the unpolarized pin) */
     int unpol_test;
+    /* static sphere (a pin with a closed-form image, not a model of the paper): Theta_e and B
+     * constant for r < sph_R, n_e constant (sph_smooth 0) or sph_ne (1 - r^2/R^2)^2
+     * (sph_smooth 1), fluid at rest (u along d_t), field along d_phi */
+    double sph_R, sph_ne, sph_Te, sph_B;
+    int sph_smooth;
 } ora_model;
 
 /* geometry */

@@ -106,3 +106,45 @@ def test_light_cone_bound(ora):
         if c[0] > 0:
             assert np.hypot(c[1] / c[0], c[2] / c[0]) <= 1 + 1e-12
             assert np.hypot(c[4] / c[3], c[5] / c[3]) <= 1 + 1e-12
+
+
+def _conversion_factor(ora, Te, nu, th=1.0, ne=1e5, B=100.0):
+    """rho_Q / (rho_Q of cold electrons x (K1/K2 + 6 Theta)): the oracle's Shcherbakov factor
+    f(X) read through the whole coefficient, with the cold-plasma rate written as
+    w_p^2 w_B^2 sin^2 / (2 c w^3) and the Bessel ratio from scipy."""
+    c = ora.thermal_coeffs(ne, Te, B, nu, th)
+    wp2 = 4 * np.pi * ne * QE ** 2 / ME
+    wB = QE * B / (ME * C)
+    rq = wp2 * wB ** 2 * np.sin(th) ** 2 / (2 * C * (2 * np.pi * nu) ** 3)
+    z = 1.0 / Te
+    X = Te * np.sqrt(np.sqrt(2.0) * np.sin(th) * 1e3 * (QE * B / (2 * np.pi * ME * C)) / nu)
+    return c[6] / (rq * (special.kve(1, z) / special.kve(2, z) + 6 * Te)), X
+
+
+def test_conversion_correction_large_X_asymptote(ora):
+    """Far above the switch at X = 120 the published correction falls as
+    -2^(-1/3) 3^(-23/6) 1e4 pi X^(-8/3): the exponential terms have died, the two 0.011 e^(-X/47.2)
+    terms cancel and the tanh switch is fully on. A wrong sign in the switch, a dropped
+    cancellation or a wrong power would show here."""
+    C83 = 2.0 ** (-1.0 / 3.0) * 3.0 ** (-23.0 / 6.0) * 1e4 * np.pi
+    for X_target in (1e3, 4e3, 2e4):
+        Te = 50.0
+        nuB = QE * 100.0 / (2 * np.pi * ME * C)
+        nu = np.sqrt(2.0) * np.sin(1.0) * 1e3 * nuB * (Te / X_target) ** 2
+        f, X = _conversion_factor(ora, Te, nu)
+        assert abs(X / X_target - 1) < 1e-12
+        assert abs(f / (-C83 * X ** (-8.0 / 3.0)) - 1) < 1e-9, (X, f, -C83 * X ** (-8.0 / 3.0))
+
+
+def test_conversion_correction_small_X_and_switch(ora):
+    """f -> 1 as X -> 0 (the high-frequency limit that the cold-plasma pin fixes at finite
+    temperature), and f is continuous through the switch around X = 120 (no step larger than the
+    fit's own variation over the grid)."""
+    Te = 50.0
+    nuB = QE * 100.0 / (2 * np.pi * ME * C)
+    f0, X0 = _conversion_factor(ora, Te, np.sqrt(2.0) * np.sin(1.0) * 1e3 * nuB * (Te / 1e-6) ** 2)
+    assert X0 < 2e-6 and abs(f0 - 1) < 1e-5
+    xs = np.linspace(60.0, 240.0, 721)
+    fs = np.array([_conversion_factor(ora, Te, np.sqrt(2.0) * np.sin(1.0) * 1e3 * nuB * (Te / x) ** 2)[0] for x in xs])
+    d = np.abs(np.diff(fs))
+    assert d.max() < 10 * np.median(d), (d.max(), np.median(d))

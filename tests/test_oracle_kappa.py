@@ -112,3 +112,60 @@ def test_light_cone_and_circular_parity(ora):
         # theta -> pi - theta flips the circular terms and keeps the rest
         sign = np.array([1, 1, -1, 1, 1, -1, 1, -1])
         assert np.allclose(b, sign * a, rtol=1e-9, atol=0), (a, b)
+
+
+def _kappa_average(kernel, Te, kappa):
+    """<kernel(g)> over the kappa distribution N ~ g p (1 + (g - 1)/(kappa w))^-(kappa+1),
+    w = (kappa - 3) Theta / kappa, by scipy's adaptive quadrature over s = ln p on fixed
+    breakpoints (not the oracle's Gauss-Legendre rule); the heaviest tail, kappa = 3.5 with the
+    kernel 2 g, falls only as e^(-s/2), so the range runs to s = 90."""
+    kw = (kappa - 3.0) * Te
+
+    def weight(s):
+        p = math.exp(s)
+        g = math.sqrt(1.0 + p * p)
+        return g * p * (1.0 + p * p / (g + 1.0) / kw) ** -(kappa + 1.0) * p * p / g, g, p
+
+    def num_f(s):
+        w, g, p = weight(s)
+        return w * kernel(g, p)
+
+    pts = [-14.0, -4.0, -1.0, 0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 8.0, 11.0, 15.0, 20.0, 30.0, 45.0, 60.0, 90.0]
+    num = den = 0.0
+    for a, b in zip(pts, pts[1:]):
+        num += integrate.quad(num_f, a, b, limit=200, epsabs=0, epsrel=1e-13)[0]
+        den += integrate.quad(lambda s: weight(s)[0], a, b, limit=200, epsabs=0, epsrel=1e-13)[0]
+    return num / den
+
+
+@pytest.mark.parametrize("kappa", [3.5, 4.5, 8.0])
+@pytest.mark.parametrize("Te", [0.3, 3.0, 30.0])
+def test_kappa_rotativities_are_the_distribution_averages(ora, kappa, Te):
+    """The kappa rotativities are the thermal ones with the Bessel ratios K0/K2 and
+    K1/K2 + 6 Theta replaced by the averages of asinh(p)/(g p) and 2 g - 1/g over the kappa
+    distribution (the same Shcherbakov corrections at the same X multiply both, so they cancel
+    in the ratio). The averages are taken here by an independent quadrature; a wrong w, a wrong
+    normalisation or a wrong kernel in the oracle's rule would show."""
+    th, nu = 0.9, 230e9
+    q = ora.kappa_coeffs(1e6, Te, 30.0, nu, th, kappa)
+    f = ora.thermal_coeffs(1e6, Te, 30.0, nu, th)
+    z = 1.0 / Te
+    k0, k1, k2 = special.kve(0, z), special.kve(1, z), special.kve(2, z)
+    aV = _kappa_average(lambda g, p: math.asinh(p) / (g * p), Te, kappa)
+    aQ = _kappa_average(lambda g, p: 2.0 * g - 1.0 / g, Te, kappa)
+    assert abs((q[7] / f[7]) / (aV / (k0 / k2)) - 1) < 1e-8, (q[7] / f[7], aV / (k0 / k2))
+    assert abs((q[6] / f[6]) / (aQ / (k1 / k2 + 6.0 * Te)) - 1) < 1e-8, (q[6] / f[6], aQ / (k1 / k2 + 6.0 * Te))
+
+
+def test_kappa_mean_energy_closed_form(ora):
+    """Ultrarelativistic kappa electrons have <g> = kappa w 3/(kappa - 3) = 3 Theta (Beta-function
+    integrals of g^2 (1 + g/(kappa w))^-(kappa+1)), so the Faraday-conversion average
+    <2 g - 1/g> tends to 6 Theta, as for thermal electrons (up to terms of order 1/Theta)."""
+    for kappa in (4.0, 6.0):
+        Te = 3000.0
+        q = ora.kappa_coeffs(1e6, Te, 30.0, 230e9, 0.9, kappa)
+        f = ora.thermal_coeffs(1e6, Te, 30.0, 230e9, 0.9)
+        z = 1.0 / Te
+        ratio_mj = special.kve(1, z) / special.kve(2, z) + 6.0 * Te
+        avg = (q[6] / f[6]) * ratio_mj
+        assert abs(avg / (6.0 * Te) - 1) < 1e-3, (kappa, avg / (6 * Te))
