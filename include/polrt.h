@@ -390,7 +390,10 @@ int rt_get_batch_config(rt_ctx *ctx, int form, rt_batch_config *cfg);
  * library holds until the process exits. The whole image is one chunk, so nx*ny must not
  * exceed rt_render_static_max_pixels() (13076 pixels, e.g. 114x114): larger images return
  * RT_ERR_SIZE. out_iquv (and status, if given) must be device memory, else RT_ERR_INVALID.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * It renders the forms RT_FP64 and RT_MIXED (thermal or kappa electrons by quadrature); the
+ * other forms (RT_UNPOL, RT_SURROGATE, whose network scratch it does not hold) return
+ * RT_ERR_INVALID. It runs one pass of each kernel, at the blocks per SM that
+ * rt_set_render_config sets (its chunk count does not apply). The first call on a device looks up the array's device address (cudaGetSymbolAddress),
  * so make that first call before any stream capture. Every call shares the one array and
  * clears its counters first; calls that overlap on the GPU (on different streams or from
  * several threads) race on it and must be serialized by the caller. Synchronizes the

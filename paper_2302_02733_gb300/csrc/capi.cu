@@ -15,8 +15,6 @@ using namespace prt;
 
 namespace {
 constexpr size_t kAlign = 256;
-constexpr size_t kBlockBytes = sizeof(PathState) * kBlockStates + sizeof(int);
-constexpr int kBudgetBlocksPerRay = 20;  // 640 saved states per ray on average per chunk
 constexpr size_t kPerRayBytes = sizeof(RayRecord) + kBudgetBlocksPerRay * kBlockBytes;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }

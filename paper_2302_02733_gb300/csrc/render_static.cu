@@ -20,8 +20,7 @@ namespace {
 
 constexpr size_t kStaticBytes = 512ull << 20;  // 512 MiB of scratch per device
 constexpr size_t kStaticAlign = 256;
-constexpr size_t kStaticBlockBytes = sizeof(PathState) * kBlockStates + sizeof(int);
-constexpr size_t kStaticPerRay = sizeof(RayRecord) + 20 * kStaticBlockBytes;  // 640 states per ray
+constexpr size_t kStaticPerRay = sizeof(RayRecord) + kBudgetBlocksPerRay * kBlockBytes;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -71,7 +70,7 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     size_t off = up(sizeof(Counters));
     RayRecord *rec = (RayRecord *)(base + off);
     off = up(off + sizeof(RayRecord) * (size_t)nrays);
-    long long nblocks = (long long)((kStaticBytes - off - kStaticAlign) / kStaticBlockBytes);
+    long long nblocks = (long long)((kStaticBytes - off - kStaticAlign) / kBlockBytes);
     Arena ar;
     ar.states = (PathState *)(base + off);
     ar.prev = (int *)(base + off + (size_t)nblocks * sizeof(PathState) * kBlockStates);
@@ -85,14 +84,18 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, nrays, 0};
     XferArgs xa{cam, mod, ar, rec, ctr, nrays, 0, out_iquv, status, nullptr};
     cudaEventRecord(c->ev[0], c->stream);
-    launch_geodesic(ga, c->nsm * c->geo_bps, c->stream);
+    // the launch shape of rt_set_render_config (blocks per SM), as rt_render's one-pass shape
+    const int geo_b = c->rcfg.geo_blocks_per_sm > 0 ? c->rcfg.geo_blocks_per_sm : c->geo_bps;
+    const int xf_max = form == RT_FP64 ? c->fp64_bps : c->mixed_bps;
+    const int xf_b = c->rcfg.xfer_blocks_per_sm > 0 ? std::min(c->rcfg.xfer_blocks_per_sm, xf_max) : xf_max;
+    launch_geodesic(ga, c->nsm * geo_b, c->stream);
     cudaEventRecord(c->ev[1], c->stream);
     xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
     const int coef = mod.edf == RT_EDF_KAPPA ? 1 : 0;
     if (form == RT_FP64)
-        launch_transfer_fp64(xa, coef, c->nsm * c->fp64_bps, c->stream);
+        launch_transfer_fp64(xa, coef, c->nsm * xf_b, c->stream);
     else
-        launch_transfer_mixed(xa, coef, c->nsm * c->mixed_bps, c->stream);
+        launch_transfer_mixed(xa, coef, c->nsm * xf_b, c->stream);
     cudaEventRecord(c->ev[2], c->stream);
     if (cudaGetLastError() != cudaSuccess) return RT_ERR_CUDA;
     if (cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -103,6 +106,8 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     c->last_rays = nrays;
     c->last_blocks_total = nblocks;
     c->last_was_batch = false;
+    c->last_was_overlap = false;  // one pass of each kernel: the counters report this call
+    c->last_chunks = 1;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     return RT_OK;
 }

@@ -27,6 +27,10 @@ struct __align__(16) PathState {
 // Each block records the block that precedes it on the same ray, so the transfer can walk
 // a ray's states backward.
 constexpr int kBlockStates = 32;
+// Bytes of one arena block (states plus its back link), and the arena budget per ray: 20 blocks,
+// 640 saved states per ray on average over a chunk (the mean is about 300).
+constexpr size_t kBlockBytes = sizeof(PathState) * kBlockStates + sizeof(int);
+constexpr int kBudgetBlocksPerRay = 20;
 
 struct Camera {
     double a, r_cam, theta_o, nu_obs, fov, L_unit;

@@ -56,3 +56,12 @@ def test_create_without_gpu_reports_an_error():
 
     with pytest.raises(polrt.PolrtError):
         polrt.rt_create(0, None)
+
+
+def test_static_render_limit_matches_the_documented_figure(lib):
+    """rt_render_static's pixel limit is derived from the same arena constants as rt_render's
+    workspace; the header and the design notes state 13076 pixels."""
+    from paper_2302_02733_gb300 import polrt
+
+    assert polrt.rt_render_static_max_pixels() == 13076
+    assert "13076 pixels" in open(__graft_entry__.ROOT + "/include/polrt.h").read()

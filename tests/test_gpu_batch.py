@@ -148,7 +148,7 @@ def test_image_library_96(rt, ora, synth, torus_grid):
     e = np.concatenate(errs)
     print(f"library96 vs oracle: p50 {np.median(e):.2e} p99 {np.percentile(e, 99):.2e} max {e.max():.2e}; "
           f"full-image flux errors {max(ferrs):.2e}")
-    assert np.percentile(e, 99) <= 5e-4 and max(ferrs) <= 1e-4
+    assert np.percentile(e, 99) <= 1e-4 and max(ferrs) <= 1e-5
 
 
 def test_chunk_mode_equals_single_renders(rt, synth, torus_grid):
