@@ -150,9 +150,23 @@ def oracle_sample(cam, prims, g, npix, seed=0, nthreads=0):
     ix, iy = ix.ravel()[:npix], iy.ravel()[:npix]
     ocam, om = oracle.camera(cam), oracle.grid_model(prims, g)
     t = time.perf_counter()
-    oracle.render_pixels(ocam, om, ix, iy, nthreads=nthreads)
+    ref = oracle.render_pixels(ocam, om, ix, iy, nthreads=nthreads)[0]
     dt = time.perf_counter() - t
+    oracle_sample.last = (ix, iy, ref)
     return ix.size / dt, ix.size, stride, dt
+
+
+def vs_oracle(img, ix, iy, ref):
+    """Per-pixel error max_S |S - S_oracle| / max(I_oracle, 1e-8 max I_oracle) over the sampled
+    pixels (p50, p99, max) and the error of their summed intensity."""
+    import numpy as np
+
+    g = img[iy, ix].double().cpu().numpy()
+    scale = np.maximum(ref[:, 0], 1e-8 * ref[:, 0].max())
+    err = np.abs(g - ref).max(axis=-1) / scale
+    return {"pixels": int(ix.size), "pixel_rel_err_p50": float(np.median(err)),
+            "pixel_rel_err_p99": float(np.percentile(err, 99)), "pixel_rel_err_max": float(err.max()),
+            "sampled_flux_rel_err": float(abs(g[:, 0].sum() / ref[:, 0].sum() - 1))}
 
 
 def run_reference(args):
@@ -362,7 +376,7 @@ def main():
 
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2302_02733_gb300 import build, polrt
+    from paper_2302_02733_gb300 import build, polrt, synth
 
     build.build()
     dev = f"cuda:{local}"
@@ -430,6 +444,10 @@ def main():
         achieved_alone = pts_per_launch * XFER_FLOP_PER_POINT[args.form] / (alone["ms_transfer"] / 1e3) / 1e12
         dom = f"transfer_kernel ({args.form})"
     traffic = GEO_DRAM_BYTES_PER_STEP * steps_per_launch / max(chunks, 1) if geo_ms >= xf_ms else None
+    try:
+        probe = polrt.rt_fp64_fma_peak(local)  # measured FP64 FMA rate of this device
+    except polrt.PolrtError:
+        probe = None
     roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
             "traffic_source": "bytes per launch, scaled by steps from the ncu capture of the 256^2 case",
@@ -437,7 +455,10 @@ def main():
             "launches_per_image": chunks,
             "note": ("overlapped: each launch shares the SMs with the transfer of the previous chunk"
                      if chunks > 1 else "one launch per image"),
+            "measured_fp64_fma_peak": probe,
+            "frac_of_measured_fma_peak": (achieved / probe) if probe else None,
             "alone": {"achieved": achieved_alone, "frac": achieved_alone / FP64_PEAK_TFLOPS,
+                      "frac_of_measured_fma_peak": (achieved_alone / probe) if probe else None,
                       "ms_geodesic": alone["ms_geodesic"], "ms_transfer": alone["ms_transfer"],
                       "ms_total": alone["ms_total"]}}
 
@@ -445,6 +466,7 @@ def main():
              "points_per_image": pts_per_launch, "mean_steps_per_ray": steps_per_launch / npix}
 
     # the plain FP64 form on the same image
+    o64 = None
     if not args.no_compare and form != polrt.RT_FP64:
         o64 = torch.empty((cam.ny, cam.nx, 4), dtype=torch.float64, device=dev)
         step(polrt.RT_FP64, o64)
@@ -507,7 +529,12 @@ def main():
 
         oracle.build()
         rate, n, stride, dt = oracle_sample(cam, prims, g, 8192)
+        sample = oracle_sample.last
         rate1, n1, stride1, dt1 = oracle_sample(cam, prims, g, 512, nthreads=1)
+        # the benchmark image (and the FP64 form's) against the oracle on the timed sample
+        extra["vs_oracle_sample"] = {"chosen_form": vs_oracle(out, *sample)}
+        if o64 is not None:
+            extra["vs_oracle_sample"]["fp64_form"] = vs_oracle(o64, *sample)
         cpu = {"value": rate, "unit": "pixels/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} pixels (stride {stride}) of the {cam.nx}^2 image, {dt:.1f} s",
                "single_thread": {"value": rate1, "unit": "pixels/s", "cores": 1,
@@ -521,6 +548,9 @@ def main():
                 "data": "synthetic (seeded FM torus on an FMKS grid, log-normal perturbations)",
                 "config": {"workload": f"grmhd-torus-{cam.nx}x{cam.ny}", "grid": "288x128x128x8 f32",
                            "inclination_deg": 20, "freq_ghz": 230, "form": args.form,
+                           "beta_min": synth.TorusParams().beta_min,
+                           "perturbation_sigma": synth.TorusParams().sigma_pert,
+                           "R_high": 40, "M_unit_g": 1e19,
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (151 MB grid, multi-GB path arena); no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),

@@ -46,7 +46,7 @@ enum {
     RT_ERR_NOT_READY = -4,  /* no model or no camera set */
     RT_ERR_WORKSPACE = -5,  /* the path arena ran out; rays carry RT_RAY_OVERFLOW */
     RT_ERR_SIZE = -6,       /* a size beyond a fixed limit of the call */
-    RT_ERR_STALL = -7       /* a bounded wait inside a batched launch ran out; results invalid */
+    RT_ERR_STALL = -7       /* a bounded wait inside a kernel ran out; results invalid */
 };
 
 enum { RT_MODEL_ADAF = 1, RT_MODEL_GRID = 2 };
@@ -324,10 +324,29 @@ typedef struct {
 int rt_set_render_config(rt_ctx *ctx, const rt_render_config *cfg);
 int rt_get_render_config(rt_ctx *ctx, rt_render_config *cfg);
 
+/* The grid fetch of the FP32 transfer (Section 2.1: the grid's primitives are interpolated at
+ * every point of the geodesic): form RT_MIXED with thermal electrons on a grid model, in
+ * rt_render, rt_render_depths and rt_render_adaptive. RT_FETCH_GATHER: each point reads the
+ * eight cells of its trilinear stencil with plain loads. RT_FETCH_STAGED: while a lane works on
+ * one saved state, the stencil of its next state is copied into the lane's slot of shared
+ * memory by one TMA tensor load, completing on an mbarrier (every wait is bounded; one that
+ * runs out makes the render return RT_ERR_STALL). The image is the same bit for bit either way;
+ * only the time differs. RT_FETCH_AUTO (the default) takes the one measured faster on GB300 for
+ * the benchmark image. Other forms and models always gather. Unknown modes: RT_ERR_INVALID. */
+enum { RT_FETCH_AUTO = 0, RT_FETCH_GATHER = 1, RT_FETCH_STAGED = 2 };
+int rt_set_grid_fetch(rt_ctx *ctx, int mode);
+int rt_get_grid_fetch(rt_ctx *ctx, int *mode);
+
 /* Counters of the last rt_render (synchronizes). */
 int rt_last_counters(rt_ctx *ctx, rt_counters *out);
 
 const char *rt_error_string(int code);
+
+/* The device's measured FP64 FMA rate [TFLOP/s, an FMA counting 2]: independent FMA chains on
+ * every SM, timed with CUDA events over five launches after a warm-up. A measurement helper
+ * (the paper has no counterpart): the benchmark reports the geodesic's FP64 fraction against it
+ * beside the nominal peak. Synchronizes the device. */
+int rt_fp64_fma_peak(int device, double *tflops);
 
 /* ---- Batched rendering (image libraries, MCMC fitting) -------------------------------------
  * Many images of different cameras and model parameters in one persistent launch, replayed

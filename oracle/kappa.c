@@ -31,7 +31,7 @@
  *
  * Quadrature: every distribution integral is taken over s = ln p by composite Gauss-Legendre
  * (8 nodes per panel of width 1/8); the kernels F, G, H by the trapezoid rule in t of their
- * representations int_0^inf exp(-x cosh t) cosh(a t) [/cosh t] dt, step 1/50.
+ * representations int_0^inf exp(-x cosh t) cosh(a t) [/cosh t] dt, step min(1, x^-1/2) / 10.
  */
 #include <math.h>
 #include <string.h>
@@ -47,7 +47,9 @@ double ora_bessel_k_scaled(int n, double z);
 void ora_synch_kernels(double x, double out[3]) {
     out[0] = out[1] = out[2] = 0.0;
     if (!(x > 0.0) || x > 740.0) return;
-    const double h = 0.02;
+    /* the integrand peaks at t = 0 with width x^-1/2: the step follows it (geometric convergence
+     * of the trapezoid rule for these analytic integrands, below 1e-15 relative) */
+    const double h = 0.1 * fmin(1.0, 1.0 / sqrt(x));
     double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
     for (int k = 0; k < 100000; k++) {
         double t = k * h, wgt = k == 0 ? 0.5 : 1.0;

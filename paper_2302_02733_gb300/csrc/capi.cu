@@ -16,8 +16,46 @@ using namespace prt;
 namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kPerRayBytes = sizeof(RayRecord) + kBudgetBlocksPerRay * kBlockBytes;
+// RT_FETCH_AUTO: the grid fetch measured faster on GB300 for the benchmark image
+constexpr bool kStagedByDefault = false;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// The tensor map of the staged grid fetch: the grid's [n1][n2][n3][8] floats as a 4-d tensor
+// (innermost first: 8 primitives, n3, n2, n1; rows 32 bytes apart), loaded in boxes of one
+// cell's 8 floats x 2 x 2 x 2 cells. The driver's encoder is reached through the runtime, so the
+// library links no driver library. False if the grid is too small for the box or the encoder
+// refuses it (the fetch then gathers).
+bool encode_grid_tmap(CUtensorMap *map, const float *prims, int n1, int n2, int n3) {
+    if (n1 < 2 || n2 < 2 || n3 < 2) return false;
+    typedef CUresult (*Encode)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = (Encode)fn;
+    }
+    const cuuint64_t dims[4] = {8, (cuuint64_t)n3, (cuuint64_t)n2, (cuuint64_t)n1};
+    const cuuint64_t strides[3] = {32, 32ull * n3, 32ull * n3 * n2};  // bytes, dims 1..3
+    const cuuint32_t box[4] = {8, 2, 2, 2}, estr[4] = {1, 1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)prims, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Whether the FP32 transfer of this render stages its grid fetch (rt_set_grid_fetch).
+bool use_staged(const rt_ctx *c, int form, int coef, const Model &mod, const JobDev *jobs) {
+    if (form != RT_MIXED || coef != 0 || jobs || mod.kind != RT_MODEL_GRID || !c->have_tmap) return false;
+    return c->fetch == RT_FETCH_STAGED || (c->fetch == RT_FETCH_AUTO && kStagedByDefault);
+}
 }  // namespace
 
 
@@ -40,7 +78,7 @@ const char *rt_error_string(int code) {
         case RT_ERR_NOT_READY: return "model or camera not set";
         case RT_ERR_WORKSPACE: return "path arena overflow: enlarge the workspace";
         case RT_ERR_SIZE: return "size beyond the call's fixed limit";
-        case RT_ERR_STALL: return "a bounded wait in the batched kernel ran out";
+        case RT_ERR_STALL: return "a bounded wait in a kernel ran out";
         default: return "unknown error";
     }
 }
@@ -67,6 +105,7 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     c->geo_bps = geodesic_blocks_per_sm();
     c->fp64_bps = transfer_blocks_per_sm_fp64();
     c->mixed_bps = transfer_blocks_per_sm_mixed();
+    c->staged_bps = transfer_blocks_per_sm_staged();
     c->pipe_bps[0] = pipe_blocks_per_sm_fp64();
     c->pipe_bps[1] = pipe_blocks_per_sm_mixed();
     bool ok = cudaMalloc(&c->d_stats, (8 + 4 * kStatBlocks) * sizeof(double)) == cudaSuccess &&
@@ -123,6 +162,7 @@ int rt_destroy(rt_ctx *c) {
     cudaFree(c->d_wpk);
     cudaFree(c->d_tpk);
     cudaFree(c->d_mlpaux);
+    cudaFree(c->d_gpart);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     for (int i = 0; i < 3; i++)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -196,6 +236,7 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
         }
         cudaMemcpyKind kind = is_device_ptr(g.prims) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         CK(cudaMemcpyAsync(c->d_prims, g.prims, bytes, kind, c->stream));
+        c->have_tmap = encode_grid_tmap(&c->tmap, c->d_prims, g.n1, g.n2, g.n3);
         if (!c->d_x2) {
             if (cudaMalloc(&c->d_x2, sizeof(double) * kX2TabW * kX2TabT) != cudaSuccess ||
                 cudaMalloc(&c->d_x2f, sizeof(float) * kX2TabW * kX2TabT) != cudaSuccess) {
@@ -207,7 +248,8 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
             cudaFree(c->d_x1c);
             c->d_x1c = nullptr;
             c->x1c_n = 0;
-            if (cudaMalloc(&c->d_x1c, sizeof(double) * g.n1) != cudaSuccess) {
+            // 1 / r_c as doubles, then as FP32 pairs (value, remainder)
+            if (cudaMalloc(&c->d_x1c, (sizeof(double) + sizeof(float2)) * g.n1) != cudaSuccess) {
                 cudaGetLastError();
                 return RT_ERR_NOMEM;
             }
@@ -217,8 +259,15 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
             // the same X1_in and dx1 as the fetch (make_model)
             double x1in = std::log(g.r_in), dx1 = (std::log(g.r_out) - x1in) / g.n1;
             std::vector<double> irc(g.n1);
-            for (int i = 0; i < g.n1; i++) irc[i] = std::exp(-(x1in + (i + 0.5) * dx1));
+            std::vector<float2> irc2(g.n1);
+            for (int i = 0; i < g.n1; i++) {
+                irc[i] = std::exp(-(x1in + (i + 0.5) * dx1));
+                irc2[i].x = (float)irc[i];
+                irc2[i].y = (float)(irc[i] - (double)irc2[i].x);
+            }
             CK(cudaMemcpyAsync(c->d_x1c, irc.data(), sizeof(double) * g.n1, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->d_x1c + g.n1, irc2.data(), sizeof(float2) * g.n1, cudaMemcpyHostToDevice,
+                               c->stream));
             CK(cudaStreamSynchronize(c->stream));
         }
         GridModel gm{};
@@ -489,6 +538,8 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
             launch_transfer_fp64(xa, coef, xf_grid, st);
         else if (form == RT_UNPOL)
             launch_unpol(xa, xf_grid, st);
+        else if (use_staged(c, form, coef, mod, jobs))
+            launch_transfer_staged(xa, c->tmap, xf_grid, st);
         else
             launch_transfer_mixed(xa, coef, xf_grid, st);
         CK(cudaEventRecord(te[i], st));
@@ -748,6 +799,8 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
                 launch_transfer_fp64(xa, coef, xf_grid, c->stream);
             else if (form == RT_UNPOL)
                 launch_unpol(xa, xf_grid, c->stream);
+            else if (use_staged(c, form, coef, mod, nullptr))
+                launch_transfer_staged(xa, c->tmap, xf_grid, c->stream);
             else
                 launch_transfer_mixed(xa, coef, xf_grid, c->stream);
             CK(cudaGetLastError());
@@ -764,6 +817,7 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     CK(cudaStreamSynchronize(c->stream));
     c->last_rays = nrays;
     c->last_was_batch = false;
+    if (c->h_ctr->n_status[kStageStatus] > 0) return RT_ERR_STALL;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     if (steps_out) {  // every ray of this camera recorded its steps
         c->have_steps = true;
@@ -900,6 +954,18 @@ int rt_kappa_coeffs(rt_ctx *c, const double *in, long long n, double *out) {
         cudaGetLastError();
         return RT_ERR_CUDA;
     }
+    return RT_OK;
+}
+
+int rt_set_grid_fetch(rt_ctx *c, int mode) {
+    if (!c || mode < RT_FETCH_AUTO || mode > RT_FETCH_STAGED) return RT_ERR_INVALID;
+    c->fetch = mode;
+    return RT_OK;
+}
+
+int rt_get_grid_fetch(rt_ctx *c, int *mode) {
+    if (!c || !mode) return RT_ERR_INVALID;
+    *mode = c->fetch;
     return RT_OK;
 }
 

@@ -34,6 +34,42 @@ inline int check_camera(const rt_camera &cam) {
     return RT_OK;
 }
 
+// The static camera's frame on the host (the kernels' camera_tetrad): t-leg along d_t, spatial
+// legs by Gram-Schmidt of d_phi, d_theta, d_r in the Kerr-Schild metric at (r, th).
+inline void host_camera_frame(double a, double r, double th, double e[4][4]) {
+    double s = std::sin(th), c = std::cos(th), s2 = s * s;
+    double sig = r * r + a * a * c * c, q = 2.0 * r / sig;
+    double g[4][4] = {};
+    g[0][0] = -(1.0 - q);
+    g[0][1] = g[1][0] = q;
+    g[0][3] = g[3][0] = -a * q * s2;
+    g[1][1] = 1.0 + q;
+    g[1][3] = g[3][1] = -a * s2 * (1.0 + q);
+    g[2][2] = sig;
+    g[3][3] = s2 * (sig + a * a * s2 * (1.0 + q));
+    auto dot = [&](const double *u, const double *v) {
+        double d = 0.0;
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) d += g[i][j] * u[i] * v[j];
+        return d;
+    };
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) e[i][j] = 0.0;
+    e[0][0] = 1.0 / std::sqrt(-g[0][0]);
+    for (int i = 3; i >= 1; i--) {
+        double v[4] = {0.0, 0.0, 0.0, 0.0}, w[4];
+        v[i] = 1.0;
+        double p0 = dot(v, e[0]);
+        for (int k = 0; k < 4; k++) w[k] = v[k] + p0 * e[0][k];
+        for (int j = 3; j > i; j--) {
+            double pj = dot(v, e[j]);
+            for (int k = 0; k < 4; k++) w[k] -= pj * e[j][k];
+        }
+        double n = 1.0 / std::sqrt(dot(w, w));
+        for (int k = 0; k < 4; k++) e[i][k] = w[k] * n;
+    }
+}
+
 inline Camera make_camera(const rt_camera &rc, double eps, int nmax) {
     Camera cam{};
     cam.a = rc.a;
@@ -51,6 +87,12 @@ inline Camera make_camera(const rt_camera &rc, double eps, int nmax) {
     cam.f_a = (float)cam.a;
     cam.f_nu_obs = (float)cam.nu_obs;
     cam.f_L_unit = (float)cam.L_unit;
+    double e[4][4];
+    host_camera_frame(cam.a, cam.r_cam, cam.theta_o, e);
+    for (int i = 0; i < 3; i++)
+        for (int k = 0; k < 4; k++) cam.f_e[i][k] = (float)e[i + 1][k];
+    cam.f_pix = (float)(cam.fov / cam.nx);
+    cam.f_r_cam = (float)cam.r_cam;
     return cam;
 }
 
@@ -99,7 +141,10 @@ inline Model make_model(const rt_ctx *c, const Camera &cam, double M_unit = 0.0,
         gm.prims = reinterpret_cast<const float4 *>(c->d_prims);
         gm.x2_table = c->d_x2;
         gm.x1_irc = c->d_x1c;
+        gm.x1_irc_f2 = reinterpret_cast<const float2 *>(c->d_x1c + g.n1);
         gm.idx3 = g.n3 / (2.0 * kPi);
+        gm.f_idx3_hi = (float)gm.idx3;
+        gm.f_idx3_lo = (float)(gm.idx3 - (double)gm.f_idx3_hi);
         double L = cam.L_unit;
         gm.rho_unit = (M_unit > 0.0 ? M_unit : g.M_unit) / (L * L * L);
         gm.b_unit = kC * std::sqrt(4.0 * kPi * gm.rho_unit);

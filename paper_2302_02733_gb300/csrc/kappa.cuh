@@ -16,10 +16,16 @@
 // (a_Q, a_V) kept inside the light cone. For Maxwell-Juttner electrons the rotativity averages
 // are exactly K0/K2 and K1/K2 + 6 Theta.
 //
-// Numerics (device): F, G, H from tables of their logarithms on 4096 nodes in ln x
-// (x in [1e-12, 740]) with cubic interpolation, built once per context by the trapezoid rule
-// on their cosh-integral representations; the distribution integrals over s = ln p by
-// Gauss-Legendre, 8 nodes per panel of width 1/2 (1/8 for Maxwell-Juttner electrons).
+// Numerics (device), two grades:
+//  - tabulated (kExact false; the FP32 render, the surrogate's training set and fallback,
+//    rt_kappa_coeffs): F, G, H from tables of their logarithms on 4096 nodes in ln x
+//    (x in [1e-12, 740]) with cubic interpolation, built once per context by the trapezoid
+//    rule on their cosh-integral representations; the distribution integrals over s = ln p
+//    by Gauss-Legendre, 8 nodes per panel of width 1/2 (1/8 for Maxwell-Juttner electrons);
+//    about 1e-8 relative;
+//  - exact (kExact true; the FP64 render): F, G, H evaluated at every node by the trapezoid
+//    rule (synch_kernels_exact, about 1e-14 relative) and 8 nodes per panel of width 1/8 for
+//    every distribution, so that the quadrature error is far below the FP64 form's 1e-9.
 #pragma once
 #include "rt_common.cuh"
 
@@ -61,6 +67,36 @@ __device__ __forceinline__ void synch_kernels_tab(const KappaTables &T, double x
     }
 }
 
+// F, G, H at x by the trapezoid rule on int_0^inf e^{-x cosh t} c(t) dt with
+// c = cosh(5t/3)/cosh t, cosh(2t/3), cosh(t/3) and cosh(t/3)/cosh t, at step 0.25 min(1, x^-1/2)
+// (the integrand's peak at t = 0 is x^-1/2 wide; the rule converges geometrically for these
+// analytic integrands, to about 1e-14 relative here), every cosh from u = e^{t/3}.
+__device__ __forceinline__ void synch_kernels_exact(double x, double k[3]) {
+    k[0] = k[1] = k[2] = 0.0;
+    if (!(x > 0.0) || x >= 740.0) return;
+    const double h = 0.25 * fmin(1.0, rsqrt(x));
+    double e0 = 0.5 * exp(-x);  // t = 0, half weight: every c(0) = 1
+    double a = e0, b = e0, c = e0, d = e0;
+    for (int i = 1; i < 4096; i++) {
+        double u = exp(i * h * (1.0 / 3.0)), iu = 1.0 / u;
+        double u2 = u * u, iu2 = iu * iu, u3 = u2 * u, iu3 = iu2 * iu;
+        double ch = 0.5 * (u3 + iu3);
+        double arg = x * ch;
+        if (arg > 745.0) break;
+        double e = exp(-arg), ich = 1.0 / ch;
+        double c13 = 0.5 * (u + iu);
+        double ta = e * 0.5 * (u3 * u2 + iu3 * iu2) * ich;
+        a += ta;
+        b += e * 0.5 * (u2 + iu2);
+        c += e * c13;
+        d += e * c13 * ich;
+        if (i > 4 && ta < 1e-19 * a) break;
+    }
+    k[0] = x * h * a;
+    k[1] = x * h * b;
+    k[2] = x * h * c + h * d;
+}
+
 struct Edf {
     bool thermal;
     double theta, kappa, kw, norm;
@@ -99,9 +135,11 @@ __device__ __forceinline__ double bessel_k2_scaled(double z) {
     return h * sum;
 }
 
-// out: jI jQ jV aI aQ aV rQ rV (cgs). kappa <= 0 selects Maxwell-Juttner electrons.
-__device__ __forceinline__ void kappa_coeffs_quad(const KappaTables &T, double ne, double Te, double B, double nu, double thB,
-                                  double kappa, double out[8]) {
+// out: jI jQ jV aI aQ aV rQ rV (cgs). kappa <= 0 selects Maxwell-Juttner electrons. kExact:
+// the exact grade (kernels at every node, 8 panels per unit of s), else the tabulated one.
+template <bool kExact = false>
+__device__ __forceinline__ void kappa_coeffs_quad(const KappaTables &T, double ne, double Te, double B, double nu,
+                                                  double thB, double kappa, double out[8]) {
 #pragma unroll
     for (int i = 0; i < 8; i++) out[i] = 0.0;
     if (!(ne > 0.0) || !(Te > 0.0) || !(B > 0.0) || !(nu > 0.0)) return;
@@ -126,7 +164,7 @@ __device__ __forceinline__ void kappa_coeffs_quad(const KappaTables &T, double n
     }
     // panels per unit of s: the kappa integrands are smooth power laws; far above nu_c the
     // Maxwell-Juttner integrand is a peak about 0.1 wide in s and needs four times more
-    const int kPanels = d.thermal ? 8 : 2;
+    const int kPanels = (kExact || d.thermal) ? 8 : 2;
     // normalisation (kappa) and rotativity averages over the whole momentum range
     double nacc = 0.0, rv = 0.0, rq = 0.0;
     {
@@ -171,7 +209,10 @@ __device__ __forceinline__ void kappa_coeffs_quad(const KappaTables &T, double n
             double g = sqrt(1.0 + p * p);
             double N, D, kk[3];
             d.eval(p, g, N, D);
-            synch_kernels_tab(T, X / (g * g), kk);
+            if (kExact)
+                synch_kernels_exact(X / (g * g), kk);
+            else
+                synch_kernels_tab(T, X / (g * g), kk);
             double dg = hw * T.glw[i] * p * p / g;
             double ig = 1.0 / g;
             e[0] += dg * N * kk[0];

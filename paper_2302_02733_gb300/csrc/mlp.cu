@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(128, 1) mlp_forward_kernel(const float4 *__res
 constexpr int kTrT = kPkWBytes, kTrA0 = kTrT + kPkTBytes, kTrA1 = kTrA0 + 128 * 16 * 2;
 constexpr int kTrA2 = kTrA1 + 128 * 80 * 2, kTrA3 = kTrA2 + 128 * 80 * 2, kTrDZ = kTrA3 + 128 * 80 * 2;
 constexpr int kTrDZT = kTrDZ + 128 * 80 * 2, kTrAT = kTrDZT + 64 * 128 * 2, kTrBar = kTrAT + 128 * 128 * 2;
-constexpr int kTrSmem = kTrBar + 16;
+constexpr int kTrSmem = kTrBar + 32;  // mbarrier, TMEM slot, the warps' losses
 // TMEM columns: pre-activations Z1-Z3, scratch S (outputs, then dA), weight-gradient images G1-G4
 constexpr uint32_t kCZ1 = 0, kCZ2 = 64, kCZ3 = 128, kCS = 192, kCG1 = 288, kCG2 = 352, kCG3 = 416, kCG4 = 480;
 
@@ -167,11 +167,13 @@ __device__ __forceinline__ void transpose_row(const unsigned char *A, unsigned c
             *reinterpret_cast<const __nv_bfloat16 *>(A + kmaj_off(r, k, K));
 }
 
-// grad (the FP32 master layout) += d loss / d theta over this block's 128 samples, with
-// loss = sum over samples and outputs of (y - t)^2 / (ntot * 8); loss_out += this block's loss.
+// gpart[block] (the FP32 master layout) = d loss / d theta over this block's 128 samples, with
+// loss = sum over samples and outputs of (y - t)^2 / (ntot * 8); lpart[block] = this block's
+// loss. Every element is written once (no atomics), so that a fixed-order sum over the blocks
+// (mlp_sum_kernel, mlp_adam_kernel) makes a training run depend only on its seed.
 __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float4 *__restrict__ x, const float *__restrict__ t,
                                                           long long n, long long ntot, const uint4 *__restrict__ wpk,
-                                                          const uint4 *__restrict__ tpk, float *grad, float *loss_out,
+                                                          const uint4 *__restrict__ tpk, float *gpart, float *lpart,
                                                           unsigned *err) {
     extern __shared__ __align__(128) unsigned char sm[];
     const int r = threadIdx.x, warp = r >> 5;
@@ -245,8 +247,10 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float4 *__restri
         *reinterpret_cast<__nv_bfloat16 *>(sm + kTrDZT + kmaj_off(k, r, 128)) = __float2bfloat16_rn(dy[k]);
     transpose_row<80>(sm + kTrA3, sm + kTrAT, r);
     for (int o = 16; o >= 1; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if ((r & 31) == 0) atomicAdd(loss_out, lsum / (8.0f * (float)ntot));
+    float *wl = reinterpret_cast<float *>(sm + kTrBar + 12);  // 4 floats after the TMEM slot
+    if ((r & 31) == 0) wl[warp] = lsum;
     tc_barrier();
+    if (r == 0) lpart[blockIdx.x] = (((wl[0] + wl[1]) + wl[2]) + wl[3]) / (8.0f * (float)ntot);
     if (r == 0 && s.ok) {
         tc_gemm(tm + kCG4, sAT, sDZT, 16, 128, false);  // dW4^T = A3^T dY
         tc_gemm(tm + kCS, sDZ, sT + kPkT4, 80, 16, false);  // dA3 = dY W4
@@ -278,6 +282,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float4 *__restri
     }
 
     // weight gradients: TMEM lane k holds d loss / d W_L[o][k] for input index k (k == in: bias)
+    float *g = gpart + (long long)blockIdx.x * kMlpParams;
     if (s.ok) {
         const uint32_t gc[4] = {kCG1, kCG2, kCG3, kCG4};
         for (int L = 1; L <= 4; L++) {
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float4 *__restri
                 tmem_ld16(tm + lane + gc[3], v);
             }
             if (r <= in)
-                for (int o = 0; o < out; o++) atomicAdd(grad + mlp_index(L, o, r), v[o]);
+                for (int o = 0; o < out; o++) g[mlp_index(L, o, r)] = v[o];
         }
     }
     if (!s.ok && r == 0) atomicOr(err, 1u);
@@ -298,17 +303,38 @@ __global__ void __launch_bounds__(128, 1) mlp_grad_kernel(const float4 *__restri
     if (warp == 0) tmem_dealloc(tm, 512);
 }
 
-// ---- Adam ----------------------------------------------------------------------------------
-__global__ void mlp_adam_kernel(float *th, float *m, float *v, float *grad, int n, float lr, float b1, float b2,
-                                float eps, float c1, float c2) {
+// ---- fixed-order sums over the blocks, Adam ---------------------------------------------------
+// acc (+)= sum over blocks b = 0 .. nb-1, in that order, of gpart[b]; loss = sum of lpart
+__global__ void mlp_sum_kernel(const float *gpart, const float *lpart, int nb, float *acc, float *loss, bool add) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kMlpParams) {
+        float g = add ? acc[i] : 0.f;
+        for (int b = 0; b < nb; b++) g += gpart[(long long)b * kMlpParams + i];
+        acc[i] = g;
+    }
+    if (i == 0 && loss) {
+        float l = add ? *loss : 0.f;
+        for (int b = 0; b < nb; b++) l += lpart[b];
+        *loss = l;
+    }
+}
+
+// One Adam step on the gradient summed (in block order) from gpart; loss = the summed loss.
+__global__ void mlp_adam_kernel(float *th, float *m, float *v, const float *gpart, const float *lpart, int nb,
+                                float *loss, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && loss) {
+        float l = 0.f;
+        for (int b = 0; b < nb; b++) l += lpart[b];
+        *loss = l;
+    }
     if (i >= n) return;
-    float g = grad[i];
+    float g = 0.f;
+    for (int b = 0; b < nb; b++) g += gpart[(long long)b * kMlpParams + i];
     float mi = b1 * m[i] + (1.f - b1) * g, vi = b2 * v[i] + (1.f - b2) * g * g;
     m[i] = mi;
     v[i] = vi;
     th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    grad[i] = 0.f;
 }
 
 // ---- launchers -----------------------------------------------------------------------------
@@ -332,16 +358,21 @@ void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, 
 }
 
 void launch_mlp_grad(const float *x, const float *t, long long n, long long ntot, const void *wpk, const void *tpk,
-                     float *grad, float *loss, unsigned *err, cudaStream_t s) {
+                     float *gpart, float *lpart, unsigned *err, cudaStream_t s) {
     unsigned grid = (unsigned)((n + 127) / 128);
     mlp_grad_kernel<<<grid, 128, kTrSmem, s>>>(reinterpret_cast<const float4 *>(x), t, n, ntot,
                                                reinterpret_cast<const uint4 *>(wpk),
-                                               reinterpret_cast<const uint4 *>(tpk), grad, loss, err);
+                                               reinterpret_cast<const uint4 *>(tpk), gpart, lpart, err);
 }
 
-void launch_mlp_adam(float *th, float *m, float *v, float *grad, float lr, float b1, float b2, float eps, float c1,
-                     float c2, cudaStream_t s) {
-    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(th, m, v, grad, kMlpParams, lr, b1, b2, eps, c1, c2);
+void launch_mlp_sum(const float *gpart, const float *lpart, int nb, float *acc, float *loss, bool add, cudaStream_t s) {
+    mlp_sum_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(gpart, lpart, nb, acc, loss, add);
+}
+
+void launch_mlp_adam(float *th, float *m, float *v, const float *gpart, const float *lpart, int nb, float *loss,
+                     float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s) {
+    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(th, m, v, gpart, lpart, nb, loss, kMlpParams, lr, b1, b2,
+                                                             eps, c1, c2);
 }
 
 }  // namespace prt

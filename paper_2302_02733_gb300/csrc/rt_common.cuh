@@ -16,6 +16,8 @@ constexpr double kH = 6.62607015e-27;
 constexpr double kPi = 3.14159265358979323846;
 
 enum RayStatus : uint8_t { kHorizon = 1, kEscape = 2, kNmax = 3, kNan = 4, kOverflow = 5 };
+// Counters::n_status slot that counts lanes whose staged grid fetch's wait ran out
+constexpr int kStageStatus = 7;
 
 // One saved geodesic state: r, theta, phi, K^t, K^r, K^theta, K^phi and the step h taken
 // from it (negative when that step was reflected through the polar axis). 64 bytes.
@@ -40,6 +42,10 @@ struct Camera {
     double rh;             // outer horizon radius
     double r_stop;         // 1.05 rh: the horizon stop
     float f_a, f_nu_obs, f_L_unit;  // float copies for the FP32 transfer (no per-point conversion)
+    // the FP32 transfer's camera reading: spatial legs e_r, e_theta, e_phi of the camera frame
+    // (rows 0..2, KS components), pixel side [M] and r_cam in float
+    float f_e[3][4];
+    float f_pix, f_r_cam;
 };
 
 struct AdafModel {
@@ -56,7 +62,9 @@ struct GridModel {
     const float4 *prims;   // [n1][n2][n3] cells of two float4: (rho,u,U1,U2),(U3,B1,B2,B3)
     const double *x2_table;  // inverse FMKS guess table [kX2TabW][kX2TabT]
     const double *x1_irc;    // 1 / r at the radial cell centres [n1]
+    const float2 *x1_irc_f2; // the same as FP32 pairs (value, remainder), for the FP32 transfer
     double idx3;             // 1 / dx3
+    float f_idx3_hi, f_idx3_lo;  // 1 / dx3 as an FP32 pair
     double rho_unit, b_unit, ne_unit, R_high, R_low, sigma_cut, gamma_ad;
     // float copies for the FP32 transfer (no per-point conversion); poly_alpha1 = poly_alpha + 1
     const float *x2_table_f;

@@ -19,6 +19,11 @@ struct rt_ctx {
     float *d_x2f = nullptr;     // float copy of the FMKS inverse table
     double *d_x1c = nullptr;    // 1 / r at the radial cell centres
     int x1c_n = 0;
+    // the grid as a 4-d tensor [n1][n2][n3][8] of floats, box 8 x 2 x 2 x 2, for the staged fetch
+    CUtensorMap tmap{};
+    bool have_tmap = false;
+    int fetch = RT_FETCH_AUTO;
+    int staged_bps = 1;
     double eps = 0.05;
     int nmax = 20000;
     void *ws = nullptr;
@@ -38,6 +43,8 @@ struct rt_ctx {
     float *d_theta = nullptr;
     void *d_wpk = nullptr, *d_tpk = nullptr, *d_mlpaux = nullptr;
     rt_mlp_norm mlp_norm{};
+    float *d_gpart = nullptr;   // per-block gradient partials (kMlpParams each) and losses
+    long long gpart_cap = 0;    // blocks they hold
     bool have_mlp = false;
     prt::Counters *h_ctr = nullptr;  // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};

@@ -1,5 +1,7 @@
 // Kernel argument blocks and launchers shared by the host API and the kernels.
 #pragma once
+#include <cuda.h>
+
 #include "rt_common.cuh"
 
 namespace prt {
@@ -135,6 +137,10 @@ constexpr size_t kSinTabBytes = 1024 * 3 * sizeof(double);
 // coef: 0 thermal fits, 1 kappa quadrature at every emitting point, 2 surrogate outputs
 void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s);
 void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s);
+// the FP32 transfer (thermal electrons, grid model, one image) with the grid fetch staged
+// through shared memory by TMA loads of map: the grid as a 4-d tensor [n1][n2][n3][8] of floats
+// with a box of 8 x 2 x 2 x 2
+void launch_transfer_staged(const XferArgs &a, const CUtensorMap &map, int grid, cudaStream_t s);
 void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s);
 void launch_unpol(const XferArgs &a, int grid, cudaStream_t s);  // Stokes I only, FP32
 void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s,
@@ -148,5 +154,6 @@ void launch_image_sums(const void *img, int form, long long npix, double domega,
 int geodesic_blocks_per_sm();
 int transfer_blocks_per_sm_fp64();
 int transfer_blocks_per_sm_mixed();
+int transfer_blocks_per_sm_staged();
 
 }  // namespace prt

@@ -17,10 +17,11 @@ using namespace prt;
 namespace prt {
 int mlp_init_attributes();
 void launch_mlp_pack(const float *th, void *wpk, void *tpk, cudaStream_t s);
+void launch_mlp_sum(const float *gpart, const float *lpart, int nb, float *acc, float *loss, bool add, cudaStream_t s);
 void launch_mlp_grad(const float *x, const float *t, long long n, long long ntot, const void *wpk, const void *tpk,
                      float *grad, float *loss, unsigned *err, cudaStream_t s);
-void launch_mlp_adam(float *th, float *m, float *v, float *grad, float lr, float b1, float b2, float eps, float c1,
-                     float c2, cudaStream_t s);
+void launch_mlp_adam(float *th, float *m, float *v, const float *gpart, const float *lpart, int nb, float *loss,
+                     float lr, float b1, float b2, float eps, float c1, float c2, cudaStream_t s);
 
 __device__ __forceinline__ unsigned long long sm64(unsigned long long z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -223,6 +224,22 @@ int ensure_mlp(rt_ctx *c) {
     return RT_OK;
 }
 
+// The per-block gradient partials of up to nb blocks of 128 samples (and their losses after them).
+int ensure_gpart(rt_ctx *c, long long nb) {
+    if (c->gpart_cap >= nb) return RT_OK;
+    cudaFree(c->d_gpart);
+    c->d_gpart = nullptr;
+    c->gpart_cap = 0;
+    if (cudaMalloc(&c->d_gpart, (size_t)nb * (kMlpParams + 1) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return RT_ERR_NOMEM;
+    }
+    c->gpart_cap = nb;
+    return RT_OK;
+}
+float *gpart_loss(rt_ctx *c) { return c->d_gpart + c->gpart_cap * kMlpParams; }
+constexpr long long kGradChunkBlocks = 1024;  // rt_mlp_grad: samples per launch, in blocks of 128
+
 float *mlp_m(rt_ctx *c) { return c->d_theta + kMlpParams; }
 float *mlp_v(rt_ctx *c) { return c->d_theta + 2 * kMlpParams; }
 float *mlp_g(rt_ctx *c) { return c->d_theta + 3 * kMlpParams; }
@@ -301,9 +318,17 @@ int rt_mlp_grad(rt_ctx *c, const float *x, const float *t, long long n, float *g
     if (!c->have_mlp) return RT_ERR_NOT_READY;
     if (!is_device_ptr(x) || !is_device_ptr(t)) return RT_ERR_INVALID;
     SK(cudaSetDevice(c->device));
-    SK(cudaMemsetAsync(mlp_g(c), 0, kMlpParams * sizeof(float), c->stream));
+    const long long nb = (n + 127) / 128;
+    int rv = ensure_gpart(c, std::min(nb, kGradChunkBlocks));
+    if (rv) return rv;
     SK(cudaMemsetAsync(c->d_mlpaux, 0, 2 * sizeof(float), c->stream));
-    launch_mlp_grad(x, t, n, n, c->d_wpk, c->d_tpk, mlp_g(c), aux_loss(c), aux_err(c), c->stream);
+    // chunks of at most kGradChunkBlocks blocks, each summed in block order onto the last
+    for (long long b0 = 0; b0 < nb; b0 += kGradChunkBlocks) {
+        const long long nbk = std::min(kGradChunkBlocks, nb - b0), off = b0 * 128, nk = std::min(n - off, nbk * 128);
+        launch_mlp_grad(x + 4 * off, t + 8 * off, nk, n, c->d_wpk, c->d_tpk, c->d_gpart, gpart_loss(c), aux_err(c),
+                        c->stream);
+        launch_mlp_sum(c->d_gpart, gpart_loss(c), (int)nbk, mlp_g(c), aux_loss(c), b0 > 0, c->stream);
+    }
     SK(cudaGetLastError());
     float h[2];
     SK(cudaMemcpyAsync(grad, mlp_g(c), kMlpParams * sizeof(float), cudaMemcpyDefault, c->stream));
@@ -322,6 +347,9 @@ int rt_mlp_train(rt_ctx *c, const float *x, const float *t, long long n, int ste
     if (!c->have_mlp) return RT_ERR_NOT_READY;
     if (!is_device_ptr(x) || !is_device_ptr(t)) return RT_ERR_INVALID;
     SK(cudaSetDevice(c->device));
+    const int nb = batch / 128;
+    int rg = ensure_gpart(c, nb);
+    if (rg) return rg;
     float *losses = nullptr;
     if (cudaMalloc(&losses, sizeof(float) * steps) != cudaSuccess) {
         cudaGetLastError();
@@ -347,10 +375,10 @@ int rt_mlp_train(rt_ctx *c, const float *x, const float *t, long long n, int ste
         pb1 *= b1;
         pb2 *= b2;
         float lrs = lr * 0.5f * (1.0f + cosf(3.14159265f * s / steps));  // cosine decay
-        launch_mlp_grad(x + 4 * off, t + 8 * off, batch, batch, c->d_wpk, c->d_tpk, mlp_g(c), losses + s, aux_err(c),
-                        c->stream);
-        launch_mlp_adam(c->d_theta, mlp_m(c), mlp_v(c), mlp_g(c), lrs, b1, b2, eps, (float)(1.0 - pb1),
-                        (float)(1.0 - pb2), c->stream);
+        launch_mlp_grad(x + 4 * off, t + 8 * off, batch, batch, c->d_wpk, c->d_tpk, c->d_gpart, gpart_loss(c),
+                        aux_err(c), c->stream);
+        launch_mlp_adam(c->d_theta, mlp_m(c), mlp_v(c), c->d_gpart, gpart_loss(c), nb, losses + s, lrs, b1, b2, eps,
+                        (float)(1.0 - pb1), (float)(1.0 - pb2), c->stream);
         launch_mlp_pack(c->d_theta, c->d_wpk, c->d_tpk, c->stream);
         if (cudaGetLastError() != cudaSuccess) rv = RT_ERR_CUDA;
     }

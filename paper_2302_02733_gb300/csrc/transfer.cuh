@@ -13,6 +13,7 @@
 // (the path itself is always the FP64 geodesic).
 #pragma once
 #include "camera.cuh"
+#include "ffloat.cuh"
 #include "rt_kernels.cuh"
 
 namespace prt {
@@ -580,11 +581,20 @@ __device__ __forceinline__ R fmks_theta_w(const GridModel &g, R w, R x2, R *dth2
 template <typename R>
 __device__ __forceinline__ R fmks_y(const GridModel &g, R w, R th, R mu) {
     R fw = w * R(kX2TabW - 1);
-    int iw = min(max((int)fw, 0), kX2TabW - 2);
-    R tw = fw - R(iw);
     R ft = th * R((kX2TabT - 1) / kPi);
-    int it = min(max((int)ft, 0), kX2TabT - 2);
-    R tt = ft - R(it);
+    int iw, it;
+    R tw, tt;
+    if constexpr (sizeof(R) == 4) {  // fw in [0, 63], ft in [0, 1023]: no conversion instructions
+        iw = min(max(floor_small(fw), 0), kX2TabW - 2);
+        it = min(max(floor_small(ft), 0), kX2TabT - 2);
+        tw = fw - i2f_small(iw);
+        tt = ft - i2f_small(it);
+    } else {
+        iw = min(max((int)fw, 0), kX2TabW - 2);
+        it = min(max((int)ft, 0), kX2TabT - 2);
+        tw = fw - R(iw);
+        tt = ft - R(it);
+    }
     R x00, x01, x10, x11;
     if (sizeof(R) == 8) {
         const double *T = g.x2_table;
@@ -623,49 +633,120 @@ __device__ __forceinline__ void cell_axis(int n, int &i0, R &f) {
     f = fmin(fmax(f, R(0)), R(1));
 }
 
-// Plasma state of the FMKS grid at (r, theta, phi). The trilinear fractions are formed from
-// FP64 differences to a cell centre (r / r_c - 1, theta - pi/2 of the equator, phi / dx3 minus
-// its floor) before rounding to R: on a grid with structure from cell to cell, a fraction taken
-// from the absolute FP32 coordinates (X1 up to ln r_out, the cell index up to n) is off by
-// 1e-5 of a cell, which the steep thermal emissivity magnifies about twentyfold.
+// The trilinear fetch of the FMKS grid at (r, theta, phi) in three steps, so that a caller can
+// stage the eight cells itself (grid_plasma runs all three):
+//  - grid_cell: the corner cell (i0, j0, k0) and the fractions. They are formed from FP64
+//    differences to a cell centre (r / r_c - 1, theta - pi/2 of the equator, phi / dx3 minus
+//    its floor) before rounding to R: on a grid with structure from cell to cell, a fraction
+//    taken from the absolute FP32 coordinates (X1 up to ln r_out, the cell index up to n) is
+//    off by 1e-5 of a cell, which the steep thermal emissivity magnifies about twentyfold.
+//  - grid_interp (or an interpolation of staged cells in the same order): the primitives;
+//  - grid_state: the primitives converted to n_e, Theta_e, B, u and b.
 template <typename R>
-__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, double rd, double thd, double phd,
-                                            Plasma<R> &o) {
+struct GridCell {
+    int i0, j0, k0, k1;
+    R r, w, y;      // r in R, the FMKS blend weight and y = X2 - 1/2
+    R w1, w2, w3;   // trilinear fractions
+};
+
+// false outside r_in <= r <= r_out
+template <typename R>
+__device__ __forceinline__ bool grid_cell(const GridModel &g, double rd, double thd, double phd, GridCell<R> &c) {
     typedef Mth<R> F;
-    o.valid = false;
-    R r = R(rd), th = R(thd);
-    if (r < pick<R>(g.r_in, g.f_r_in) || r > pick<R>(g.r_out, g.f_r_out)) return;
-    R X1 = F::log_(r);
-    R w = F::exp_(pick<R>(g.mks_smooth, g.f_mks_smooth) * (pick<R>(g.x1in, g.f_x1in) - X1));
-    // radial: corner from the approximate X1, fraction ln(r / r_c) / dx1 about that centre
-    int i0 = (int)F::floor_((X1 - pick<R>(g.x1in, g.f_x1in)) / pick<R>(g.dx1, g.f_dx1) - R(0.5));
-    i0 = min(max(i0, 0), g.n1 - 2);
-    R w1 = F::log1p_(R(rd * g.x1_irc[i0] - 1.0)) / pick<R>(g.dx1, g.f_dx1);
-    cell_axis(g.n1, i0, w1);
-    // polar: y = X2 - 1/2; fj = y n2 + (n2 - 1)/2, fraction about the half-integer j0 - (n2 - 1)/2
-    R y = fmks_y(g, w, th, R(thd - 0.5 * kPi));
-    R t = y * R(g.n2), c2 = R(0.5 * (g.n2 - 1));
-    int j0 = (int)F::floor_(t + c2);
-    j0 = min(max(j0, 0), g.n2 - 2);
-    R w2 = t - (R(j0) - c2);
-    cell_axis(g.n2, j0, w2);
-    // azimuthal (periodic)
-    double fk = phd * g.idx3 - 0.5, kf = floor(fk);
-    R w3 = R(fk - kf);
-    long long kl = (long long)kf % g.n3;
-    int k0 = (int)(kl < 0 ? kl + g.n3 : kl);
-    int k1 = k0 + 1 == g.n3 ? 0 : k0 + 1;
-    R P[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    R r, th, y, w, w1, w2, w3;
+    int i0, j0, k0;
+    if constexpr (sizeof(R) == 4) {
+        // FP32 form: r, theta, phi as FP32 pairs; the fractions' differences from the pairs by
+        // error-free products, with no FP64 instruction and no int/float conversion
+        float rl, thl, ph, phl;
+        split_ff(rd, r, rl);
+        split_ff(thd, th, thl);
+        split_ff(phd, ph, phl);
+        if (r < g.f_r_in || r > g.f_r_out) return false;
+        float X1 = logf(r);
+        w = expf(g.f_mks_smooth * (g.f_x1in - X1));
+        i0 = min(max(floor_small((X1 - g.f_x1in) / g.f_dx1 - 0.5f), 0), g.n1 - 2);
+        // r / r_c - 1 = (p - 1) + (e + r il + rl ih): p = r ih rounded (in [1/2, 2], so p - 1 is
+        // exact), e its exact error; one rounding at the end
+        const float2 ic = g.x1_irc_f2[i0];
+        float pr = r * ic.x;
+        float dl = (pr - 1.0f) + (fmaf(r, ic.x, -pr) + fmaf(r, ic.y, rl * ic.x));
+        w1 = log1pf(dl) / g.f_dx1;  // ln(r / r_c) / dx1
+        cell_axis(g.n1, i0, w1);
+        // theta - pi/2 from the pair, pi/2 = 1.57079637f - 4.37113883e-8f
+        y = fmks_y(g, w, th, (th - 1.57079637f) + (thl + 4.37113883e-8f));
+        float t = y * i2f_small(g.n2), c2 = 0.5f * i2f_small(g.n2 - 1);
+        j0 = min(max(floor_small(t + c2), 0), g.n2 - 2);
+        w2 = t - (i2f_small(j0) - c2);
+        cell_axis(g.n2, j0, w2);
+        // azimuthal: phi / dx3 - 1/2 = p + pc - 1/2, p = ph ih rounded, pc its exact error and
+        // the remainders' products (|phi / dx3| < 2^22)
+        float p = ph * g.f_idx3_hi;
+        float pc = fmaf(ph, g.f_idx3_hi, -p) + fmaf(ph, g.f_idx3_lo, phl * g.f_idx3_hi);
+        float tk = p - 0.5f;
+        int kk = floor_small(tk);
+        float fr = (tk - i2f_small(kk)) + pc;
+        if (fr < 0.0f) {
+            fr += 1.0f;
+            kk--;
+        } else if (fr >= 1.0f) {
+            fr -= 1.0f;
+            kk++;
+        }
+        w3 = fr;
+        kk %= g.n3;
+        k0 = kk < 0 ? kk + g.n3 : kk;
+    } else {
+        r = R(rd);
+        th = R(thd);
+        if (r < pick<R>(g.r_in, g.f_r_in) || r > pick<R>(g.r_out, g.f_r_out)) return false;
+        R X1 = F::log_(r);
+        w = F::exp_(pick<R>(g.mks_smooth, g.f_mks_smooth) * (pick<R>(g.x1in, g.f_x1in) - X1));
+        // radial: corner from the approximate X1, fraction ln(r / r_c) / dx1 about that centre
+        i0 = (int)F::floor_((X1 - pick<R>(g.x1in, g.f_x1in)) / pick<R>(g.dx1, g.f_dx1) - R(0.5));
+        i0 = min(max(i0, 0), g.n1 - 2);
+        w1 = F::log1p_(R(rd * g.x1_irc[i0] - 1.0)) / pick<R>(g.dx1, g.f_dx1);
+        cell_axis(g.n1, i0, w1);
+        // polar: y = X2 - 1/2; fj = y n2 + (n2 - 1)/2, fraction about the half-integer j0 - (n2 - 1)/2
+        y = fmks_y(g, w, th, R(thd - 0.5 * kPi));
+        R t = y * R(g.n2), c2 = R(0.5 * (g.n2 - 1));
+        j0 = (int)F::floor_(t + c2);
+        j0 = min(max(j0, 0), g.n2 - 2);
+        w2 = t - (R(j0) - c2);
+        cell_axis(g.n2, j0, w2);
+        // azimuthal (periodic)
+        double fk = phd * g.idx3 - 0.5, kf = floor(fk);
+        w3 = R(fk - kf);
+        long long kl = (long long)kf % g.n3;
+        k0 = (int)(kl < 0 ? kl + g.n3 : kl);
+    }
+    c.i0 = i0;
+    c.j0 = j0;
+    c.k0 = k0;
+    c.k1 = k0 + 1 == g.n3 ? 0 : k0 + 1;
+    c.r = r;
+    c.w = w;
+    c.y = y;
+    c.w1 = w1;
+    c.w2 = w2;
+    c.w3 = w3;
+    return true;
+}
+
+template <typename R>
+__device__ __forceinline__ void grid_interp(const GridModel &g, const GridCell<R> &c, R P[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) P[q] = R(0);
 #pragma unroll
     for (int di = 0; di < 2; di++)
 #pragma unroll
         for (int dj = 0; dj < 2; dj++) {
-            long long row = ((long long)(i0 + di) * g.n2 + (j0 + dj)) * g.n3;
-            R wij = (di ? w1 : R(1) - w1) * (dj ? w2 : R(1) - w2);
+            long long row = ((long long)(c.i0 + di) * g.n2 + (c.j0 + dj)) * g.n3;
+            R wij = (di ? c.w1 : R(1) - c.w1) * (dj ? c.w2 : R(1) - c.w2);
 #pragma unroll
             for (int dk = 0; dk < 2; dk++) {
-                long long cell = row + (dk ? k1 : k0);
-                R wt = wij * (dk ? w3 : R(1) - w3);
+                long long cell = row + (dk ? c.k1 : c.k0);
+                R wt = wij * (dk ? c.w3 : R(1) - c.w3);
                 float4 lo = __ldg(g.prims + 2 * cell), hi = __ldg(g.prims + 2 * cell + 1);
                 P[0] += wt * R(lo.x);
                 P[1] += wt * R(lo.y);
@@ -677,11 +758,26 @@ __device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, 
                 P[7] += wt * R(hi.w);
             }
         }
+}
+
+// Weights of the trilinear interpolation in the order of grid_interp: corner (di, dj, dk).
+template <typename R>
+__device__ __forceinline__ R trilinear_weight(const GridCell<R> &c, int di, int dj, int dk) {
+    R wij = (di ? c.w1 : R(1) - c.w1) * (dj ? c.w2 : R(1) - c.w2);
+    return wij * (dk ? c.w3 : R(1) - c.w3);
+}
+
+template <typename R>
+__device__ __forceinline__ void grid_state(const GridModel &g, const KS<R> &m, const GridCell<R> &c, const R P[8],
+                                           Plasma<R> &o) {
+    typedef Mth<R> F;
+    o.valid = false;
+    const R r = c.r;
     R rho = P[0], uu = P[1];
     if (!(rho > R(0)) || !(uu > R(0))) return;
     R dth2, dd;
-    fmks_mu(g, w, y, &dth2, &dd);
-    R dth1 = -pick<R>(g.mks_smooth, g.f_mks_smooth) * w * dd;
+    fmks_mu(g, c.w, c.y, &dth2, &dd);
+    R dth1 = -pick<R>(g.mks_smooth, g.f_mks_smooth) * c.w * dd;
     R Ut[4] = {R(0), r * P[2], dth1 * P[2] + dth2 * P[3], P[4]};
     R Bi[4] = {R(0), r * P[5], dth1 * P[5] + dth2 * P[6], P[7]};
     // KS lapse 1/sqrt(1+q), shift beta^r = q/(1+q)
@@ -713,6 +809,19 @@ __device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, 
     o.Te = R(kMp / kMe) * (ga - R(1)) * uu / (rho * (R(1) + Rt));
     o.B = F::sqrt_(fmax(bsq, R(0))) * pick<R>(g.b_unit, g.f_b_unit);
     o.valid = true;
+}
+
+template <typename R>
+__device__ __forceinline__ void grid_plasma(const GridModel &g, const KS<R> &m, double rd, double thd, double phd,
+                                            Plasma<R> &o) {
+    GridCell<R> c;
+    if (!grid_cell(g, rd, thd, phd, c)) {
+        o.valid = false;
+        return;
+    }
+    R P[8];
+    grid_interp(g, c, P);
+    grid_state(g, m, c, P, o);
 }
 
 // ------------------------------------------------------------------------------------------

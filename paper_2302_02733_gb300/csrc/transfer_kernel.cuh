@@ -4,28 +4,15 @@
 // plasma, and if the point emits it projects onto the fluid screen and takes the exact
 // constant-coefficient step. Instantiated for the FP64 and the mixed (FP32 transfer) forms.
 #pragma once
+#include <cuda.h>
+
 #include "surrogate.cuh"
+#include "tc.cuh"
 #include "transfer.cuh"
 
 namespace prt {
 
-// double -> float rounded to nearest even with integer operations only, so the FP32 form
-// reads the FP64 path without using the FP64 pipe. Magnitudes below the float normal range
-// become signed zero; above it, infinity.
-__device__ __forceinline__ float d2f_int(double d) {
-    unsigned long long x = (unsigned long long)__double_as_longlong(d);
-    unsigned hi = (unsigned)(x >> 32), lo = (unsigned)x;
-    unsigned sign = hi & 0x80000000u;
-    int fe = (int)((hi >> 20) & 0x7ffu) - 896;
-    if (fe <= 0) return __uint_as_float(sign);
-    if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
-    unsigned mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    unsigned rem = lo & 0x1fffffffu;
-    unsigned f = sign | ((unsigned)fe << 23) | mant;
-    f += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & (mant & 1u));
-    return __uint_as_float(f);
-}
-
+// The FP32 form reads the FP64 path with d2f_int (ffloat.cuh): integer operations only.
 template <typename R>
 __device__ __forceinline__ R to_real(double d);
 template <>
@@ -237,10 +224,11 @@ __device__ __forceinline__ void kappa_point_coeffs(const XferArgs *pa, long long
             return;
         }
     }
-    // quadrature (CM 1, or CM 2 outside the network's box), in FP64
+    // quadrature (CM 1, or CM 2 outside the network's box), in FP64: the exact grade for the
+    // FP64 form, the tabulated one for the FP32 forms
     double thB = atan2((double)sth, (double)cth), nu = (double)(w * nu_obs);
     double cd[8];
-    kappa_coeffs_quad(pa->kt, (double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, cd);
+    kappa_coeffs_quad<sizeof(R) == 8>(pa->kt, (double)pl.ne, (double)pl.Te, (double)pl.B, nu, thB, mdl.kappa, cd);
 #pragma unroll
     for (int k = 0; k < 8; k++) cf[k] = R(cd[k]);
     if (!(cf[0] > F::jflush))  // as for the thermal fits: no relative precision left
@@ -248,10 +236,19 @@ __device__ __forceinline__ void kappa_point_coeffs(const XferArgs *pa, long long
         for (int k = 0; k < 6; k++) cf[k] = R(0);
 }
 
-template <typename R, int CM = 0>
+// pre (optional): the grid cell of this state and its interpolated primitives, fetched by the
+// caller (the staged transfer); a null cell pointer means the state lies outside the grid.
+template <typename R>
+struct PreFetch {
+    const GridCell<R> *cell;
+    const R *P;
+};
+
+template <typename R, int CM = 0, bool PRE = false>
 __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, const double4_32a &q0,
                                            const double4_32a &q1, const R *sgw, XLane<R> &Ln, KS<R> &m,
-                                           const XferArgs *pa = nullptr, long long st = 0) {
+                                           const XferArgs *pa = nullptr, long long st = 0,
+                                           PreFetch<R> pre = PreFetch<R>{nullptr, nullptr}) {
     const R a = pick<R>(c.a, c.f_a);
     R r = to_real<R>(q0.x), th = to_real<R>(q0.y), ph = to_real<R>(q0.z);
     R K[4] = {to_real<R>(q0.w), to_real<R>(q1.x), to_real<R>(q1.y), to_real<R>(q1.z)};
@@ -267,10 +264,14 @@ __device__ __forceinline__ bool xfer_point(const Camera &c, const Model &mdl, co
         Ln.a2[2] = -Ln.a2[2];
     }
     Plasma<R> pl;
-    if (mdl.kind == 1)
+    if (PRE) {
+        pl.valid = false;
+        if (pre.cell) grid_state(mdl.grid, m, *pre.cell, pre.P, pl);
+    } else if (mdl.kind == 1) {
         adaf_plasma(mdl.adaf, a, m, r, pl);
-    else
+    } else {
         grid_plasma(mdl.grid, m, q0.x, q0.y, q0.z, pl);
+    }
     R e1[4], e2[4], w, sth, cth;
     if (pl.valid) fluid_tetrad(m, K, pl.u, pl.b, e1, e2, w, sth, cth);
     if (Ln.basis || pl.valid) {
@@ -327,23 +328,47 @@ __device__ __forceinline__ void xfer_finish(const Camera &c, const KS<R> &m, int
     for (int i = 0; i < 4; i++) Ln.S[i] += Ln.Slo[i];
     if (Ln.basis) {
         // camera screen: x along e_phi, y along -e_theta, each normal to the ray
-        double e[4][4], s[3];
-        camera_tetrad(c.a, c.r_cam, c.theta_o, e);
-        sky_direction(c, ix, iy, s);
-        double xh[3] = {-s[2] * s[0], -s[2] * s[1], 1.0 - s[2] * s[2]};
-        double nx = rsqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
-        double yh[3] = {s[1] * s[0], -1.0 + s[1] * s[1], s[1] * s[2]};
-        double yx = yh[0] * xh[0] * nx + yh[1] * xh[1] * nx + yh[2] * xh[2] * nx;
         R X[4], Y[4];
-        for (int k = 0; k < 3; k++) {
-            xh[k] *= nx;
-            yh[k] -= yx * xh[k];
-        }
-        double ny = rsqrt(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
+        if constexpr (sizeof(R) == 4) {
+            // the FP32 form: the camera frame from the host (c.f_e), the sky direction in float,
+            // with no FP64 instruction (this runs once per ray, on a lane of its own)
+            float px = (i2f_small(ix) + 0.5f) * c.f_pix - 0.5f * (c.f_pix * i2f_small(c.nx));
+            float py = (i2f_small(iy) + 0.5f) * c.f_pix - 0.5f * (c.f_pix * i2f_small(c.ny));
+            float al = px / c.f_r_cam, be = py / c.f_r_cam;
+            float n = rsqrtf(1.0f + al * al + be * be);
+            float s[3] = {-n, -be * n, al * n};
+            float xh[3] = {-s[2] * s[0], -s[2] * s[1], 1.0f - s[2] * s[2]};
+            float nx = rsqrtf(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
+            float yh[3] = {s[1] * s[0], -1.0f + s[1] * s[1], s[1] * s[2]};
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) {
-            X[mu] = R(xh[0] * e[1][mu] + xh[1] * e[2][mu] + xh[2] * e[3][mu]);
-            Y[mu] = R(ny * (yh[0] * e[1][mu] + yh[1] * e[2][mu] + yh[2] * e[3][mu]));
+            for (int k = 0; k < 3; k++) xh[k] *= nx;
+            float yx = yh[0] * xh[0] + yh[1] * xh[1] + yh[2] * xh[2];
+#pragma unroll
+            for (int k = 0; k < 3; k++) yh[k] -= yx * xh[k];
+            float ny = rsqrtf(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                X[mu] = xh[0] * c.f_e[0][mu] + xh[1] * c.f_e[1][mu] + xh[2] * c.f_e[2][mu];
+                Y[mu] = ny * (yh[0] * c.f_e[0][mu] + yh[1] * c.f_e[1][mu] + yh[2] * c.f_e[2][mu]);
+            }
+        } else {
+            double e[4][4], s[3];
+            camera_tetrad(c.a, c.r_cam, c.theta_o, e);
+            sky_direction(c, ix, iy, s);
+            double xh[3] = {-s[2] * s[0], -s[2] * s[1], 1.0 - s[2] * s[2]};
+            double nx = rsqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);
+            double yh[3] = {s[1] * s[0], -1.0 + s[1] * s[1], s[1] * s[2]};
+            double yx = yh[0] * xh[0] * nx + yh[1] * xh[1] * nx + yh[2] * xh[2] * nx;
+            for (int k = 0; k < 3; k++) {
+                xh[k] *= nx;
+                yh[k] -= yx * xh[k];
+            }
+            double ny = rsqrt(yh[0] * yh[0] + yh[1] * yh[1] + yh[2] * yh[2]);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                X[mu] = R(xh[0] * e[1][mu] + xh[1] * e[2][mu] + xh[2] * e[3][mu]);
+                Y[mu] = R(ny * (yh[0] * e[1][mu] + yh[1] * e[2][mu] + yh[2] * e[3][mu]));
+            }
         }
         R lx[4], ly[4], E1[4], E2[4];
         m.lower(X, lx);
@@ -465,6 +490,189 @@ __global__ void __launch_bounds__(kXferThreads, sizeof(R) == 4 ? 4 : 1) transfer
             if (status) status[(long long)iy * c.nx + ix] = (uint8_t)rstat;
             live = false;
         }
+    }
+    if (my_pts) atomicAdd(&p.ctr->points, my_pts);
+    if (my_emit) atomicAdd(&p.ctr->emitting, my_emit);
+}
+
+// ---- The grid fetch staged through shared memory by TMA (FP32 form, thermal electrons) ----
+// Each lane owns a 256-byte slot of shared memory and an mbarrier. While it works on one saved
+// state, the 2 x 2 x 2 cells of the next state's trilinear stencil are copied into its slot by
+// one TMA tensor load: a box of 8 floats x 2 x 2 x 2 cells of the grid seen as a 4-d tensor
+// [n1][n2][n3][8]. The fetch's latency then hides behind a whole point of work, and the eight
+// 32-byte gathers leave the load/store path. At the periodic seam in phi (k1 = 0) the two
+// k cells are not adjacent in memory, and the lane copies that stencil with plain loads. The
+// interpolation takes the cells in grid_interp's order, so the image is the same bit for bit.
+
+// TMA: the box of the 4-d tensor map at coordinates (c0, c1, c2, c3), innermost first, into
+// shared memory at dst, counted on the mbarrier bar's transaction bytes.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Arrive on bar (this thread's one arrival) and expect bytes more of transactions.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// The staged cells of one state in grid_interp's order: cell (di, dj, dk) at float4
+// ((di 2 + dj) 2 + dk) 2 (and + 1).
+template <typename R>
+__device__ __forceinline__ void grid_interp_staged(const GridCell<R> &c, const float4 *s, R P[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) P[q] = R(0);
+#pragma unroll
+    for (int di = 0; di < 2; di++)
+#pragma unroll
+        for (int dj = 0; dj < 2; dj++) {
+            R wij = (di ? c.w1 : R(1) - c.w1) * (dj ? c.w2 : R(1) - c.w2);
+#pragma unroll
+            for (int dk = 0; dk < 2; dk++) {
+                R wt = wij * (dk ? c.w3 : R(1) - c.w3);
+                const int o = ((di * 2 + dj) * 2 + dk) * 2;
+                float4 lo = s[o], hi = s[o + 1];
+                P[0] += wt * R(lo.x);
+                P[1] += wt * R(lo.y);
+                P[2] += wt * R(lo.z);
+                P[3] += wt * R(lo.w);
+                P[4] += wt * R(hi.x);
+                P[5] += wt * R(hi.y);
+                P[6] += wt * R(hi.z);
+                P[7] += wt * R(hi.w);
+            }
+        }
+}
+
+// CM: the coefficients (0: thermal fits; the only one staged so far)
+template <int CM = 0>
+__global__ void __launch_bounds__(kXferThreads, 4) transfer_kernel_staged(XferArgs p, const __grid_constant__ CUtensorMap tmap) {
+    typedef float R;
+    __shared__ R sgw[32];
+    __shared__ __align__(128) float4 stc[kXferThreads * 16];
+    __shared__ __align__(8) unsigned long long bars[kXferThreads];
+    fill_bessel_weights(sgw);
+    const uint32_t bar = smem_u32(&bars[threadIdx.x]);
+    float4 *slot_s = stc + threadIdx.x * 16;
+    const uint32_t slot_a = smem_u32(slot_s);
+    mbar_init(bar, 1);
+    __syncthreads();
+    const GridModel &g = p.model.grid;
+    long long ray = -1;
+    int blk = -1, slot = 0, n = 0, rstat = 0;
+    bool live = false, drained = false, failed = false;
+    XLane<R> Ln;
+    unsigned long long my_pts = 0, my_emit = 0;
+    uint32_t phase = 0;
+    // the next state's cell, and where its stencil is: 0 nowhere (outside the grid), 1 in
+    // flight (TMA), 2 in the slot (plain loads at the seam)
+    GridCell<R> nc;
+    int nmode = 0;
+    auto stage = [&](int b, int s) {
+        const double4_32a q = *reinterpret_cast<const double4_32a *>(p.arena.states + (long long)b * kBlockStates + s);
+        nmode = 0;
+        if (!grid_cell<R>(g, q.x, q.y, q.z, nc)) return;
+        if (nc.k1 != 0) {
+            fence_smem_async();  // the slot's last reads (generic proxy) before the TMA's writes
+            mbar_expect_tx(bar, 16 * sizeof(float4));
+            tma_load_4d(slot_a, &tmap, 0, nc.k0, nc.j0, nc.i0, bar);
+            nmode = 1;
+        } else {
+#pragma unroll
+            for (int di = 0; di < 2; di++)
+#pragma unroll
+                for (int dj = 0; dj < 2; dj++) {
+                    long long row = ((long long)(nc.i0 + di) * g.n2 + (nc.j0 + dj)) * g.n3;
+#pragma unroll
+                    for (int dk = 0; dk < 2; dk++) {
+                        long long cell = row + (dk ? nc.k1 : nc.k0);
+                        const int o = ((di * 2 + dj) * 2 + dk) * 2;
+                        slot_s[o] = __ldg(g.prims + 2 * cell);
+                        slot_s[o + 1] = __ldg(g.prims + 2 * cell + 1);
+                    }
+                }
+            nmode = 2;
+        }
+    };
+    // the state after (b, s) on the walk toward the camera
+    auto step_back = [&](int &b, int &s) {
+        if (--s < 0) {
+            b = p.arena.prev[b];
+            s = kBlockStates - 1;
+        }
+    };
+    for (;;) {
+        bool want = !live && !drained;
+        unsigned long long t = warp_pop(&p.ctr->xfer_next, want);
+        if (want) {
+            if (t < (unsigned long long)p.nrays) {
+                ray = (long long)t;
+                RayRecord rec = p.rec[ray];
+                rstat = rec.status;
+                if (rec.nstates >= 2) {
+                    blk = rec.last_block;
+                    slot = (rec.nstates - 1) % kBlockStates;
+                    n = rec.nstates - 1;
+                    Ln.reset();
+                    live = true;
+                    int b1 = blk, s1 = slot;
+                    step_back(b1, s1);
+                    stage(b1, s1);
+                } else {
+                    int ix, iy;
+                    map_pixel(p.pix_list, ray + p.ray_offset, p.cam.nx, p.cam.ny, ix, iy);
+                    long long pix = (long long)iy * p.cam.nx + ix;
+                    xfer_zero<R>(pix, p.out, p.depth);
+                    if (p.status) p.status[pix] = (uint8_t)rstat;
+                }
+            } else {
+                drained = true;
+            }
+        }
+        if (__all_sync(0xffffffffu, !live && drained)) break;
+        if (!live) continue;
+
+        step_back(blk, slot);
+        n--;
+        const double4_32a *src = reinterpret_cast<const double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot);
+        double4_32a q0 = src[0], q1 = src[1];
+        // this state's primitives from the slot, then the next state's stencil into it
+        const GridCell<R> cc = nc;
+        const int cmode = nmode;
+        R P[8];
+        if (cmode == 1 && !failed) {
+            if (mbar_wait(bar, phase))
+                phase ^= 1u;
+            else
+                failed = true;  // the copy is still owed on this phase
+        }
+        if (cmode != 0) grid_interp_staged(cc, slot_s, P);
+        if (n > 0 && !failed) {
+            int b1 = blk, s1 = slot;
+            step_back(b1, s1);
+            stage(b1, s1);
+        } else {
+            nmode = 0;
+        }
+        KS<R> m;
+        PreFetch<R> pre{cmode != 0 && !failed ? &cc : nullptr, P};
+        if (xfer_point<R, CM, true>(p.cam, p.model, q0, q1, sgw, Ln, m, &p, 0, pre)) my_emit++;
+        my_pts++;
+        if (n == 0) {
+            int ix, iy;
+            map_pixel(p.pix_list, ray + p.ray_offset, p.cam.nx, p.cam.ny, ix, iy);
+            xfer_finish<R, R>(p.cam, m, ix, iy, Ln, p.out, p.depth);
+            if (p.status) p.status[(long long)iy * p.cam.nx + ix] = (uint8_t)rstat;
+            live = false;
+        }
+    }
+    if (failed) {  // report, and give the copy in flight (bounded) time to land before exit
+        atomicAdd(&p.ctr->n_status[kStageStatus], 1u);
+        mbar_wait(bar, phase);
     }
     if (my_pts) atomicAdd(&p.ctr->points, my_pts);
     if (my_emit) atomicAdd(&p.ctr->emitting, my_emit);

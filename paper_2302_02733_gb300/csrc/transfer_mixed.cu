@@ -16,6 +16,14 @@ void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s
         default: break;
     }
 }
+void launch_transfer_staged(const XferArgs &a, const CUtensorMap &map, int grid, cudaStream_t s) {
+    transfer_kernel_staged<0><<<grid, kXferThreads, 0, s>>>(a, map);
+}
+int transfer_blocks_per_sm_staged() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transfer_kernel_staged<0>, kXferThreads, 0) != cudaSuccess) n = 1;
+    return n > 0 ? n : 1;
+}
 void launch_unpol(const XferArgs &a, int grid, cudaStream_t s) {
     if (a.jobs)
         unpol_kernel<float, true><<<grid, kXferThreads, 0, s>>>(a);

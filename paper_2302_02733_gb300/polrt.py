@@ -75,6 +75,7 @@ class rt_batch_config(C.Structure):
 
 
 RT_BATCH_PERSISTENT, RT_BATCH_CHUNKS = 0, 1
+RT_FETCH_AUTO, RT_FETCH_GATHER, RT_FETCH_STAGED = 0, 1, 2
 
 
 _lib = None
@@ -126,6 +127,9 @@ def lib():
         L.rt_get_batch_config.argtypes = [_VP, C.c_int, C.POINTER(rt_batch_config)]
         L.rt_set_render_config.argtypes = [_VP, C.POINTER(rt_render_config)]
         L.rt_get_render_config.argtypes = [_VP, C.POINTER(rt_render_config)]
+        L.rt_set_grid_fetch.argtypes = [_VP, C.c_int]
+        L.rt_fp64_fma_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
+        L.rt_get_grid_fetch.argtypes = [_VP, C.POINTER(C.c_int)]
         L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
         L.rt_error_string.restype = C.c_char_p
@@ -378,12 +382,16 @@ def rt_surrogate_fit(ctx, x, y, valid, t, lo, hi) -> rt_mlp_norm:
     return n
 
 
-def rt_render_adaptive(ctx, form: int, out, status=None, base_step: int = 8, tol: float = 1e-3) -> int:
-    """Adaptive render into device buffers; returns the number of rays traced."""
+def rt_render_adaptive(ctx, form: int, out, status=None, base_step: int = 8, tol: float = 1e-3,
+                       check: bool = True) -> int:
+    """Adaptive render into device buffers; returns the number of rays traced (with check=False,
+    the return code; the rays traced are then rt_last_counters' "rays")."""
     _check_images(ctx, form, out, status)
     n = C.c_longlong(0)
-    _check(lib().rt_render_adaptive(ctx, form, _ptr(out), _ptr(status), base_step, tol, C.byref(n)),
-           "rt_render_adaptive")
+    rc = lib().rt_render_adaptive(ctx, form, _ptr(out), _ptr(status), base_step, tol, C.byref(n))
+    if not check:
+        return rc
+    _check(rc, "rt_render_adaptive")
     return n.value
 
 
@@ -457,6 +465,24 @@ def rt_get_batch_config(ctx, form: int) -> dict:
     b = rt_batch_config()
     _check(lib().rt_get_batch_config(ctx, form, C.byref(b)), "rt_get_batch_config")
     return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
+
+
+def rt_fp64_fma_peak(device: int = 0) -> float:
+    """Measured FP64 FMA rate of the device in TFLOP/s."""
+    v = C.c_double(0.0)
+    _check(lib().rt_fp64_fma_peak(device, C.byref(v)), "rt_fp64_fma_peak")
+    return v.value
+
+
+def rt_set_grid_fetch(ctx, mode: int):
+    """RT_FETCH_AUTO, RT_FETCH_GATHER or RT_FETCH_STAGED (TMA-staged stencils)."""
+    _check(lib().rt_set_grid_fetch(ctx, mode), "rt_set_grid_fetch")
+
+
+def rt_get_grid_fetch(ctx) -> int:
+    m = C.c_int(0)
+    _check(lib().rt_get_grid_fetch(ctx, C.byref(m)), "rt_get_grid_fetch")
+    return m.value
 
 
 def rt_set_render_config(ctx, geo_blocks_per_sm: int = 0, xfer_blocks_per_sm: int = 0, chunks: int = 0):

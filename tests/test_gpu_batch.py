@@ -230,3 +230,38 @@ def test_unpolarized_batch_equals_single_renders(rt, synth, torus_grid):
         assert torch.isfinite(o).all() and torch.equal(s, rst) and err.max() <= 1e-5, (c.nx, c.incl_deg)
     with pytest.raises(polrt.PolrtError):
         polrt.rt_batch_autotune(ctx, polrt.RT_UNPOL, jobs)
+
+
+def test_checkpointed_library_resumes_on_the_gpu(rt, synth, torus_grid, tmp_path):
+    """An image library rendered through rt_render_batch in batches of 2, interrupted after the
+    first batch and resumed, equals the same library rendered in one go (and each image its
+    rt_render image, mixed form: bit for bit)."""
+    from paper_2302_02733_gb300.library import LibraryJob, gpu_batch_renderer, render_library
+
+    polrt, ctx = rt
+    prims, g = torus_grid
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
+    lib = [LibraryJob(id=k, camera=c, M_unit=mu, R_high=rh) for k, (c, mu, rh) in enumerate(small_jobs(synth))]
+    base = gpu_batch_renderer(ctx, polrt.RT_MIXED)
+    calls = []
+
+    def interrupted(part):
+        if calls:
+            raise KeyboardInterrupt
+        calls.append(len(part))
+        return base(part)
+
+    with pytest.raises(KeyboardInterrupt):
+        render_library(lib, str(tmp_path / "a"), interrupted, batch=2)
+    assert render_library(lib, str(tmp_path / "a"), base, batch=2) == [j.id for j in lib[2:]]
+    prims_dev = torch.from_numpy(prims).cuda()
+    for j in lib:
+        img = np.load(tmp_path / "a" / f"img_{j.id:06d}.npy")
+        # rt_render of the image's own parameters: the batched image, bit for bit
+        gj = dataclasses.replace(g, M_unit=j.M_unit, R_high=j.R_high)
+        polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, gj))
+        polrt.rt_set_camera(ctx, j.camera)
+        one = torch.zeros((j.camera.ny, j.camera.nx, 4), dtype=torch.float32, device="cuda")
+        polrt.rt_render(ctx, polrt.RT_MIXED, one)
+        assert np.array_equal(img, one.cpu().numpy())

@@ -188,3 +188,29 @@ def test_trained_surrogate_against_quadrature(rt, ora):
     print(f"2^20 points: quadrature {times['quadrature'] * 1e3:.1f} ms, surrogate {times['surrogate'] * 1e3:.1f} ms, "
           f"speed-up {times['quadrature'] / times['surrogate']:.1f}x")
     assert times["surrogate"] * 5 < times["quadrature"]
+
+
+def test_training_is_reproducible(rt):
+    """The gradient of a batch is summed over its 128-sample tiles in a fixed order (no atomics),
+    so two training runs from the same parameters and seed give the same network bit for bit,
+    and so does the single gradient call twice."""
+    polrt, ctx = rt
+    rng = np.random.default_rng(41)
+    n = 1 << 14
+    x = torch.from_numpy(rng.uniform(-1, 1, (n, 4)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(0, 1, (n, 8)).astype(np.float32)).cuda()
+    norm = polrt.mlp_norm(BOX[:4], BOX[4:])
+    runs = []
+    for _ in range(2):
+        polrt.rt_mlp_set_params(ctx, init_theta(42), norm)
+        curve = np.zeros(300, dtype=np.float32)
+        polrt.rt_mlp_train(ctx, x, t, 300, 2048, 2e-3, 43, curve)
+        theta = np.zeros(M.NPARAM, dtype=np.float32)
+        polrt.rt_mlp_get_params(ctx, theta)
+        runs.append((theta, curve))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert not np.array_equal(runs[0][0], init_theta(42).astype(np.float32))
+    g1, g2 = np.zeros(M.NPARAM, dtype=np.float32), np.zeros(M.NPARAM, dtype=np.float32)
+    l1 = polrt.rt_mlp_grad(ctx, x, t, g1)
+    l2 = polrt.rt_mlp_grad(ctx, x, t, g2)
+    assert np.array_equal(g1, g2) and l1 == l2
