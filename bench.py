@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form (96-image library) leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the kappa/surrogate leg")
     ap.add_argument("--no-highres", action="store_true", help="skip the ADAF 4096^2 leg")
+    ap.add_argument("--fetch", default="auto", choices=["auto", "gather", "staged"],
+                    help="grid fetch of the FP32 transfer (rt_set_grid_fetch)")
     return ap.parse_args()
 
 
@@ -386,6 +388,8 @@ def main():
     form = polrt.RT_MIXED if args.form == "mixed" else polrt.RT_FP64
     odt = torch.float32 if form == polrt.RT_MIXED else torch.float64
     ctx = polrt.rt_create(local, stream.cuda_stream)
+    polrt.rt_set_grid_fetch(ctx, {"auto": polrt.RT_FETCH_AUTO, "gather": polrt.RT_FETCH_GATHER,
+                                  "staged": polrt.RT_FETCH_STAGED}[args.fetch])
     polrt.rt_set_camera(ctx, cam)
     prims_dev = torch.from_numpy(prims).to(dev)
     polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g))
@@ -547,7 +551,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64 geodesic + f32 transfer" if form == polrt.RT_MIXED else "f64",
                 "data": "synthetic (seeded FM torus on an FMKS grid, log-normal perturbations)",
                 "config": {"workload": f"grmhd-torus-{cam.nx}x{cam.ny}", "grid": "288x128x128x8 f32",
-                           "inclination_deg": 20, "freq_ghz": 230, "form": args.form,
+                           "inclination_deg": 20, "freq_ghz": 230, "form": args.form, "grid_fetch": args.fetch,
                            "beta_min": synth.TorusParams().beta_min,
                            "perturbation_sigma": synth.TorusParams().sigma_pert,
                            "R_high": 40, "M_unit_g": 1e19,
