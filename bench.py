@@ -238,6 +238,16 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
     polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
     mo = polrt.rt_last_counters(ctx)["ms_total"]
     res["other_mode"] = {"launch": launch[other], "value": npix / (mo / 1e3), "ms_per_batch": mo}
+    if polrt.RT_BATCH_PERSISTENT in (shape["mode"], other):
+        if other != polrt.RT_BATCH_PERSISTENT:  # the last batch ran mode 1: run mode 0 once more
+            polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, g, t, b, polrt.RT_BATCH_PERSISTENT)
+            polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
+        st = polrt.rt_get_batch_stats(ctx)
+        res["persistent_flow"] = {
+            "geo_sleep_frac": st["geo_sleeps"] / max(st["geo_iters"], 1),
+            "xfer_sleep_frac": st["xfer_sleeps"] / max(st["xfer_iters"], 1),
+            "empty_polls_per_ticket": st["ticket_polls"] / max(st["tickets"], 1),
+            "ready_polls_per_ray": st["ready_polls"] / npix, "free_spins": st["free_spins"], "raw": st}
     # the same library unpolarized (the fitting loop's form; always mode 1)
     uouts = [torch.empty((j.n, j.n), dtype=torch.float32, device=dev) for j in table]
     ujobs = polrt.make_jobs((c, j.M_unit, j.R_high, o, None, None) for c, j, o in zip(cams, table, uouts))

@@ -401,6 +401,18 @@ int rt_render_batch(rt_ctx *ctx, int form, const rt_job *jobs, int njobs);
 int rt_batch_autotune(rt_ctx *ctx, int form, const rt_job *jobs, int njobs, rt_batch_config *best);
 int rt_set_batch_config(rt_ctx *ctx, int form, const rt_batch_config *cfg);
 int rt_get_batch_config(rt_ctx *ctx, int form, rt_batch_config *cfg);
+/* Flow statistics of the last batch rendered as one persistent launch (mode 0): lane
+ * iterations of the geodesic and the transfer warps' loops and, of those, the ones in which the
+ * whole warp slept (no lane could step: waiting for path blocks, or for rays to be published);
+ * polls of a ticket's ring slot that found no block yet, polls of a ready slot that found no
+ * ray yet, polls of a busy slot when returning a block, and tickets taken. A measurement of the
+ * persistent kernel's flow control (the paper has no counterpart). RT_ERR_NOT_READY before a
+ * mode-0 batch. */
+typedef struct {
+    uint64_t geo_iters, geo_sleeps, xfer_iters, xfer_sleeps;
+    uint64_t ticket_polls, ready_polls, free_spins, tickets;
+} rt_batch_stats;
+int rt_get_batch_stats(rt_ctx *ctx, rt_batch_stats *out);
 
 /* rt_render without any device allocation, for callers that cannot allocate (their device
  * memory is budgeted by someone else, or allocation is forbidden on their code path). The

@@ -161,6 +161,7 @@ int enqueue(rt_ctx *c, int form, const rt_batch_config &cfg, int njobs, long lon
 
 int finish(rt_ctx *c, long long nrays) {
     BK(cudaStreamSynchronize(c->bstream));
+    c->have_pstats = true;
     const PipeCounters &k = *c->h_pctr;
     Counters &h = *c->h_ctr;
     memset(&h, 0, sizeof(h));
@@ -314,6 +315,23 @@ int rt_set_batch_config(rt_ctx *c, int form, const rt_batch_config *cfg) {
 int rt_get_batch_config(rt_ctx *c, int form, rt_batch_config *cfg) {
     if (!c || !cfg || (form != RT_FP64 && form != RT_MIXED)) return RT_ERR_INVALID;
     *cfg = c->bcfg[fidx(form)];
+    return RT_OK;
+}
+
+int rt_get_batch_stats(rt_ctx *c, rt_batch_stats *out) {
+    if (!c || !out) return RT_ERR_INVALID;
+    if (!c->have_pstats) return RT_ERR_NOT_READY;
+    BK(cudaSetDevice(c->device));
+    BK(cudaStreamSynchronize(c->bstream));
+    const PipeCounters &k = *c->h_pctr;
+    out->geo_iters = k.geo_iters;
+    out->geo_sleeps = k.geo_sleeps;
+    out->xfer_iters = k.xfer_iters;
+    out->xfer_sleeps = k.xfer_sleeps;
+    out->ticket_polls = k.ticket_polls;
+    out->ready_polls = k.ready_polls;
+    out->free_spins = k.free_spins;
+    out->tickets = k.tickets;
     return RT_OK;
 }
 

@@ -37,27 +37,30 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Return a block to the ring at the next tail position. The slot is written only once the
 // ticket of the previous lap has taken its value (that ticket exists: the ring never holds
 // more than nblocks free blocks), and only after this lane's accesses to the block.
-__device__ __forceinline__ void pool_free(const Pool &P, PipeCounters *c, int b) {
+__device__ __forceinline__ int pool_free(const Pool &P, PipeCounters *c, int b) {
     unsigned long long pos = atomicAdd(&c->pool_tail, 1ull);
     volatile int *slot = P.ring + (pos % (unsigned long long)P.nblocks);
     int spin = 0;
     while (*slot >= 0) {
         if (++spin > kRingSpin) {
             atomicOr(&c->err, kPipeErrRing);
-            return;
+            return spin;
         }
     }
     __threadfence();
     *slot = b;
+    return spin;
 }
 
 // Free every block of a ray from its current block back to the first (own writes only).
-__device__ __forceinline__ void pool_free_chain(const Pool &P, PipeCounters *c, int blk) {
+__device__ __forceinline__ int pool_free_chain(const Pool &P, PipeCounters *c, int blk) {
+    int spins = 0;
     while (blk >= 0) {
         int pb = P.prev[blk];
-        pool_free(P, c, blk);
+        spins += pool_free(P, c, blk);
         blk = pb;
     }
+    return spins;
 }
 
 __device__ __forceinline__ void save_state(const Pool &P, int blk, int slot, const double y[7], double h) {
@@ -90,8 +93,10 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
     int job = 0, n = 0, blk = -1, slot = 0;
     bool live = false, drained = false, cancel = false;
     unsigned long long my_steps = 0, t0 = 0;
+    unsigned long long n_iter = 0, n_sleep = 0, n_tpoll = 0, n_spin = 0, n_tick = 0;
     unsigned backoff = 256;
     for (;;) {
+        n_iter++;
         bool want = !live && !drained && tk < 0;
         unsigned long long t = warp_pop(&p.ctr->geo_next, want);
         if (want) {
@@ -118,6 +123,7 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
         if (ask) {
             tk = (long long)pos;
             t0 = global_ns();
+            n_tick++;
         }
         bool go = live && tk < 0;
         if (tk >= 0) {
@@ -127,7 +133,7 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
                 *sl = -1;
                 tk = -1;
                 if (cancel) {  // the ray was given up: return the late block
-                    pool_free(p.pool, p.ctr, b);
+                    n_spin += pool_free(p.pool, p.ctr, b);
                     cancel = false;
                 } else {
                     if (blk >= 0) p.pool.fill[blk] = slot;
@@ -138,7 +144,7 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
                 }
             } else if (!cancel && global_ns() - t0 > kPoolStallNs) {
                 // no block for too long: give the ray up as an overflow, keep the ticket
-                pool_free_chain(p.pool, p.ctr, blk);
+                n_spin += pool_free_chain(p.pool, p.ctr, blk);
                 RayRecord rec = {-1, 0, kOverflow, 0};
                 publish(p, ray, rec);
                 atomicAdd(&p.ctr->n_status[kOverflow], 1u);
@@ -151,9 +157,11 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
                 tk = -1;
                 cancel = false;
             }
+            if (tk >= 0) n_tpoll++;
         }
         if (__all_sync(0xffffffffu, !go)) {  // nothing to step in this warp: wait a little
             if (__any_sync(0xffffffffu, live || tk >= 0)) {
+                n_sleep++;
                 __nanosleep(backoff);
                 backoff = min(2u * backoff, 8192u);
             }
@@ -179,7 +187,7 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
             my_steps += (unsigned long long)n;
             RayRecord rec;
             if (status == kNan) {
-                pool_free_chain(p.pool, p.ctr, blk);
+                n_spin += pool_free_chain(p.pool, p.ctr, blk);
                 rec = RayRecord{-1, 0, kNan, 0};
             } else {
                 p.pool.fill[blk] = slot;
@@ -191,6 +199,11 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
         }
     }
     if (my_steps) atomicAdd(&p.ctr->steps, my_steps);
+    atomicAdd(&p.ctr->geo_iters, n_iter);
+    if (n_sleep) atomicAdd(&p.ctr->geo_sleeps, n_sleep);
+    if (n_tpoll) atomicAdd(&p.ctr->ticket_polls, n_tpoll);
+    if (n_spin) atomicAdd(&p.ctr->free_spins, n_spin);
+    if (n_tick) atomicAdd(&p.ctr->tickets, n_tick);
 }
 
 template <typename R, typename OutT>
@@ -201,8 +214,10 @@ __device__ __forceinline__ void pipe_transfer(const PipeArgs &p, const R *sgw) {
     bool live = false, pending = false, drained = false;
     XLane<R> Ln;
     unsigned long long my_pts = 0, my_emit = 0;
+    unsigned long long n_iter = 0, n_sleep = 0, n_rpoll = 0, n_spin = 0;
     unsigned backoff = 256;
     for (;;) {
+        n_iter++;
         bool want = !live && !pending && !drained;
         unsigned long long t = warp_pop(&p.ctr->xfer_next, want);
         if (want) {
@@ -241,10 +256,13 @@ __device__ __forceinline__ void pipe_transfer(const PipeArgs &p, const R *sgw) {
                 atomicOr(&p.ctr->err, kPipeErrReady);
                 pending = false;
                 drained = true;
+            } else {
+                n_rpoll++;
             }
         }
         if (__all_sync(0xffffffffu, !live && !pending && drained)) break;
         if (!__any_sync(0xffffffffu, live)) {  // the whole warp waits for rays: back off
+            n_sleep++;
             __nanosleep(backoff);
             backoff = min(2u * backoff, 32768u);
             continue;
@@ -255,7 +273,7 @@ __device__ __forceinline__ void pipe_transfer(const PipeArgs &p, const R *sgw) {
         // move from state n to state n-1, returning each block once it is passed
         if (--slot < 0) {
             int pb = __ldcg(p.pool.prev + blk);
-            pool_free(p.pool, p.ctr, blk);
+            n_spin += pool_free(p.pool, p.ctr, blk);
             blk = pb;
             slot = __ldcg(p.pool.fill + blk) - 1;
         }
@@ -271,12 +289,16 @@ __device__ __forceinline__ void pipe_transfer(const PipeArgs &p, const R *sgw) {
             ray_pixel(ray - J.ray_begin, J.cam.nx, J.cam.ny, ix, iy);
             xfer_finish<R, OutT>(J.cam, m, ix, iy, Ln, J.out, J.depth);
             if (J.status) J.status[(long long)iy * J.cam.nx + ix] = (uint8_t)rstat;
-            pool_free(p.pool, p.ctr, blk);
+            n_spin += pool_free(p.pool, p.ctr, blk);
             live = false;
         }
     }
     if (my_pts) atomicAdd(&p.ctr->points, my_pts);
     if (my_emit) atomicAdd(&p.ctr->emitting, my_emit);
+    atomicAdd(&p.ctr->xfer_iters, n_iter);
+    if (n_sleep) atomicAdd(&p.ctr->xfer_sleeps, n_sleep);
+    if (n_rpoll) atomicAdd(&p.ctr->ready_polls, n_rpoll);
+    if (n_spin) atomicAdd(&p.ctr->free_spins, n_spin);
 }
 
 template <typename R, typename OutT>

@@ -94,6 +94,7 @@ struct rt_ctx {
     long long brays_cap = 0;
     prt::Pool pool{};
     prt::PipeCounters *d_pctr = nullptr, *h_pctr = nullptr;
+    bool have_pstats = false;             // h_pctr holds a finished mode-0 batch
     int pipe_bps[2] = {1, 1};             // resident blocks per SM of the fp64 / mixed pipe kernel
     rt_batch_config bcfg[2] = {};         // per form; geo_warps == 0 means not tuned yet
     long long bcal_rays[2] = {0, 0};      // rays of the batch the shape was tuned on (0: set by hand)

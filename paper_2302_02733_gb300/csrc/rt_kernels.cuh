@@ -91,6 +91,12 @@ struct PipeCounters {
     unsigned int n_status[8];
     unsigned int err;                                    // kPipeErr* bits
     unsigned int pad1;
+    // flow statistics, summed over lanes at their exit (one atomic each): loop iterations of
+    // the geodesic and transfer warps, iterations in which the whole warp slept (nothing to
+    // step, or no ray published yet), empty polls of a ticket's ring slot and of a ready slot,
+    // and polls of a busy slot when returning a block
+    unsigned long long geo_iters, geo_sleeps, xfer_iters, xfer_sleeps;
+    unsigned long long ticket_polls, ready_polls, free_spins, tickets;
 };
 constexpr unsigned kPipeErrRing = 1u;   // a free-ring slot never changed
 constexpr unsigned kPipeErrReady = 2u;  // a transfer lane never received its ray

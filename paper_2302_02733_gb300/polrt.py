@@ -129,6 +129,7 @@ def lib():
         L.rt_get_render_config.argtypes = [_VP, C.POINTER(rt_render_config)]
         L.rt_set_grid_fetch.argtypes = [_VP, C.c_int]
         L.rt_fp64_fma_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
+        L.rt_get_batch_stats.argtypes = [_VP, C.c_void_p]
         L.rt_get_grid_fetch.argtypes = [_VP, C.POINTER(C.c_int)]
         L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
@@ -454,6 +455,18 @@ def rt_batch_autotune(ctx, form: int, jobs) -> dict:
     b = rt_batch_config()
     _check(lib().rt_batch_autotune(ctx, form, jobs, len(jobs), C.byref(b)), "rt_batch_autotune")
     return {k: getattr(b, k) for k, _ in rt_batch_config._fields_}
+
+
+class rt_batch_stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("geo_iters", "geo_sleeps", "xfer_iters", "xfer_sleeps", "ticket_polls",
+                                          "ready_polls", "free_spins", "tickets")]
+
+
+def rt_get_batch_stats(ctx) -> dict:
+    """Flow statistics of the last persistent (mode 0) batch."""
+    st = rt_batch_stats()
+    _check(lib().rt_get_batch_stats(ctx, C.byref(st)), "rt_get_batch_stats")
+    return {k: getattr(st, k) for k, _ in rt_batch_stats._fields_}
 
 
 def rt_set_batch_config(ctx, form: int, geo_warps: int, step_tile: int, blocks_per_sm: int, mode: int = 0):
