@@ -233,14 +233,15 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
     # the other mode at the autotuner's best shape for it, for comparison
     other = polrt.RT_BATCH_PERSISTENT if shape["mode"] == polrt.RT_BATCH_CHUNKS else polrt.RT_BATCH_CHUNKS
     g, t, b = (shape["geo_warps"] or 4), (shape["step_tile"] or 1), (shape["blocks_per_sm"] or 2)
-    polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, g, t, b, other)
+    go = shape.get("geo_warps_odd", 0)
+    polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, g, t, b, other, go)
     polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
     polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
     mo = polrt.rt_last_counters(ctx)["ms_total"]
     res["other_mode"] = {"launch": launch[other], "value": npix / (mo / 1e3), "ms_per_batch": mo}
     if polrt.RT_BATCH_PERSISTENT in (shape["mode"], other):
         if other != polrt.RT_BATCH_PERSISTENT:  # the last batch ran mode 1: run mode 0 once more
-            polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, g, t, b, polrt.RT_BATCH_PERSISTENT)
+            polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, g, t, b, polrt.RT_BATCH_PERSISTENT, go)
             polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)
         st = polrt.rt_get_batch_stats(ctx)
         res["persistent_flow"] = {

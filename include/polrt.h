@@ -364,7 +364,8 @@ typedef struct {
 
 /* Launch shape of the batched form. mode 0 (RT_BATCH_PERSISTENT) is one persistent launch,
  * captured in a CUDA graph: each block has 8 warps, geo_warps of them integrate geodesics and
- * the rest run the transfer; step_tile is the number of RK4 steps a lane takes between its
+ * the rest run the transfer (odd-numbered blocks take geo_warps_odd instead when it is not 0,
+ * so that the two roles can be balanced in steps of half a warp per block); step_tile is the number of RK4 steps a lane takes between its
  * queue and pool checks; blocks_per_sm is the number of resident blocks per SM (the grid is
  * that times the SM count). mode 1 (RT_BATCH_CHUNKS) treats the rays of all images as one ray
  * space and runs it like one large image in the overlapped shape of rt_set_render_config
@@ -379,6 +380,7 @@ typedef struct {
     int blocks_per_sm;  /* 1..(the kernel's occupancy limit) (mode 0) */
     float ms;
     int mode;           /* RT_BATCH_PERSISTENT or RT_BATCH_CHUNKS */
+    int geo_warps_odd;  /* 0 (as geo_warps) or 1..7: geodesic warps of odd-numbered blocks (mode 0) */
 } rt_batch_config;
 enum { RT_BATCH_PERSISTENT = 0, RT_BATCH_CHUNKS = 1 };
 

@@ -148,7 +148,7 @@ int enqueue(rt_ctx *c, int form, const rt_batch_config &cfg, int njobs, long lon
     BK(cudaMemsetAsync(c->d_ready, 0xff, sizeof(int) * (size_t)nrays, s));
     launch_pool_init(c->pool, c->d_pctr, s);
     PipeArgs a{c->d_jobs, njobs, c->d_sctab, c->pool, c->d_brec, c->d_ready, c->d_pctr, nrays, cfg.geo_warps,
-               cfg.step_tile};
+               cfg.step_tile, cfg.geo_warps_odd > 0 ? cfg.geo_warps_odd : cfg.geo_warps};
     int grid = c->nsm * cfg.blocks_per_sm;
     if (form == RT_FP64)
         launch_pipe_fp64(a, grid, s);
@@ -184,6 +184,7 @@ int finish(rt_ctx *c, long long nrays) {
 bool valid_cfg(const rt_ctx *c, int form, const rt_batch_config &b) {
     if (b.mode == RT_BATCH_CHUNKS) return true;
     return b.mode == RT_BATCH_PERSISTENT && b.geo_warps >= 1 && b.geo_warps <= kPipeThreads / 32 - 1 &&
+           b.geo_warps_odd >= 0 && b.geo_warps_odd <= kPipeThreads / 32 - 1 &&
            b.step_tile >= 1 && b.step_tile <= 16 && b.blocks_per_sm >= 1 && b.blocks_per_sm <= c->pipe_bps[fidx(form)];
 }
 
@@ -218,7 +219,7 @@ int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config
     // first the number of geodesic warps at step tile 1, then the step tile at the best of
     // them; each shape is timed twice and keeps its faster time (one launch is noisy)
     int maxb = c->pipe_bps[fidx(form)];
-    rt_batch_config top{0, 0, 0, 0.f, RT_BATCH_PERSISTENT};
+    rt_batch_config top{0, 0, 0, 0.f, RT_BATCH_PERSISTENT, 0};
     bool warm = false;
     auto trial = [&](rt_batch_config cand) -> int {
         if (!warm) {  // one untimed launch first
@@ -244,13 +245,23 @@ int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config
         return RT_OK;
     };
     for (int g : {2, 3, 4, 5, 6}) {
-        rv = trial(rt_batch_config{g, 1, maxb, 0.f, RT_BATCH_PERSISTENT});
+        rv = trial(rt_batch_config{g, 1, maxb, 0.f, RT_BATCH_PERSISTENT, 0});
         if (rv) return rv;
     }
-    if (top.geo_warps > 0) {
+    // half a warp per block either side of the best split (odd blocks one warp off): the
+    // split at which neither role waits for the other usually lies between two whole numbers
+    if (top.geo_warps > 0 && maxb >= 2) {
         const int g = top.geo_warps;
+        for (int o : {g - 1, g + 1}) {
+            if (o < 1 || o > kPipeThreads / 32 - 1) continue;
+            rv = trial(rt_batch_config{g, 1, maxb, 0.f, RT_BATCH_PERSISTENT, o});
+            if (rv) return rv;
+        }
+    }
+    if (top.geo_warps > 0) {
+        const int g = top.geo_warps, go = top.geo_warps_odd;
         for (int t : {2, 4}) {
-            rv = trial(rt_batch_config{g, t, maxb, 0.f, RT_BATCH_PERSISTENT});
+            rv = trial(rt_batch_config{g, t, maxb, 0.f, RT_BATCH_PERSISTENT, go});
             if (rv) return rv;
         }
     }
@@ -259,7 +270,8 @@ int autotune(rt_ctx *c, int form, const rt_job *jobs, int njobs, rt_batch_config
         int r = render_chunks(c, form, k, rays);
         if (r == RT_OK) r = render_chunks(c, form, k, rays);  // the first call allocates
         if (r == RT_OK && (top.geo_warps == 0 || c->last_ms_total < top.ms))
-            top = rt_batch_config{top.geo_warps, top.step_tile, top.blocks_per_sm, c->last_ms_total, RT_BATCH_CHUNKS};
+            top = rt_batch_config{top.geo_warps, top.step_tile, top.blocks_per_sm, c->last_ms_total, RT_BATCH_CHUNKS,
+                                  top.geo_warps_odd};
         else if (r != RT_OK && r != RT_ERR_NOMEM)
             return r;
     }
@@ -364,9 +376,9 @@ int rt_render_batch(rt_ctx *c, int form, const rt_job *jobs, int njobs) {
         // rays) runs in the persistent kernel, whose pool bounds its memory
         if (rv != RT_ERR_NOMEM) return rv;
         cfg.mode = RT_BATCH_PERSISTENT;
-        if (!valid_cfg(c, form, cfg)) cfg = rt_batch_config{4, 1, c->pipe_bps[fidx(form)], 0.f, RT_BATCH_PERSISTENT};
+        if (!valid_cfg(c, form, cfg)) cfg = rt_batch_config{4, 1, c->pipe_bps[fidx(form)], 0.f, RT_BATCH_PERSISTENT, 0};
     }
-    long long key[8] = {form + 1,         njobs,          nrays, cfg.geo_warps, cfg.step_tile, cfg.blocks_per_sm,
+    long long key[8] = {form + 1,         njobs,          nrays, cfg.geo_warps * 16 + cfg.geo_warps_odd, cfg.step_tile, cfg.blocks_per_sm,
                         c->pool.nblocks, c->jobs_cap};
     if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
         drop_graph(c);

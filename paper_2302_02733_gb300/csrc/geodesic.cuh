@@ -54,11 +54,11 @@ __device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double 
     for (int i = 0; i < 7; i++) out[i] = fma(h6, k4[i], fma(h3, k3[i], fma(h3, k2[i], fma(h6, k1[i], y[i]))));
 }
 
-// Initial state of the backward ray through pixel (ix, iy): the camera tetrad's past-directed
-// null vector K = -e_0 + s^i e_i at (r_cam, theta_o, 0).
+// Initial state of the backward ray through pixel (ix, iy): the camera frame's past-directed
+// null vector K = -e_0 + s^i e_i at (r_cam, theta_o, 0), the frame computed once per camera.
 __device__ __forceinline__ void ray_start(const Camera &c, int ix, int iy, double y[7]) {
-    double e[4][4], s[3];
-    camera_tetrad(c.a, c.r_cam, c.theta_o, e);
+    const double(&e)[4][4] = c.e;
+    double s[3];
     sky_direction(c, ix, iy, s);
     y[0] = c.r_cam;
     y[1] = c.theta_o;

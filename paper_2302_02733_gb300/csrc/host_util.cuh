@@ -87,10 +87,11 @@ inline Camera make_camera(const rt_camera &rc, double eps, int nmax) {
     cam.f_a = (float)cam.a;
     cam.f_nu_obs = (float)cam.nu_obs;
     cam.f_L_unit = (float)cam.L_unit;
-    double e[4][4];
-    host_camera_frame(cam.a, cam.r_cam, cam.theta_o, e);
+    host_camera_frame(cam.a, cam.r_cam, cam.theta_o, cam.e);
+    cam.pix = cam.fov / cam.nx;
+    cam.inv_r_cam = 1.0 / cam.r_cam;
     for (int i = 0; i < 3; i++)
-        for (int k = 0; k < 4; k++) cam.f_e[i][k] = (float)e[i + 1][k];
+        for (int k = 0; k < 4; k++) cam.f_e[i][k] = (float)cam.e[i + 1][k];
     cam.f_pix = (float)(cam.fov / cam.nx);
     cam.f_r_cam = (float)cam.r_cam;
     return cam;

@@ -12,6 +12,7 @@
 // with A_nu = (K^a d_a g_{nu b}) K^b and B_nu = 1/2 d_nu g_ab K^a K^b, is evaluated
 // directly, without forming the 40 connection coefficients.
 #pragma once
+#include "ffloat.cuh"
 #include "rt_common.cuh"
 
 namespace prt {
@@ -138,8 +139,12 @@ constexpr double kSinLo = -0.25 * kPi;
 constexpr double kSinH = 1.5 * kPi / (kSinTab - 1);
 
 __device__ __forceinline__ void sincos_tab(const double *__restrict__ tab, double th, double *s, double *c) {
-    int k = __double2int_rn(fma(th, 1.0 / kSinH, -kSinLo / kSinH));
-    if (k < 1 || k > kSinTab - 2) {  // outside the table (a NaN converts to INT_MIN)
+    // the nearest node from theta rounded to FP32, with integer and FP32 operations (an FP64
+    // to int conversion would take the FP64 pipe); a node one off, for a theta halfway between
+    // two, leaves |delta| a few 1e-7 above kSinH / 2, well inside the polynomials' accuracy.
+    // A NaN or infinite theta gives a k outside the table.
+    int k = rint_small(fmaf(d2f_int(th), float(1.0 / kSinH), float(-kSinLo / kSinH)));
+    if (k < 1 || k > kSinTab - 2) {  // outside the table
         sincos(th, s, c);
         return;
     }

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kPipeThreads, sizeof(R) == 4 ? 2 : 1) pipe_ker
     fill_bessel_weights(sgw);
     for (int i = threadIdx.x; i < 3 * kSinTab; i += blockDim.x) tab[i] = p.sctab[i];
     __syncthreads();
-    if ((int)(threadIdx.x >> 5) < p.geo_warps)
+    if ((int)(threadIdx.x >> 5) < ((blockIdx.x & 1) ? p.geo_warps_odd : p.geo_warps))
         pipe_geodesic(p, tab);
     else
         pipe_transfer<R, OutT>(p, sgw);

@@ -42,8 +42,12 @@ struct Camera {
     double rh;             // outer horizon radius
     double r_stop;         // 1.05 rh: the horizon stop
     float f_a, f_nu_obs, f_L_unit;  // float copies for the FP32 transfer (no per-point conversion)
-    // the FP32 transfer's camera reading: spatial legs e_r, e_theta, e_phi of the camera frame
-    // (rows 0..2, KS components), pixel side [M] and r_cam in float
+    // the camera frame (static observer; rows e_t, e_r, e_theta, e_phi, KS components) from
+    // the host, the pixel side fov / nx [M] and 1 / r_cam: per-ray constants that would
+    // otherwise be recomputed in FP64 on a lane of their own at every ray's start and end
+    double e[4][4];
+    double pix, inv_r_cam;
+    // the same for the FP32 transfer's camera reading: spatial legs (rows e_r, e_theta, e_phi)
     float f_e[3][4];
     float f_pix, f_r_cam;
 };

@@ -114,6 +114,7 @@ struct PipeArgs {
     long long nrays;
     int geo_warps;      // 1..7
     int step_tile;      // RK4 steps per lane between queue and pool checks
+    int geo_warps_odd;  // 1..7: the geodesic warps of odd-numbered blocks
 };
 
 void launch_pool_init(const Pool &p, PipeCounters *c, cudaStream_t s);

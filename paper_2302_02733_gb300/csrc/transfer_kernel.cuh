@@ -352,8 +352,8 @@ __device__ __forceinline__ void xfer_finish(const Camera &c, const KS<R> &m, int
                 Y[mu] = ny * (yh[0] * c.f_e[0][mu] + yh[1] * c.f_e[1][mu] + yh[2] * c.f_e[2][mu]);
             }
         } else {
-            double e[4][4], s[3];
-            camera_tetrad(c.a, c.r_cam, c.theta_o, e);
+            const double(&e)[4][4] = c.e;
+            double s[3];
             sky_direction(c, ix, iy, s);
             double xh[3] = {-s[2] * s[0], -s[2] * s[1], 1.0 - s[2] * s[2]};
             double nx = rsqrt(xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2]);

@@ -71,7 +71,7 @@ class rt_job(C.Structure):
 
 class rt_batch_config(C.Structure):
     _fields_ = [("geo_warps", C.c_int), ("step_tile", C.c_int), ("blocks_per_sm", C.c_int), ("ms", C.c_float),
-                ("mode", C.c_int)]
+                ("mode", C.c_int), ("geo_warps_odd", C.c_int)]
 
 
 RT_BATCH_PERSISTENT, RT_BATCH_CHUNKS = 0, 1
@@ -469,8 +469,9 @@ def rt_get_batch_stats(ctx) -> dict:
     return {k: getattr(st, k) for k, _ in rt_batch_stats._fields_}
 
 
-def rt_set_batch_config(ctx, form: int, geo_warps: int, step_tile: int, blocks_per_sm: int, mode: int = 0):
-    b = rt_batch_config(geo_warps, step_tile, blocks_per_sm, 0.0, mode)
+def rt_set_batch_config(ctx, form: int, geo_warps: int, step_tile: int, blocks_per_sm: int, mode: int = 0,
+                        geo_warps_odd: int = 0):
+    b = rt_batch_config(geo_warps, step_tile, blocks_per_sm, 0.0, mode, geo_warps_odd)
     _check(lib().rt_set_batch_config(ctx, form, C.byref(b)), "rt_set_batch_config")
 
 
