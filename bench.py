@@ -225,7 +225,7 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
     fp64 = steps * GEO_FLOP_PER_STEP / (m / 1e3) / 1e12
     shape = polrt.rt_get_batch_config(ctx, polrt.RT_MIXED)
     launch = {polrt.RT_BATCH_PERSISTENT: "one persistent kernel per batch, replayed from a CUDA graph",
-              polrt.RT_BATCH_CHUNKS: "the images' rays as one ray space, overlapped chunks of two kernels"}
+              polrt.RT_BATCH_CHUNKS: "the images' rays as one ray space, in the overlapped two-kernel shape of rt_render"}
     res = {"workload": "image library: 96 images, N in {128,256,512}, torus grid, mixed form", "images": 96,
            "pixels": npix, "value": npix / (m / 1e3), "unit": "pixels/s", "ms_per_batch": m,
            "launch": launch[shape["mode"]], "shape": shape,
@@ -288,6 +288,8 @@ def highres_leg(polrt, ctx, dev, torch):
     del img
     return {"workload": "ADAF (seed 1), i = 60 deg, 4096^2, mixed form", "value": n * n / (c["ms_total"] / 1e3),
             "unit": "pixels/s", "ms_per_image": c["ms_total"], "chunks": c["chunks"],
+            "shape": {0: "one pass", 1: "overlapped halves", 2: "streamed"}[c["shape"]],
+            "geodesic_launches": c["geodesic_launches"], "transfer_launches": c["transfer_launches"],
             "vs_oracle_64x64": {"pixel_rel_err_p99": float(np.percentile(err, 99)), "pixel_rel_err_max": float(err.max()),
                                 "flux_rel_err": float(abs(sub[..., 0].sum() / ref[..., 0].sum() - 1))}}
 
@@ -430,7 +432,8 @@ def main():
             counters = polrt.rt_last_counters(ctx)
             kt_geo.append(counters["ms_geodesic"])
             kt_xf.append(counters["ms_transfer"])
-            launches += 2 * counters["chunks"] + 2  # geodesic + transfer per chunk, two image-sum kernels
+            # the geodesic and transfer launches, and the two image-sum kernels
+            launches += counters["geodesic_launches"] + counters["transfer_launches"] + 2
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -439,13 +442,18 @@ def main():
     value = job_rate(ws, npix, ms_max / 1e3)
 
     # per-kernel roofline of the dominant kernel (measured live with CUDA events in the library).
-    # In the overlapped launch shape the geodesic of one chunk shares the SMs with the transfer of
-    # the previous one, so its durations include that sharing; the kernel alone (one pass of each
-    # kernel, the shape used below 2^19 rays) is timed once after the timed region.
+    # In the overlapped launch shapes the geodesic shares the SMs with the transfers, so its
+    # durations include that sharing; the kernel alone (one pass of each kernel, the shape used
+    # below 2^19 rays) is timed once after the timed region.
     geo_ms, xf_ms = statistics.mean(kt_geo), statistics.mean(kt_xf)
     steps_per_launch = counters["steps"]
     pts_per_launch = counters["points"]
-    chunks = counters["chunks"]
+    geo_launches = max(counters["geodesic_launches"], 1)
+    shape_note = {0: "one launch per image",
+                  1: "overlapped in two workspace halves: each geodesic launch shares the SMs with the "
+                     "transfer of the previous chunk",
+                  2: "streamed: one geodesic launch per image beside the transfers of its completed chunks "
+                     f"({counters['transfer_launches']} transfer launches)"}[counters["shape"]]
     polrt.rt_set_render_config(ctx, 0, 0, 1)
     step()
     alone = polrt.rt_last_counters(ctx)
@@ -458,7 +466,7 @@ def main():
         achieved = pts_per_launch * XFER_FLOP_PER_POINT[args.form] / (xf_ms / 1e3) / 1e12
         achieved_alone = pts_per_launch * XFER_FLOP_PER_POINT[args.form] / (alone["ms_transfer"] / 1e3) / 1e12
         dom = f"transfer_kernel ({args.form})"
-    traffic = GEO_DRAM_BYTES_PER_STEP * steps_per_launch / max(chunks, 1) if geo_ms >= xf_ms else None
+    traffic = GEO_DRAM_BYTES_PER_STEP * steps_per_launch / geo_launches if geo_ms >= xf_ms else None
     try:
         probe = polrt.rt_fp64_fma_peak(local)  # measured FP64 FMA rate of this device
     except polrt.PolrtError:
@@ -467,9 +475,8 @@ def main():
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
             "traffic_source": "bytes per launch, scaled by steps from the ncu capture of the 256^2 case",
             "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-            "launches_per_image": chunks,
-            "note": ("overlapped: each launch shares the SMs with the transfer of the previous chunk"
-                     if chunks > 1 else "one launch per image"),
+            "launches_per_image": geo_launches,
+            "note": shape_note,
             "measured_fp64_fma_peak": probe,
             "frac_of_measured_fma_peak": (achieved / probe) if probe else None,
             "alone": {"achieved": achieved_alone, "frac": achieved_alone / FP64_PEAK_TFLOPS,

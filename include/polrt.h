@@ -140,8 +140,14 @@ typedef struct {
                                      * overlapped render the span from the first launch's start
                                      * to the last one's end; 0 after a batch */
     float ms_total;                 /* device time of the whole render or batch */
-    uint32_t chunks;                /* ray chunks of the last rt_render (each one geodesic and one
-                                     * transfer launch); 0 after a batch */
+    uint32_t chunks;                /* ray chunks of the last rt_render; 0 after a batch */
+    uint32_t shape;                 /* launch shape of the last rt_render: 0 one pass (of each
+                                     * kernel per chunk), 1 overlapped in two workspace halves,
+                                     * 2 streamed (rt_render_config); 0 after a batch */
+    uint32_t geodesic_launches;     /* geodesic kernels the last rt_render launched (one per
+                                     * chunk, or one per streamed piece); 0 after a batch */
+    uint32_t transfer_launches;     /* transfer kernels it launched (streamed: one per run of
+                                     * complete chunks); 0 after a batch */
 } rt_counters;
 
 /* Create a context on CUDA device `device`, enqueueing on `stream` (a cudaStream_t, or
@@ -174,7 +180,8 @@ int rt_set_integrator(rt_ctx *ctx, double eps, int nmax);
  * NULL to go back to a library-owned workspace. */
 int rt_set_workspace(rt_ctx *ctx, void *dev_ptr, size_t bytes);
 size_t rt_workspace_min_bytes(void);
-/* Workspace size the library would use for the current camera (a sizing hint). */
+/* Workspace size the library would use for the current camera: every ray's path at once, as
+ * the streamed overlapped shape needs (a sizing hint; smaller workspaces render in chunks). */
 int rt_workspace_hint(const rt_ctx *ctx, size_t *bytes);
 
 /* Render the IQUV image: out_iquv holds nx*ny*4 values, row-major [iy][ix][I,Q,U,V]
@@ -300,26 +307,43 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
 /* Launch shape of rt_render and rt_render_depths (forms RT_FP64, RT_MIXED, RT_UNPOL).
  * geo_blocks_per_sm and xfer_blocks_per_sm are the resident blocks per SM the geodesic and
  * transfer kernels are launched with (the grid is that times the SM count; 0 = automatic).
- * chunks >= 2 overlaps the two phases: the rays are split into that many chunks, each with its
- * own half of the workspace in turn, and the geodesic kernel of chunk i + 1 runs on one
- * internal stream beside the transfer kernel of chunk i on another, so the FP64 geodesic and
- * the FP32 transfer share the SMs. chunks 1 runs the phases one after the other on the
- * context's stream. chunks 0 (the default, with {0, 0, 0}) is automatic: RT_MIXED and RT_UNPOL
- * images of 2^19 rays or more are overlapped in 4 to 16 chunks of about 2^17 rays, with the
- * geodesic at 1 block per SM and the transfer at its occupancy; smaller images, and the RT_FP64
- * and RT_SURROGATE forms, run one pass of each kernel (RT_SURROGATE overlaps its features,
- * network and transfer passes when chunks >= 2 is set).
+ * chunks >= 2 overlaps the two phases, so that the FP64 geodesic and the FP32 transfer share
+ * the SMs, in one of two shapes:
+ *   - streamed, in pieces of the rays that the workspace holds at once (1 when it holds every
+ *     ray's path; up to 64; a library-owned workspace first grows to what 60% of the free
+ *     device memory allows). The longest-first order is dealt to the pieces, and each piece's
+ *     order is cut into `chunks` contiguous chunks. One geodesic launch traces a piece; each
+ *     ray that stops counts toward its chunk, and the lane that completes a chunk raises a flag
+ *     in mapped host memory. rt_render waits on the host for the flags and launches one
+ *     transfer for each run of complete chunks on a second internal stream, beside the
+ *     geodesic still running (after the geodesic has ended, at the transfer's full occupancy);
+ *     a piece starts when the previous one has ended. The call occupies its host thread until
+ *     the render ends.
+ *   - in two halves of the workspace, when a piece would hold under 1/64 of the rays (and for
+ *     RT_SURROGATE): the rays are dealt to the chunks, each chunk uses one half in turn, and
+ *     the geodesic kernel of chunk i + 1 runs on one internal stream beside the transfer
+ *     kernel of chunk i on another. last_chunk_div >= 2 shrinks the last chunk to
+ *     1/last_chunk_div of a regular one (1 to 16; 0 = 1).
+ * In both, the transfer runs with no more blocks per SM than fit in the register file beside
+ * the geodesic's. chunks 1 runs the phases one after the other on the context's stream.
+ * chunks 0 (the default, with {0, 0, 0, 0}) is automatic: RT_MIXED and RT_UNPOL images of 2^19
+ * rays or more are overlapped, streamed in chunks of about 2^15 rays (at least 16 per piece)
+ * with the geodesic at 2 blocks per SM, or in halves of 4 to 16 chunks of about 2^17 rays with
+ * the geodesic at 1 block per SM; smaller images, and the RT_FP64 and RT_SURROGATE forms, run
+ * one pass of each kernel (RT_SURROGATE overlaps its features, network and transfer passes, in
+ * halves, when chunks >= 2 is set).
  * Independently of the shape, a full render records each pixel's step count, and the next
- * render of the same camera and integrator takes its rays longest first (dealt round-robin to
- * the chunks), so that no launch ends waiting for a few long photon-ring rays. The first render
- * of a new camera of 2^18 rays or more predicts the counts from a probe of one ray per 8 x 8
- * block; the next render rebuilds the order from the counts the first one recorded. The image is the
- * same either way (every ray takes the same arithmetic); only the time differs. Shapes that
- * exceed the kernels' occupancy or chunks above 256 return RT_ERR_INVALID. */
+ * render of the same camera and integrator takes its rays longest first, so that no launch ends
+ * waiting for a few long photon-ring rays. The first render of a new camera of 2^18 rays or more
+ * predicts the counts from a probe of one ray per 8 x 8 block; the next render rebuilds the
+ * order from the counts the first one recorded. The image is the same in every shape and order
+ * (every ray takes the same arithmetic); only the time differs. Shapes that exceed the
+ * kernels' occupancy, chunks above 256 or last_chunk_div outside 0..16 return RT_ERR_INVALID. */
 typedef struct {
     int geo_blocks_per_sm;
     int xfer_blocks_per_sm;
     int chunks;
+    int last_chunk_div;
 } rt_render_config;
 int rt_set_render_config(rt_ctx *ctx, const rt_render_config *cfg);
 int rt_get_render_config(rt_ctx *ctx, rt_render_config *cfg);
@@ -339,6 +363,17 @@ int rt_get_grid_fetch(rt_ctx *ctx, int *mode);
 
 /* Counters of the last rt_render (synchronizes). */
 int rt_last_counters(rt_ctx *ctx, rt_counters *out);
+
+/* Timeline of the last overlapped render (synchronizes): for each of its chunks, four device
+ * times in ms from the first geodesic launch's start, in out[4 * k .. 4 * k + 3]: geodesic
+ * start, geodesic end, transfer start, transfer end (CUDA events on the two launching
+ * streams). In the streamed shape (one geodesic launch for all the chunks of a piece) every
+ * chunk reports its piece's launch's start and end, and the chunks that one transfer launch
+ * covered report the same transfer start and end. out (host) holds `cap` chunks; *n receives the chunk count, of which
+ * min(*n, cap) are written. An overlapped rt_render_batch (RT_BATCH_CHUNKS) has one too.
+ * *n = 0 when the last render was not overlapped (one pass, a persistent batch, or
+ * rt_render_static). For choosing a chunk count and launch shape. */
+int rt_last_timeline(rt_ctx *ctx, float *out, int cap, int *n);
 
 const char *rt_error_string(int code);
 
@@ -368,12 +403,12 @@ typedef struct {
  * so that the two roles can be balanced in steps of half a warp per block); step_tile is the number of RK4 steps a lane takes between its
  * queue and pool checks; blocks_per_sm is the number of resident blocks per SM (the grid is
  * that times the SM count). mode 1 (RT_BATCH_CHUNKS) treats the rays of all images as one ray
- * space and runs it like one large image in the overlapped shape of rt_set_render_config
- * (chunks of about 2^17 rays, 2 to 64 of them, up to 256 when the workspace is short; a batch
- * that needs more runs in mode 0; the geodesic of one chunk beside the transfer of the
- * previous), on the context's stream and without a graph; geo_warps, step_tile and
- * blocks_per_sm are then ignored. ms is the time the autotuner measured for this shape (0
- * when set by hand). */
+ * space and runs it like one large image in the automatic overlapped shape of
+ * rt_set_render_config: streamed, in pieces of the ray space that the workspace holds (up to
+ * 64), or, beyond that, in two workspace halves (chunks of about 2^17 rays, 2 to 64 of them, up
+ * to 256 when the workspace is short; a batch that needs more runs in mode 0); on the
+ * context's streams and without a graph; geo_warps, step_tile and blocks_per_sm are then
+ * ignored. ms is the time the autotuner measured for this shape (0 when set by hand). */
 typedef struct {
     int geo_warps;      /* 1..7 (mode 0) */
     int step_tile;      /* 1..16 (mode 0) */

@@ -173,6 +173,8 @@ int finish(rt_ctx *c, long long nrays) {
     c->last_rays = nrays;
     c->last_blocks_total = c->pool.nblocks;
     c->last_was_batch = true;
+    c->last_was_overlap = false;
+    c->last_was_streamed = false;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->bev[0], c->bev[1]) == cudaSuccess) c->last_ms_total = ms;
     cudaGetLastError();

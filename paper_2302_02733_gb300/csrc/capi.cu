@@ -2,6 +2,8 @@
 // All arithmetic of the method runs in the kernels. The host derives only constants of the
 // parameters (units, horizon radius, grid spacings).
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -16,6 +18,15 @@ using namespace prt;
 namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kPerRayBytes = sizeof(RayRecord) + kBudgetBlocksPerRay * kBlockBytes;
+// automatic overlapped shape: about 2^kAutoChunkShift rays per chunk, 4 to kAutoChunksMax
+// chunks, the last with 1/kAutoLastDiv of a regular chunk's share
+constexpr int kAutoChunkShift = 17;
+constexpr int kAutoChunksMax = 16;
+constexpr int kAutoLastDiv = 1;
+// automatic streamed shape: about 2^kStreamChunkShift rays per chunk, at least 16 per piece,
+// kStreamGeoBlocks geodesic blocks per SM
+constexpr int kStreamChunkShift = 15;
+constexpr int kStreamGeoBlocks = 2;
 // RT_FETCH_AUTO: the grid fetch measured faster on GB300 for the benchmark image
 constexpr bool kStagedByDefault = false;
 
@@ -108,6 +119,10 @@ int rt_create(rt_ctx **out, int device, void *stream) {
     c->staged_bps = transfer_blocks_per_sm_staged();
     c->pipe_bps[0] = pipe_blocks_per_sm_fp64();
     c->pipe_bps[1] = pipe_blocks_per_sm_mixed();
+    c->geo_regs = geodesic_regs();
+    c->xf_regs_fp64 = transfer_regs_fp64();
+    c->xf_regs_mixed = transfer_regs_mixed();
+    c->regs_per_sm = prop.regsPerMultiprocessor;
     bool ok = cudaMalloc(&c->d_stats, (8 + 4 * kStatBlocks) * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->d_sctab, kSinTabBytes) == cudaSuccess &&
               cudaMalloc(&c->d_syn, kSynTabBytes) == cudaSuccess && cudaMalloc(&c->d_gl, 16 * sizeof(double)) == cudaSuccess &&
@@ -144,6 +159,7 @@ int rt_destroy(rt_ctx *c) {
     if (c->have_oev)
         for (int i = 0; i < 4 * rt_ctx::kMaxChunks; i++) cudaEventDestroy(c->oev[i]);
     if (c->h_ctr2) cudaFreeHost(c->h_ctr2);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
     cudaFree(c->d_steps);
     cudaFree(c->d_order);
     cudaFree(c->d_ohist);
@@ -300,11 +316,17 @@ int rt_set_workspace(rt_ctx *c, void *dev_ptr, size_t bytes) {
     return RT_OK;
 }
 
+// Workspace bytes the streamed shape needs for nrays rays: counters, chunk counts, ray records
+// and the arena at the per-ray budget.
+static size_t streamed_bytes(long long nrays) {
+    return align_up(sizeof(Counters)) + align_up(sizeof(unsigned) * rt_ctx::kMaxChunks) + (size_t)nrays * kPerRayBytes +
+           4 * kAlign;
+}
+
 int rt_workspace_hint(const rt_ctx *c, size_t *bytes) {
     if (!c || !bytes) return RT_ERR_INVALID;
     if (!c->have_cam) return RT_ERR_NOT_READY;
-    long long nrays = (long long)c->cam.nx * c->cam.ny;
-    *bytes = align_up(sizeof(Counters)) + (size_t)nrays * kPerRayBytes + 4 * kAlign;
+    *bytes = streamed_bytes((long long)c->cam.nx * c->cam.ny);
     return RT_OK;
 }
 
@@ -374,6 +396,19 @@ static int ensure_overlap(rt_ctx *c) {
         if (!c->ostream[i] && cudaStreamCreateWithFlags(&c->ostream[i], cudaStreamNonBlocking) != cudaSuccess)
             return RT_ERR_CUDA;
     if (!c->h_ctr2 && cudaMallocHost(&c->h_ctr2, sizeof(Counters)) != cudaSuccess) return RT_ERR_CUDA;
+    if (!c->h_flags) {
+        if (cudaHostAlloc(&c->h_flags, sizeof(unsigned) * rt_ctx::kMaxChunks, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_flags = nullptr;
+            return RT_ERR_CUDA;
+        }
+        if (cudaHostGetDevicePointer((void **)&c->d_flags, c->h_flags, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(c->h_flags);
+            c->h_flags = nullptr;
+            return RT_ERR_CUDA;
+        }
+    }
     if (!c->have_oev) {
         for (int i = 0; i < 4 * rt_ctx::kMaxChunks; i++)
             if (cudaEventCreate(&c->oev[i]) != cudaSuccess) {
@@ -385,13 +420,6 @@ static int ensure_overlap(rt_ctx *c) {
     return RT_OK;
 }
 
-// Overlapped render. The rays are split into K chunks that alternate between two halves of the
-// workspace, each half with its own counters, ray records and arena. Chunk i's geodesic runs on
-// ostream[0] once the transfer of chunk i - 2 (the same half) has finished, and its transfer on
-// ostream[1] once its geodesic has; so the geodesic of chunk i + 1 shares the SMs with the
-// transfer of chunk i. (A second geodesic stream, letting chunk i + 1's geodesic start beside
-// chunk i's, was slower: the two geodesics crowded the transfer out of the SMs.) Returns
-// RT_ERR_NOMEM when a half cannot hold a chunk of at most kMaxChunks-th of the rays.
 // Step-count and order arrays for npix pixels; a camera or integrator other than the one the
 // recorded steps belong to drops them.
 static int prepare_order(rt_ctx *c, const Camera &cam, long long npix) {
@@ -459,20 +487,45 @@ static int probe_steps(rt_ctx *c, const Camera &cam, Counters *ctr, RayRecord *r
     return RT_OK;
 }
 
-// Chunks of an overlapped render of nrays rays: at least `chunks`, more when a workspace half
-// cannot hold that many rays; -1 when that would need more than kMaxChunks.
-static long long overlap_chunks(const rt_ctx *c, long long nrays, int chunks, size_t per_ray) {
+// Chunk layout of an overlapped render of nrays rays: at least `chunks` chunks, the last with
+// 1/W of a regular one's share, more chunks when a workspace half cannot hold the largest;
+// K = 0 when that would need more than kMaxChunks.
+static ChunkLayout overlap_chunks(const rt_ctx *c, long long nrays, int chunks, int W, size_t per_ray) {
     const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
     const size_t off_rec = align_up(sizeof(Counters));
-    if (half < off_rec + 6 * kAlign + per_ray) return -1;
+    ChunkLayout L{nrays, 0, W};
+    if (half < off_rec + 6 * kAlign + per_ray) return L;
     long long cap = (long long)((half - off_rec - 6 * kAlign) / per_ray);
     long long K = std::min<long long>(std::max<long long>(chunks, (nrays + cap - 1) / cap), nrays);
-    return K > rt_ctx::kMaxChunks ? -1 : K;
+    for (; K <= rt_ctx::kMaxChunks; K++) {
+        L.K = (int)K;
+        if (L.max_size() <= cap) return L;
+    }
+    L.K = 0;
+    return L;
 }
 
+// Registers of a block (allocated per warp, in units of 256) and the transfer blocks per SM that
+// fit in the register file beside geo_b geodesic blocks, at most xf_b and at least 1.
+static int block_regs(int regs, int threads) { return ((regs * 32 + 255) / 256) * 256 * ((threads + 31) / 32); }
+static int xf_beside_geo(const rt_ctx *c, int form, int geo_b, int xf_b) {
+    const int xr = block_regs(form == RT_FP64 ? c->xf_regs_fp64 : c->xf_regs_mixed, kXferThreads);
+    const int room = c->regs_per_sm - geo_b * block_regs(c->geo_regs, kGeoThreads);
+    const int fit = room > 0 ? room / xr : 0;
+    return std::max(1, std::min(xf_b, fit));
+}
+
+// Overlapped render. The rays are split into K chunks that alternate between two halves of the
+// workspace, each half with its own counters, ray records and arena. Chunk i's geodesic runs on
+// ostream[0] once the transfer of chunk i - 2 (the same half) has finished, and its transfer on
+// ostream[1] once its geodesic has; so the geodesic of chunk i + 1 shares the SMs with the
+// transfer of chunk i. (A second geodesic stream, letting chunk i + 1's geodesic start beside
+// chunk i's, was slower: the two geodesics crowded the transfer out of the SMs.) Returns
+// RT_ERR_NOMEM when a half cannot hold a chunk of at most kMaxChunks-th of the rays.
 static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, const Model &mod, const int *list,
-                          uint16_t *steps_out, long long nrays, long long K, void *d_out, uint8_t *d_status,
+                          uint16_t *steps_out, const ChunkLayout &L, void *d_out, uint8_t *d_status,
                           void *d_depth, int geo_grid, int xf_grid, const JobDev *jobs = nullptr, int njobs = 0) {
+    const long long K = L.K;
     const bool sur = form == RT_SURROGATE;
     // per arena block: the states and the prev link, and for the surrogate form the network's
     // inputs and outputs of each state (16 + 32 bytes)
@@ -481,8 +534,8 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     if (rv) return rv;
     const size_t half = (c->ws_bytes / 2) & ~(size_t)(kAlign - 1);
     const size_t off_rec = align_up(sizeof(Counters));
-    // chunk k: n / K rays, one more for k < n % K (the layout of a longest-first order)
-    const long long base_n = nrays / K, extra = nrays % K, chunk = base_n + (extra ? 1 : 0);
+    // chunk k: L.size(k) rays from L.offset(k) (the layout of a longest-first order)
+    const long long chunk = L.max_size();
     Counters *ctr[2];
     RayRecord *rec[2];
     Arena ar[2];
@@ -514,7 +567,7 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     CK(cudaStreamWaitEvent(st, c->ev[0], 0));
     for (long long i = 0; i < K; i++) {
         const int h = (int)(i & 1);
-        const long long o = i * base_n + std::min(i, extra), n = base_n + (i < extra ? 1 : 0);
+        const long long o = L.offset((int)i), n = L.size((int)i);
         if (i >= 2) CK(cudaStreamWaitEvent(sg, te[i - 2], 0));
         CK(cudaMemsetAsync(ctr[h], 0, 4 * sizeof(unsigned long long), sg));  // queues + arena
         GeoArgs ga{cam, c->d_sctab, ar[h], rec[h], ctr[h], n, o};
@@ -564,7 +617,219 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
     c->last_ms_geo = g;
     c->last_ms_xfer = x;
     c->last_chunks = (int)K;
+    c->last_shape = 1;
+    c->last_geo_launches = c->last_xf_launches = (int)K;
     c->last_blocks_total = ar[0].nblocks;
+    c->last_was_streamed = false;
+    return RT_OK;
+}
+
+// Whether the workspace holds, or (when the library owns it) can grow to hold, the streamed
+// shape's nrays rays; grows it then.
+static bool prepare_streamed(rt_ctx *c, long long nrays) {
+    const size_t need = streamed_bytes(nrays);
+    if (c->ws_bytes >= need) return true;
+    if (c->ws && !c->ws_owned) return false;
+    size_t freeb = 0, total = 0;
+    if (cudaMemGetInfo(&freeb, &total) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (need > c->ws_bytes + (size_t)(0.6 * (double)freeb)) return false;
+    return ensure_workspace(c, nrays + 1) == RT_OK && c->ws_bytes >= need;
+}
+
+// Pieces of a streamed render of nrays rays: 1 when the workspace holds (or can grow to hold)
+// every path; otherwise as many as the workspace needs, after growing a library-owned one as
+// far as ensure_workspace allows; 0 (no streamed render) beyond kMaxStreamPieces.
+constexpr int kMaxStreamPieces = 64;
+static int plan_pieces(rt_ctx *c, long long nrays) {
+    if (prepare_streamed(c, nrays)) return 1;
+    if (!c->ws || c->ws_owned) ensure_workspace(c, nrays + 1);
+    const size_t fixed = streamed_bytes(0);
+    if (c->ws_bytes <= fixed) return 0;
+    const long long cap = (long long)((c->ws_bytes - fixed) / kPerRayBytes);
+    if (cap < 1) return 0;
+    for (long long P = (nrays + cap - 1) / cap; P <= kMaxStreamPieces; P++)
+        if (ChunkLayout{nrays, (int)P, 1}.max_size() <= cap) return (int)P;
+    return 0;
+}
+
+// Chunks per piece of a streamed render: `chunks` (set) or automatic, within kMaxChunks in all.
+static int stream_chunks(long long nrays, int P, int chunks, bool automatic) {
+    const long long np = ChunkLayout{nrays, P, 1}.max_size(), most = rt_ctx::kMaxChunks / P;
+    long long K = automatic ? std::max<long long>(16, np >> kStreamChunkShift) : chunks;
+    return (int)std::max<long long>(1, std::min(std::min(K, most), np));
+}
+
+// Longest wait of the host for one chunk of a streamed render. Every geodesic ends (its rays
+// take at most nmax steps), and when it has, every chunk is complete; the bound only keeps a
+// host thread from waiting without end on a GPU that no longer answers.
+constexpr double kStreamWaitSeconds = 600.0;
+
+// Streamed overlapped render, in P pieces (1 when the workspace holds every ray's path). The
+// longest-first order is dealt to the pieces (ChunkLayout {n, P, 1}), so each piece holds the
+// same mix of lengths, longest first, and is cut into K contiguous chunks. For each piece, one
+// geodesic launch on ostream[0] traces its rays into the arena. Every ray that stops counts
+// toward its chunk, and the lane that completes a chunk raises the chunk's flag in mapped host
+// memory. The host watches the flags and launches the transfers of complete chunks on
+// ostream[1], beside the geodesic still running, so no chunk boundary makes the geodesic's
+// lanes drain; a piece ends when its last transfer has. The transfers read only the paths of
+// complete chunks: each ray's states and record are released by a fence before its count, and
+// a transfer is launched after the host has seen its chunks' flags.
+static int render_streamed(rt_ctx *c, int form, int coef, const Camera &cam, const Model &mod, const int *list,
+                           uint16_t *steps_out, long long nrays, int P, int K, void *d_out, uint8_t *d_status,
+                           void *d_depth, int geo_grid, int xf_grid, int xf_grid_alone, const JobDev *jobs = nullptr,
+                           int njobs = 0) {
+    int rv = ensure_overlap(c);
+    if (rv) return rv;
+    const ChunkLayout Lp{nrays, P, 1};
+    if (P < 1 || K < 1 || (long long)P * K > rt_ctx::kMaxChunks || c->ws_bytes < streamed_bytes(Lp.max_size()))
+        return RT_ERR_NOMEM;
+    char *base = (char *)c->ws;
+    Counters *ctr = (Counters *)base;
+    size_t off = align_up(sizeof(Counters));
+    unsigned *done = (unsigned *)(base + off);
+    off = align_up(off + sizeof(unsigned) * rt_ctx::kMaxChunks);
+    RayRecord *rec = (RayRecord *)(base + off);
+    off = align_up(off + sizeof(RayRecord) * Lp.max_size());
+    Arena ar;
+    ar.nblocks = (long long)((c->ws_bytes - off - 3 * kAlign) / kBlockBytes);
+    ar.states = (PathState *)(base + off);
+    ar.prev = (int *)(base + off + (size_t)ar.nblocks * sizeof(PathState) * kBlockStates);
+    cudaStream_t sg = c->ostream[0], st = c->ostream[1];
+    cudaEvent_t *gs = c->oev, *ge = c->oev + rt_ctx::kMaxChunks, *ts = c->oev + 2 * rt_ctx::kMaxChunks,
+                *te = c->oev + 3 * rt_ctx::kMaxChunks;
+    // no launch of an earlier call may still write the flags
+    CK(cudaStreamSynchronize(sg));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(cudaStreamWaitEvent(sg, c->ev[0], 0));
+    CK(cudaStreamWaitEvent(st, c->ev[0], 0));
+    const auto t0 = std::chrono::steady_clock::now();
+    unsigned long long arena_max = 0;
+    int first = -1, last = -1, xf_launches = 0;
+    for (int p = 0; p < P; p++) {
+        const long long o_p = Lp.offset(p), n_p = Lp.size(p);
+        const ChunkLayout L{n_p, (int)std::min<long long>(K, std::max<long long>(n_p, 1)), 1};
+        const int base_k = p * K;  // this piece's chunks are base_k .. base_k + L.K - 1
+        if (p > 0) {  // the previous piece has ended: its arena and records are free
+            CK(cudaStreamSynchronize(st));
+            CK(cudaMemcpyAsync(&c->h_ctr2->arena_next, &ctr->arena_next, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, sg));
+            CK(cudaStreamSynchronize(sg));
+            arena_max = std::max(arena_max, (unsigned long long)c->h_ctr2->arena_next);
+        }
+        memset(c->h_flags, 0, sizeof(unsigned) * L.K);
+        CK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), sg));  // queues + arena
+        CK(cudaMemsetAsync(done, 0, sizeof(unsigned) * L.K, sg));
+        GeoArgs ga{cam, c->d_sctab, ar, rec, ctr, n_p, o_p};
+        ga.pix_list = list;
+        ga.steps_out = steps_out;
+        ga.jobs = jobs;
+        ga.njobs = njobs;
+        ga.chunk_done = done;
+        ga.chunk_flag = c->d_flags;
+        ga.layout = L;
+        CK(cudaEventRecord(gs[p], sg));
+        if (n_p > 0) launch_geodesic(ga, geo_grid, sg);
+        CK(cudaEventRecord(ge[p], sg));
+        CK(cudaGetLastError());
+
+        // Launch every run of consecutive chunks that are complete and not yet launched as one
+        // transfer (a chunk of long rays may complete after later ones), at the occupancy that
+        // fits beside the geodesic, or at the transfer's own once the geodesic has ended. At
+        // most one launch waits behind the running one: a new launch is made once the previous
+        // has started, so the chunks that complete meanwhile join one launch instead of queueing
+        // one each (a launch lasts at least as long as its longest ray's transfer).
+        std::vector<char> launched(L.K, 0);
+        int left = L.K, prev = -1;
+        for (int k = 0; k < L.K; k++)
+            if (L.size(k) == 0) {
+                launched[k] = 1;
+                left--;
+            }
+        while (left > 0) {
+            const cudaError_t q = cudaEventQuery(ge[p]);  // before the flags: then all are final
+            if (q != cudaSuccess && q != cudaErrorNotReady) {
+                cudaGetLastError();
+                cudaStreamSynchronize(st);
+                return RT_ERR_CUDA;
+            }
+            cudaGetLastError();  // a not-ready query
+            bool any = false, ready = false;
+            bool may = prev < 0 || cudaEventQuery(ts[base_k + prev]) == cudaSuccess;
+            cudaGetLastError();
+            for (int a = 0; a < L.K;) {
+                if (launched[a] || !__atomic_load_n(&c->h_flags[a], __ATOMIC_ACQUIRE)) {
+                    a++;
+                    continue;
+                }
+                ready = true;
+                if (!may) break;
+                int b = a + 1;
+                while (b < L.K && !launched[b] && __atomic_load_n(&c->h_flags[b], __ATOMIC_ACQUIRE)) b++;
+                const long long o = L.offset(a), n = L.offset(b - 1) + L.size(b - 1) - o;
+                XferArgs xa{cam, mod, ar, rec + o, ctr, n, o_p + o, d_out, d_status, d_depth};
+                xa.pix_list = list;
+                xa.kt = KappaTables{c->d_syn, c->d_gl, c->d_gl + 8};
+                xa.jobs = jobs;
+                xa.njobs = njobs;
+                const int grid = q == cudaSuccess ? xf_grid_alone : xf_grid;
+                CK(cudaMemsetAsync(&ctr->xfer_next, 0, sizeof(unsigned long long), st));
+                for (int k = a; k < b; k++) CK(cudaEventRecord(ts[base_k + k], st));
+                if (form == RT_FP64)
+                    launch_transfer_fp64(xa, coef, grid, st);
+                else if (form == RT_UNPOL)
+                    launch_unpol(xa, grid, st);
+                else if (use_staged(c, form, coef, mod, jobs))
+                    launch_transfer_staged(xa, c->tmap, grid, st);
+                else
+                    launch_transfer_mixed(xa, coef, grid, st);
+                for (int k = a; k < b; k++) {
+                    CK(cudaEventRecord(te[base_k + k], st));
+                    launched[k] = 1;
+                }
+                CK(cudaGetLastError());
+                if (first < 0) first = base_k + a;
+                last = base_k + b - 1;
+                xf_launches++;
+                prev = a;
+                left -= b - a;
+                any = true;
+                may = false;  // the next launch waits until this one has started
+                a = b;
+            }
+            if (any || left == 0) continue;
+            if (q == cudaSuccess && !ready) {  // the geodesic has ended, and a chunk is still incomplete
+                cudaStreamSynchronize(st);
+                return RT_ERR_CUDA;
+            }
+            if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > kStreamWaitSeconds)
+                return RT_ERR_STALL;
+            std::this_thread::yield();
+        }
+    }
+    CK(cudaStreamWaitEvent(c->stream, ge[P - 1], 0));
+    if (last >= 0) CK(cudaStreamWaitEvent(c->stream, te[last], 0));  // the transfers run in order on st
+    CK(cudaEventRecord(c->ev[2], c->stream));
+    CK(cudaMemcpyAsync(c->h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->h_ctr->arena_next = std::max(arena_max, (unsigned long long)c->h_ctr->arena_next);
+    float g = 0.f, x = 0.f;
+    if (cudaEventElapsedTime(&g, gs[0], ge[P - 1]) != cudaSuccess) g = 0.f;
+    if (first >= 0 && cudaEventElapsedTime(&x, ts[first], te[last]) != cudaSuccess) x = 0.f;
+    cudaGetLastError();
+    c->last_ms_geo = g;
+    c->last_ms_xfer = x;
+    c->last_chunks = P * K;
+    c->last_pieces = P;
+    c->last_shape = 2;
+    c->last_geo_launches = P;
+    c->last_xf_launches = xf_launches;
+    c->last_blocks_total = ar.nblocks;
+    c->last_was_streamed = true;
     return RT_OK;
 }
 
@@ -576,14 +841,23 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
 // RT_MIXED. Synchronizes; the counters describe the whole batch.
 int render_jobs_overlap(rt_ctx *c, int form, const JobDev *d_jobs, const JobDev *h_jobs, int njobs, long long nrays) {
     const size_t per_ray = kPerRayBytes;
-    const int chunks = (int)std::min<long long>(64, std::max<long long>(2, nrays >> 17));
-    long long ws_rays = 2 * ((nrays + chunks - 1) / chunks) +
-                        2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
-    int rv = ensure_workspace(c, ws_rays, per_ray);
-    if (rv) return rv;
-    long long K = overlap_chunks(c, nrays, chunks, per_ray);
-    if (K < 0) return RT_ERR_NOMEM;
-    const int geo_grid = c->nsm, xf_grid = c->nsm * (form == RT_FP64 ? c->fp64_bps : c->mixed_bps);
+    const int chunks = (int)std::min<long long>(64, std::max<long long>(2, nrays >> kAutoChunkShift));
+    // streamed when the workspace can hold every ray's path, else in two halves
+    const int P = plan_pieces(c, nrays), Kp = P > 0 ? stream_chunks(nrays, P, 0, true) : 0;
+    const bool streamed = P > 0;
+    ChunkLayout L{nrays, (int)std::min<long long>(chunks, nrays), kAutoLastDiv};
+    if (!streamed) {
+        long long ws_rays = 2 * L.max_size() +
+                            2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
+        int rv = ensure_workspace(c, ws_rays, per_ray);
+        if (rv) return rv;
+        L = overlap_chunks(c, nrays, chunks, kAutoLastDiv, per_ray);
+        if (L.K == 0) return RT_ERR_NOMEM;
+    }
+    const long long K = L.K;
+    int rv = RT_OK;
+    const int xf_own = form == RT_FP64 ? c->fp64_bps : c->mixed_bps, geo_b = streamed ? kStreamGeoBlocks : 1;
+    const int geo_grid = c->nsm * geo_b, xf_grid = c->nsm * xf_beside_geo(c, form, geo_b, xf_own);
     // longest first, as for one image, once a batch of the same cameras has recorded its steps
     unsigned long long key = 1469598103934665603ull;  // FNV-1a over the cameras and integrator
     auto mix = [&](const void *v, size_t n) {
@@ -620,15 +894,22 @@ int render_jobs_overlap(rt_ctx *c, int form, const JobDev *d_jobs, const JobDev 
     }
     const int *list = nullptr;
     if (c->have_bsteps) {
-        if (c->border_K != K) {
-            launch_order_build(c->d_bsteps, nrays, (int)K, c->d_ohist, c->d_border, c->stream);
+        // streamed: one longest-first order, cut into contiguous chunks; halves: dealt
+        const ChunkLayout Lord = streamed ? ChunkLayout{nrays, P, 1} : L;
+        if (c->border_K != Lord.K || c->border_W != Lord.W) {
+            launch_order_build(c->d_bsteps, Lord, c->d_ohist, c->d_border, c->stream);
             CK(cudaGetLastError());
-            c->border_K = K;
+            c->border_K = Lord.K;
+            c->border_W = Lord.W;
         }
         list = c->d_border;
     }
-    rv = render_overlap(c, form, 0, h_jobs[0].cam, h_jobs[0].model, list, c->d_bsteps, nrays, K, nullptr, nullptr,
-                        nullptr, geo_grid, xf_grid, d_jobs, njobs);
+    if (streamed)
+        rv = render_streamed(c, form, 0, h_jobs[0].cam, h_jobs[0].model, list, c->d_bsteps, nrays, P, Kp, nullptr,
+                             nullptr, nullptr, geo_grid, xf_grid, c->nsm * xf_own, d_jobs, njobs);
+    else
+        rv = render_overlap(c, form, 0, h_jobs[0].cam, h_jobs[0].model, list, c->d_bsteps, L, nullptr, nullptr,
+                            nullptr, geo_grid, xf_grid, d_jobs, njobs);
     if (rv) return rv;
     c->last_rays = nrays;
     c->last_was_overlap = true;
@@ -668,33 +949,48 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     // transfer at its occupancy. Smaller images run one pass of each kernel, and so do RT_FP64
     // (its FP64 transfer competes with the geodesic for the same pipe) and RT_SURROGATE (the
     // network pass beside the geodesic measured slower than one pass: 859 against 536 ms).
-    int chunks = c->rcfg.chunks, geo_b = c->rcfg.geo_blocks_per_sm;
-    if (chunks == 0) {
+    int chunks = c->rcfg.chunks, geo_b = c->rcfg.geo_blocks_per_sm, W = c->rcfg.last_chunk_div;
+    const bool auto_shape = chunks == 0;
+    if (auto_shape)
         chunks = nrays >= (1ll << 19) && (form == RT_MIXED || form == RT_UNPOL)
-                     ? (int)std::min<long long>(16, std::max<long long>(4, nrays >> 17))
+                     ? (int)std::min<long long>(kAutoChunksMax, std::max<long long>(4, nrays >> kAutoChunkShift))
                      : 1;
-        if (chunks >= 2 && geo_b == 0) geo_b = 1;
-    }
     bool ovl = chunks >= 2 && nrays >= 2;
-    // the overlapped form holds two chunks at a time, each half with its own counters
-    long long ws_rays = nrays;
-    if (ovl)
-        ws_rays = 2 * ((nrays + chunks - 1) / chunks) +
-                  2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
-    int rv = ensure_workspace(c, ws_rays, per_ray);
-    if (rv) return rv;
-    long long K = 1;
-    // a workspace too small for kMaxChunks (256) overlapped chunks (a caller's, or a nearly full
-    // device) renders in one pass of each kernel per chunk instead
-    if (ovl && (K = overlap_chunks(c, nrays, chunks, per_ray)) < 0) {
-        ovl = false;
-        K = 1;
+    // the streamed shape when the workspace can hold every ray's path (not for the surrogate
+    // form, whose network pass runs over one chunk's arena); else two halves of the workspace
+    // that hold a chunk each, with their own counters
+    int rv = RT_OK, P = ovl && !sur ? plan_pieces(c, nrays) : 0, Kp = 0;
+    const bool streamed = P > 0;
+    ChunkLayout L{nrays, 1, 1};
+    if (streamed) {
+        // contiguous ranges of each piece's longest-first order; the automatic shape takes finer
+        // chunks and a second geodesic block per SM
+        Kp = stream_chunks(nrays, P, chunks, auto_shape);
+        if (geo_b == 0) geo_b = kStreamGeoBlocks;
+    } else {
+        if (ovl && geo_b == 0) geo_b = 1;
+        if (W == 0) W = auto_shape ? kAutoLastDiv : 1;
+        long long ws_rays = nrays;
+        if (ovl)
+            ws_rays = 2 * ChunkLayout{nrays, chunks, W}.max_size() +
+                      2 * (long long)((align_up(sizeof(Counters)) + 6 * kAlign + per_ray - 1) / per_ray) + 1;
+        rv = ensure_workspace(c, ws_rays, per_ray);
+        if (rv) return rv;
+        if (ovl) {
+            // a workspace too small for kMaxChunks (256) overlapped chunks (a caller's, or a
+            // nearly full device) renders in one pass of each kernel per chunk instead
+            L = overlap_chunks(c, nrays, chunks, W, per_ray);
+            if (L.K == 0) {
+                ovl = false;
+                L = ChunkLayout{nrays, 1, 1};
+            }
+        }
     }
 
-    // one-pass shape: as many rays per chunk as the workspace holds; the Kseq chunks take the
-    // rays in the same round-robin layout as the overlapped ones (chunk k from k (n / Kseq) +
-    // min(k, n % Kseq)), so that with the longest-first order every chunk holds the same mix
-    // of lengths and none outgrows the arena's per-ray budget
+    // one-pass shape: as many rays per chunk as the workspace holds; the Kseq chunks are those of
+    // the layout {n, Kseq, 1} (chunk k from k (n / Kseq) + min(k, n % Kseq)), so that with the
+    // longest-first order every chunk holds the same mix of lengths and none outgrows the
+    // arena's per-ray budget
     const size_t per_block = kBlockBytes + (sur ? (size_t)kBlockStates * 48 : 0);
     char *base = (char *)c->ws;
     Counters *ctr = (Counters *)base;
@@ -728,16 +1024,20 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
         rv = prepare_order(c, cam, npix_img);
         if (rv) return rv;
         steps_out = c->d_steps;
-        const long long Kord = ovl ? K : Kseq;
+        // streamed: one longest-first order, cut into contiguous chunks; halves and one pass: dealt
+        const ChunkLayout Lord = streamed ? ChunkLayout{npix_img, P, 1}
+                                 : ovl    ? ChunkLayout{npix_img, L.K, L.W}
+                                          : ChunkLayout{npix_img, (int)Kseq, 1};
         if (!c->have_steps && nrays >= (1ll << 18)) {
             rv = probe_steps(c, cam, ctr, rec, chunk, ar);
             if (rv) return rv;
         }
         if (c->have_steps) {
-            if (c->order_K != Kord) {
-                launch_order_build(c->d_steps, npix_img, (int)Kord, c->d_ohist, c->d_order, c->stream);
+            if (c->order_K != Lord.K || c->order_W != Lord.W) {
+                launch_order_build(c->d_steps, Lord, c->d_ohist, c->d_order, c->stream);
                 CK(cudaGetLastError());
-                c->order_K = Kord;
+                c->order_K = Lord.K;
+                c->order_W = Lord.W;
             }
             ray_list = c->d_order;
         }
@@ -768,18 +1068,27 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     }
 
     const int xf_max = form == RT_FP64 ? c->fp64_bps : c->mixed_bps;
-    const int geo_grid = c->nsm * (geo_b > 0 ? geo_b : c->geo_bps);
-    const int xf_grid =
-        c->nsm * (c->rcfg.xfer_blocks_per_sm > 0 ? std::min(c->rcfg.xfer_blocks_per_sm, xf_max) : xf_max);
+    const int geo_bps = geo_b > 0 ? geo_b : c->geo_bps;
+    const int geo_grid = c->nsm * geo_bps;
+    const int xf_own = c->rcfg.xfer_blocks_per_sm > 0 ? std::min(c->rcfg.xfer_blocks_per_sm, xf_max) : xf_max;
+    // overlapped: no more transfer blocks per SM than fit beside the geodesic's
+    const int xf_grid = c->nsm * (ovl ? xf_beside_geo(c, form, geo_bps, xf_own) : xf_own);
     c->last_was_overlap = false;
+    c->last_was_streamed = false;
     if (ovl) {
-        rv = render_overlap(c, form, coef, cam, mod, ray_list, steps_out, nrays, K, d_out, d_status, d_depth,
-                            geo_grid, xf_grid);
+        if (streamed)
+            rv = render_streamed(c, form, coef, cam, mod, ray_list, steps_out, nrays, P, Kp, d_out, d_status, d_depth,
+                                 geo_grid, xf_grid, c->nsm * xf_own);
+        else
+            rv = render_overlap(c, form, coef, cam, mod, ray_list, steps_out, L, d_out, d_status, d_depth, geo_grid,
+                                xf_grid);
         if (rv) return rv;
         c->last_was_overlap = true;
     } else {
         CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), c->stream));
         c->last_chunks = (int)Kseq;
+        c->last_shape = 0;
+        c->last_geo_launches = c->last_xf_launches = (int)Kseq;
         const long long base_n = nrays / Kseq, extra = nrays % Kseq;
         for (long long k = 0; k < Kseq; k++) {
             const long long o = k * base_n + std::min(k, extra), n = base_n + (k < extra ? 1 : 0);
@@ -975,6 +1284,7 @@ int rt_set_render_config(rt_ctx *c, const rt_render_config *cfg) {
     if (cfg->xfer_blocks_per_sm < 0 || cfg->xfer_blocks_per_sm > std::max(c->mixed_bps, c->fp64_bps))
         return RT_ERR_INVALID;
     if (cfg->chunks < 0 || cfg->chunks > rt_ctx::kMaxChunks) return RT_ERR_INVALID;
+    if (cfg->last_chunk_div < 0 || cfg->last_chunk_div > 16) return RT_ERR_INVALID;
     c->rcfg = *cfg;
     return RT_OK;
 }
@@ -1007,6 +1317,9 @@ int rt_last_counters(rt_ctx *c, rt_counters *out) {
         out->ms_total = c->last_ms_total;
     } else {
         out->chunks = (uint32_t)c->last_chunks;
+        out->shape = (uint32_t)c->last_shape;
+        out->geodesic_launches = (uint32_t)c->last_geo_launches;
+        out->transfer_launches = (uint32_t)c->last_xf_launches;
         if (c->last_was_overlap) {
             out->ms_geodesic = c->last_ms_geo;
             out->ms_transfer = c->last_ms_xfer;
@@ -1017,6 +1330,29 @@ int rt_last_counters(rt_ctx *c, rt_counters *out) {
         if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[2]) == cudaSuccess) out->ms_total = ms;
     }
     cudaGetLastError();
+    return RT_OK;
+}
+
+int rt_last_timeline(rt_ctx *c, float *out, int cap, int *n) {
+    if (!c || !n || cap < 0 || (cap > 0 && !out)) return RT_ERR_INVALID;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    const int K = c->last_was_overlap ? c->last_chunks : 0;
+    cudaEvent_t *gs = c->oev, *ge = c->oev + rt_ctx::kMaxChunks, *ts = c->oev + 2 * rt_ctx::kMaxChunks,
+                *te = c->oev + 3 * rt_ctx::kMaxChunks;
+    const int per_piece = c->last_was_streamed ? std::max(1, K / std::max(1, c->last_pieces)) : 1;
+    for (int k = 0; k < std::min(K, cap); k++) {
+        // the streamed shape has one geodesic launch per piece for all its chunks
+        const int g = c->last_was_streamed ? k / per_piece : k;
+        cudaEvent_t ev[4] = {gs[g], ge[g], ts[k], te[k]};
+        for (int j = 0; j < 4; j++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, gs[0], ev[j]) != cudaSuccess) ms = 0.f;
+            out[4 * k + j] = ms;
+        }
+    }
+    cudaGetLastError();
+    *n = K;
     return RT_OK;
 }
 

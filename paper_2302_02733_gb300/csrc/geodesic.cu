@@ -5,6 +5,8 @@
 // global queue (warp-aggregated atomics), so long photon-ring rays do not hold a warp's
 // other lanes idle. Every state is written to a block arena, 64 B per state: each lane
 // writes two full 32 B sectors. The FP64 pipe bounds this kernel.
+#include <algorithm>
+
 #include "geodesic.cuh"
 
 namespace prt {
@@ -98,6 +100,17 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
             if (p.steps_out) p.steps_out[pix] = (uint16_t)min(n, 65535);  // by pixel, or (JOBS) by global id
             my_steps += (unsigned long long)n;
             atomicAdd(&p.ctr->n_status[status], 1u);
+            if (p.chunk_done) {
+                // release this ray's states and record to the chunk's transfer: the fence orders
+                // them before the count; the lane whose count completes the chunk fences again
+                // (acquiring the others' and releasing to the host) and raises the flag
+                __threadfence();
+                const int k = p.layout.chunk_of(ray);
+                if (atomicAdd(&p.chunk_done[k], 1u) + 1u == (unsigned)p.layout.size(k)) {
+                    __threadfence_system();
+                    *(volatile unsigned *)&p.chunk_flag[k] = 1u;
+                }
+            }
             live = false;
         }
     }
@@ -125,6 +138,19 @@ void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s) {
         geodesic_kernel<true><<<grid, kGeoThreads, 0, s>>>(a);
     else
         geodesic_kernel<false><<<grid, kGeoThreads, 0, s>>>(a);
+}
+
+static int func_regs(const void *f) {
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, f) != cudaSuccess) {
+        cudaGetLastError();
+        return 255;
+    }
+    return a.numRegs;
+}
+
+int geodesic_regs() {
+    return std::max(func_regs((const void *)geodesic_kernel<false>), func_regs((const void *)geodesic_kernel<true>));
 }
 
 int geodesic_blocks_per_sm() {

@@ -1,8 +1,8 @@
 // Longest-first ray order. A persistent kernel's launch ends when its slowest lanes finish
 // their last rays; if those rays are long (the photon ring), the SMs idle meanwhile. The step
 // counts of a previous render of the same camera (geodesics depend on the camera only) give
-// the order: a counting sort by step count, descending, dealt round-robin to the chunks so
-// that every chunk holds the same mix of lengths, longest first. The image does not depend on
+// the order: a counting sort by step count, descending, dealt to the chunks in rounds
+// (ChunkLayout) so that every chunk holds the same mix of lengths, longest first. The image does not depend on
 // the order: every ray takes the same arithmetic.
 #include <algorithm>
 
@@ -37,13 +37,12 @@ __global__ void order_scan_kernel(unsigned *hist) {
     }
 }
 
-// rank s (unique within the sort) -> chunk k = s % K, position s / K in it
-__global__ void order_scatter_kernel(const uint16_t *steps, long long n, int K, unsigned *offs, int *order) {
-    const long long base = n / K, extra = n % K;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+// rank s (unique within the sort) -> its place in the chunk layout
+__global__ void order_scatter_kernel(const uint16_t *steps, ChunkLayout L, unsigned *offs, int *order) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < L.n;
+         p += (long long)gridDim.x * blockDim.x) {
         long long s = atomicAdd(&offs[order_bucket(steps[p])], 1u);
-        long long k = s % K, q = s / K;
-        order[k * base + min(k, extra) + q] = (int)p;
+        order[L.place(s)] = (int)p;
     }
 }
 
@@ -79,12 +78,12 @@ void launch_steps_fill(uint16_t *steps, int nx, int ny, int S, cudaStream_t s) {
     steps_fill_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(steps, nx, ny, S);
 }
 
-void launch_order_build(const uint16_t *steps, long long n, int K, unsigned *hist, int *order, cudaStream_t s) {
-    int grid = (int)std::min<long long>((n + 255) / 256, 1024);
+void launch_order_build(const uint16_t *steps, const ChunkLayout &L, unsigned *hist, int *order, cudaStream_t s) {
+    int grid = (int)std::min<long long>((L.n + 255) / 256, 1024);
     cudaMemsetAsync(hist, 0, kOrderBuckets * sizeof(unsigned), s);
-    order_hist_kernel<<<grid, 256, 0, s>>>(steps, n, hist);
+    order_hist_kernel<<<grid, 256, 0, s>>>(steps, L.n, hist);
     order_scan_kernel<<<1, 32, 0, s>>>(hist);
-    order_scatter_kernel<<<grid, 256, 0, s>>>(steps, n, K, hist, order);
+    order_scatter_kernel<<<grid, 256, 0, s>>>(steps, L, hist, order);
 }
 
 }  // namespace prt

@@ -107,7 +107,10 @@ int rt_render_static(rt_ctx *c, int form, void *out_iquv, uint8_t *status) {
     c->last_blocks_total = nblocks;
     c->last_was_batch = false;
     c->last_was_overlap = false;  // one pass of each kernel: the counters report this call
+    c->last_was_streamed = false;
     c->last_chunks = 1;
+    c->last_shape = 0;
+    c->last_geo_launches = c->last_xf_launches = 1;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     return RT_OK;
 }

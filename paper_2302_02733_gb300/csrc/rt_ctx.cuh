@@ -50,6 +50,8 @@ struct rt_ctx {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     long long last_rays = 0, last_blocks_total = 0;
     int geo_bps = 1, fp64_bps = 1, mixed_bps = 1;
+    // registers per thread of the geodesic and transfer kernels, and per SM
+    int geo_regs = 255, xf_regs_fp64 = 255, xf_regs_mixed = 255, regs_per_sm = 65536;
     float last_ms_total = 0.f;
     bool last_was_batch = false;
 
@@ -61,6 +63,12 @@ struct rt_ctx {
     cudaEvent_t oev[4 * kMaxChunks] = {};
     bool have_oev = false;
     prt::Counters *h_ctr2 = nullptr;  // pinned: the second half's counters
+    // streamed overlapped shape: per chunk the completion flag the geodesic raises (mapped
+    // pinned host memory, and its device address)
+    unsigned *h_flags = nullptr, *d_flags = nullptr;
+    bool last_was_streamed = false;
+    int last_pieces = 1;  // pieces of the last streamed render (each last_chunks / last_pieces chunks)
+    int last_shape = 0, last_geo_launches = 0, last_xf_launches = 0;  // as rt_counters
 
     // longest-first ray order (order.cu), from the step counts of the last full render of the
     // same camera and integrator
@@ -71,6 +79,7 @@ struct rt_ctx {
     double order_key[8] = {};     // camera and integrator the steps belong to
     bool have_steps = false;
     long long order_K = 0;        // chunks d_order is dealt to; 0: not built
+    int order_W = 1;              // and the share divisor of its last chunk (ChunkLayout)
     int *d_probe = nullptr;       // the probe's pixel list (a new camera's predicted order)
     long long probe_cap = 0;
     bool steps_probed = false;    // d_steps holds the probe's predictions, not recorded counts
@@ -78,6 +87,7 @@ struct rt_ctx {
     uint16_t *d_bsteps = nullptr;
     int *d_border = nullptr;
     long long border_cap = 0, border_K = 0;
+    int border_W = 1;
     unsigned long long bkey = 0;  // hash of the cameras and integrator the steps belong to
     bool have_bsteps = false;
     float last_ms_geo = 0.f, last_ms_xfer = 0.f;

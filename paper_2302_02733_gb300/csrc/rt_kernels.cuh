@@ -11,6 +11,49 @@ constexpr int kXferThreads = 128;
 
 struct JobDev;
 
+// How n rays are split into K consecutive chunks: the last chunk takes 1/W of a regular one's
+// share (W = 1: equal chunks). Ranks of the longest-first sort are dealt in rounds of
+// P = (K - 1) W + 1: in each round chunk k < K - 1 takes W consecutive ranks and the last chunk
+// one, so every chunk holds the same mix of lengths, longest first. A final partial round
+// (n % P ranks) fills the regular chunks in turn.
+struct ChunkLayout {
+    long long n;
+    int K, W;
+    __host__ __device__ long long period() const { return (long long)(K - 1) * W + 1; }
+    __host__ __device__ long long size(int k) const {
+        const long long P = period(), R = n / P, rem = n % P;
+        if (k < K - 1) {
+            const long long e = rem - (long long)k * W;
+            return R * W + (e < 0 ? 0 : (e > W ? W : e));
+        }
+        return R;  // rem < P: a partial round never reaches the last chunk
+    }
+    __host__ __device__ long long offset(int k) const {
+        const long long P = period(), R = n / P, rem = n % P, kw = (long long)k * W;
+        return (long long)k * R * W + (rem < kw ? rem : kw);
+    }
+    // the largest chunk (the first)
+    __host__ __device__ long long max_size() const { return size(0); }
+    // the chunk holding index t (0 <= t < n)
+    __host__ __device__ int chunk_of(long long t) const {
+        int lo = 0, hi = K - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offset(mid) <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        return lo;
+    }
+    // rank s of the sort -> its index in the order array
+    __host__ __device__ long long place(long long s) const {
+        const long long P = period(), r = s / P, j = s % P;
+        if (j < (long long)(K - 1) * W) return offset((int)(j / W)) + r * W + j % W;
+        return offset(K - 1) + r;
+    }
+};
+
 struct GeoArgs {
     Camera cam;
     const double *sctab;  // (theta, sin, cos) table of the FP64 geodesic, 1024 entries
@@ -23,6 +66,12 @@ struct GeoArgs {
     uint16_t *steps_out;  // optional: per pixel (row-major), the ray's RK4 step count (capped at 65535)
     const JobDev *jobs;   // optional: a table of images; global ray ids then run over all of them, the
     int njobs;            // order list holds global ray ids and steps_out is indexed by them
+    // optional (streamed overlapped shape): the rays' chunks; every ray that stops adds one to
+    // chunk_done of its chunk, and the lane that completes a chunk sets its chunk_flag (mapped
+    // host memory) after a system-scope fence
+    unsigned *chunk_done;
+    unsigned *chunk_flag;
+    ChunkLayout layout;
 };
 
 struct XferArgs {
@@ -130,11 +179,10 @@ void launch_kappa_quad(const KappaTables &T, const double *in, double *out, long
 
 void launch_geodesic(const GeoArgs &a, int grid, cudaStream_t s);
 // Longest-first ray order from the step counts of a previous render of the same camera:
-// order[i] is the pixel of ray i, by step count descending (16-step buckets), dealt round-robin
-// to K chunks; chunk k holds n / K + (k < n % K) rays from index k (n / K) + min(k, n % K).
-// hist: kOrderBuckets unsigned of scratch.
+// order[i] is the pixel of ray i, by step count descending (16-step buckets), placed by the
+// layout L into its chunks. hist: kOrderBuckets unsigned of scratch.
 constexpr int kOrderBuckets = 1024;
-void launch_order_build(const uint16_t *steps, long long n, int K, unsigned *hist, int *order, cudaStream_t s);
+void launch_order_build(const uint16_t *steps, const ChunkLayout &L, unsigned *hist, int *order, cudaStream_t s);
 // The probe of a new camera: list[i] = the pixel at the centre of S x S block i (row-major over
 // blocks, clipped to the image); then every pixel takes its block's probe's step count.
 void launch_probe_list(int *list, int nx, int ny, int S, cudaStream_t s);
@@ -162,5 +210,10 @@ int geodesic_blocks_per_sm();
 int transfer_blocks_per_sm_fp64();
 int transfer_blocks_per_sm_mixed();
 int transfer_blocks_per_sm_staged();
+// registers per thread of a kernel (cudaFuncGetAttributes), for the overlapped shape's sharing
+// of an SM's register file between one geodesic block and the transfer blocks beside it
+int geodesic_regs();
+int transfer_regs_fp64();
+int transfer_regs_mixed();  // the largest of the mixed, staged and unpolarized transfers
 
 }  // namespace prt

@@ -606,7 +606,12 @@ __device__ __forceinline__ R fmks_y(const GridModel &g, R w, R th, R mu) {
         x10 = R(T[(iw + 1) * kX2TabT + it]), x11 = R(T[(iw + 1) * kX2TabT + it + 1]);
     }
     R y = (R(1) - tw) * ((R(1) - tt) * x00 + tt * x01) + tw * ((R(1) - tt) * x10 + tt * x11) - R(0.5);
-    const int iters = sizeof(R) == 8 ? 3 : 2;
+    // the bilinear table guess is within 1.3e-5 of the root in y (a cell is 1/n2 = 7.8e-3); one
+    // Newton step takes that below 1e-9 and a second to FP64's resolution. FP32 takes two as
+    // well: after one the result still depends on how the guess was rounded, which differs
+    // between the kernels this is inlined into (the single, batched and staged transfers give
+    // bit-identical mixed images only after the second)
+    const int iters = 2;
 #pragma unroll
     for (int k = 0; k < iters; k++) {
         R d;

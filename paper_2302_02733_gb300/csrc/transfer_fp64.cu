@@ -14,6 +14,15 @@ void launch_transfer_fp64(const XferArgs &a, int coef, int grid, cudaStream_t s)
         default: break;
     }
 }
+int transfer_regs_fp64() {
+    cudaFuncAttributes a{}, b{};
+    if (cudaFuncGetAttributes(&a, (const void *)transfer_kernel<double, double, 0>) != cudaSuccess ||
+        cudaFuncGetAttributes(&b, (const void *)transfer_kernel<double, double, 0, true>) != cudaSuccess) {
+        cudaGetLastError();
+        return 255;
+    }
+    return a.numRegs > b.numRegs ? a.numRegs : b.numRegs;
+}
 int transfer_blocks_per_sm_fp64() {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transfer_kernel<double, double>, kXferThreads, 0) != cudaSuccess)

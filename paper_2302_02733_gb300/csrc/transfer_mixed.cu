@@ -1,5 +1,7 @@
 // Mixed form of the transfer kernel: the FP64 geodesic path is read back, and the plasma
 // fetch, coefficients and transfer run in float.
+#include <algorithm>
+
 #include "transfer_kernel.cuh"
 
 namespace prt {
@@ -32,6 +34,21 @@ void launch_unpol(const XferArgs &a, int grid, cudaStream_t s) {
 }
 void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s) {
     sur_features_pass<float><<<grid, kXferThreads, 0, s>>>(a);
+}
+static int func_regs(const void *f) {
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, f) != cudaSuccess) {
+        cudaGetLastError();
+        return 255;
+    }
+    return a.numRegs;
+}
+int transfer_regs_mixed() {
+    int r = func_regs((const void *)transfer_kernel<float, float, 0>);
+    r = std::max(r, func_regs((const void *)transfer_kernel<float, float, 0, true>));
+    r = std::max(r, func_regs((const void *)transfer_kernel_staged<0>));
+    r = std::max(r, func_regs((const void *)unpol_kernel<float>));
+    return std::max(r, func_regs((const void *)unpol_kernel<float, true>));
 }
 int transfer_blocks_per_sm_mixed() {
     int n = 0;

@@ -53,7 +53,8 @@ class rt_counters(C.Structure):
                 ("arena_blocks_total", C.c_uint64), ("n_horizon", C.c_uint32), ("n_escape", C.c_uint32),
                 ("n_nmax", C.c_uint32), ("n_nan", C.c_uint32), ("n_overflow", C.c_uint32),
                 ("ms_geodesic", C.c_float), ("ms_transfer", C.c_float), ("ms_total", C.c_float),
-                ("chunks", C.c_uint32)]
+                ("chunks", C.c_uint32), ("shape", C.c_uint32), ("geodesic_launches", C.c_uint32),
+                ("transfer_launches", C.c_uint32)]
 
 
 class rt_mlp_norm(C.Structure):
@@ -83,7 +84,8 @@ _VP = C.c_void_p
 
 
 class rt_render_config(C.Structure):
-    _fields_ = [("geo_blocks_per_sm", C.c_int), ("xfer_blocks_per_sm", C.c_int), ("chunks", C.c_int)]
+    _fields_ = [("geo_blocks_per_sm", C.c_int), ("xfer_blocks_per_sm", C.c_int), ("chunks", C.c_int),
+                ("last_chunk_div", C.c_int)]
 
 
 def lib():
@@ -107,6 +109,7 @@ def lib():
         L.rt_image_stats.argtypes = [_VP, _VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                      C.POINTER(C.c_double)]
         L.rt_last_counters.argtypes = [_VP, C.POINTER(rt_counters)]
+        L.rt_last_timeline.argtypes = [_VP, _VP, C.c_int, C.POINTER(C.c_int)]
         L.rt_render_static.argtypes = [_VP, C.c_int, _VP, _VP]
         L.rt_render_depths.argtypes = [_VP, C.c_int, _VP, _VP, _VP]
         L.rt_kappa_coeffs.argtypes = [_VP, _VP, C.c_longlong, _VP]
@@ -499,8 +502,9 @@ def rt_get_grid_fetch(ctx) -> int:
     return m.value
 
 
-def rt_set_render_config(ctx, geo_blocks_per_sm: int = 0, xfer_blocks_per_sm: int = 0, chunks: int = 0):
-    cfg = rt_render_config(geo_blocks_per_sm, xfer_blocks_per_sm, chunks)
+def rt_set_render_config(ctx, geo_blocks_per_sm: int = 0, xfer_blocks_per_sm: int = 0, chunks: int = 0,
+                         last_chunk_div: int = 0):
+    cfg = rt_render_config(geo_blocks_per_sm, xfer_blocks_per_sm, chunks, last_chunk_div)
     _check(lib().rt_set_render_config(ctx, C.byref(cfg)), "rt_set_render_config")
 
 
@@ -534,6 +538,15 @@ def rt_last_counters(ctx) -> dict:
     c = rt_counters()
     _check(lib().rt_last_counters(ctx, C.byref(c)), "rt_last_counters")
     return {k: getattr(c, k) for k, _ in rt_counters._fields_}
+
+
+def rt_last_timeline(ctx, cap: int = 256) -> list:
+    """Per chunk of the last overlapped render: (geodesic start, geodesic end, transfer start,
+    transfer end) in ms from the first geodesic start; [] when it was not overlapped."""
+    buf = (C.c_float * (4 * cap))()
+    n = C.c_int(0)
+    _check(lib().rt_last_timeline(ctx, buf, cap, C.byref(n)), "rt_last_timeline")
+    return [tuple(buf[4 * k:4 * k + 4]) for k in range(min(n.value, cap))]
 
 
 def rt_error_string(code: int) -> str:

@@ -46,6 +46,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.rt_batch_autotune(None, 0, None, 0, None) == polrt.RT_ERR_INVALID
     assert lib.rt_set_batch_config(None, 0, None) == polrt.RT_ERR_INVALID
     assert lib.rt_render_depths(None, 0, None, None, None) == polrt.RT_ERR_INVALID
+    assert lib.rt_last_timeline(None, None, 0, None) == polrt.RT_ERR_INVALID
 
 
 def test_create_without_gpu_reports_an_error():

@@ -111,6 +111,8 @@ def test_batch_rejects_bad_jobs(rt, synth):
 
 
 def test_image_library_96(rt, ora, synth, torus_grid):
+    """The image library (96 images, N in {128, 256, 512}; the batched form's benchmark) against
+    the oracle: six full 128^2 images and a 64 x 64 strided subsample of each of the others."""
     polrt, ctx = rt
     prims, g = torus_grid
     polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
@@ -138,10 +140,10 @@ def test_image_library_96(rt, ora, synth, torus_grid):
             ref = ora.render_image(ora.camera(c), om)[0]
             gpu = o.double().cpu().numpy()
             ferrs.append(abs(gpu[..., 0].sum() / ref[..., 0].sum() - 1))
-        else:
-            q = (np.arange(16) * (j.n // 16) + j.n // 32)
+        else:  # the 64 x 64 strided subsample of pixel centres
+            q = (np.arange(64) * (j.n // 64) + j.n // 128)
             iy, ix = np.meshgrid(q, q, indexing="ij")
-            ref = ora.render_pixels(ora.camera(c), om, ix.ravel(), iy.ravel())[0].reshape(16, 16, 4)
+            ref = ora.render_pixels(ora.camera(c), om, ix.ravel(), iy.ravel())[0].reshape(64, 64, 4)
             gpu = o[q][:, q].double().cpu().numpy()
         assert np.isfinite(gpu).all()
         errs.append(rel_err(gpu, ref).ravel())

@@ -1,8 +1,10 @@
-"""The overlapped launch shape (geodesic of one ray chunk beside the transfer of the previous
-chunk, on two streams and two halves of the workspace) against one pass of each kernel: every
-ray takes the same arithmetic, so images, depth maps, status codes and step and point counts
-are identical, for every form and for chunk counts that do and do not divide the rays. Also the
-shape's argument checks and the automatic choice (one pass below 2^19 rays)."""
+"""The overlapped launch shapes against one pass of each kernel: streamed (one geodesic launch
+over all rays, each chunk's transfer launched as the chunk completes) and in two halves of the
+workspace (the geodesic of one chunk beside the transfer of the previous). Every ray takes the
+same arithmetic, so images, depth maps, status codes and step and point counts are identical,
+for every form, for chunk counts that do and do not divide the rays and for a smaller last
+chunk. Also the per-chunk timeline, the shape's argument checks and the automatic choice (one
+pass below 2^19 rays)."""
 import numpy as np
 import pytest
 
@@ -40,43 +42,105 @@ def render(polrt, ctx, form, cam, cfg, depth=False):
     return out, st, dep, polrt.rt_last_counters(ctx)
 
 
+def check_timeline(tl, K, shape):
+    """The launch order of the overlapped shapes, read from the per-chunk events.
+    Streamed (shape 2): the chunks of a piece report the piece's one geodesic launch; a transfer
+    covers a run of complete chunks of one piece (which report the same launch), transfers run
+    one after another on their stream, and a piece's geodesic starts after the previous piece's
+    transfers have ended. Two halves (shape 1): each stream runs its launches in order, a
+    transfer starts after its chunk's geodesic, and a geodesic after the transfer that last
+    used its half (chunk k - 2)."""
+    assert len(tl) == K
+    eps = 1e-3  # event resolution, ms
+    assert tl[0][0] == 0.0
+    for k, (gs, ge, ts, te) in enumerate(tl):
+        assert ge >= gs - eps and te >= ts - eps and ts >= -eps, (k, tl[k])
+    if shape == 2:
+        runs = sorted((t[2], t[3]) for t in tl)
+        for (s0, e0), (s1, e1) in zip(runs, runs[1:]):
+            same = abs(s1 - s0) < 0.01 and abs(e1 - e0) < 0.01  # chunks of one launch
+            assert same or s1 >= e0 - eps, (s0, e0, s1, e1)
+        pieces = sorted({(t[0], t[1]) for t in tl})
+        for (g0, g1) in pieces:
+            mine = [t for t in tl if (t[0], t[1]) == (g0, g1)]
+            assert all(t[2] >= g0 - eps for t in mine)
+            later = [t for t in tl if t[0] > g0 + eps]
+            if later:
+                assert min(t[0] for t in later) >= max(t[3] for t in mine) - eps
+        return len(pieces)
+    for k, (gs, ge, ts, te) in enumerate(tl):
+        assert ts >= ge - eps, (k, tl[k])
+        if k >= 1:
+            assert gs >= tl[k - 1][1] - eps and ts >= tl[k - 1][3] - eps, k
+        if k >= 2:
+            assert gs >= tl[k - 2][3] - eps, k
+    return 0
+
+
 def test_overlapped_render_is_identical(rt, synth, torus_grid):
+    """Streamed in one piece (the library's workspace holds every path), streamed in three
+    pieces (a caller's workspace of 0.45 of the image's), and in two halves (a caller's
+    workspace of 1/80 of it: a piece would hold under 1/64 of the rays), with equal chunks and,
+    in halves, with a smaller last chunk."""
     polrt, ctx = rt
     prims, g = torus_grid
     cam = synth.Camera(incl_deg=20.0, nx=200, ny=160)
     polrt.rt_set_integrator(ctx, 0.05, 20000)
     polrt.rt_set_camera(ctx, cam)
     polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
+    shapes = ((1.0, ((1, 0, 4), (2, 2, 3), (0, 0, 2), (1, 1, 7))),
+              (0.45, ((2, 0, 4), (1, 1, 7))),
+              (1 / 80, ((1, 0, 4), (1, 1, 7, 4))))
     try:
         for form, depth in ((polrt.RT_MIXED, True), (polrt.RT_FP64, False), (polrt.RT_UNPOL, False)):
             ref, st0, d0, c0 = render(polrt, ctx, form, cam, (0, 0, 1), depth)
-            assert c0["chunks"] == 1 and torch.isfinite(ref).all()
-            for cfg in ((1, 0, 4), (2, 2, 3), (0, 0, 2), (1, 1, 7)):
-                out, st, dep, c = render(polrt, ctx, form, cam, cfg, depth)
-                assert c["chunks"] == cfg[2], (form, cfg)
-                assert torch.equal(out, ref), (form, cfg)
-                assert torch.equal(st, st0), (form, cfg)
-                if depth:
-                    assert torch.equal(dep, d0), (form, cfg)
-                for k in ("rays", "steps", "points", "emitting_points", "n_horizon", "n_escape", "n_nmax"):
-                    assert c[k] == c0[k], (form, cfg, k)
-                assert c["n_overflow"] == 0 and c["ms_geodesic"] > 0 and c["ms_transfer"] > 0
+            assert c0["chunks"] == 1 and c0["shape"] == 0 and torch.isfinite(ref).all()
+            for frac, cfgs in shapes:
+                if frac < 1.0:
+                    ws = torch.empty(int(frac * polrt.rt_workspace_hint(ctx)), dtype=torch.uint8, device="cuda")
+                    polrt.rt_set_workspace(ctx, ws)
+                for cfg in cfgs:
+                    out, st, dep, c = render(polrt, ctx, form, cam, cfg, depth)
+                    assert torch.equal(out, ref), (form, frac, cfg)
+                    assert torch.equal(st, st0), (form, frac, cfg)
+                    if depth:
+                        assert torch.equal(dep, d0), (form, frac, cfg)
+                    for k in ("rays", "steps", "points", "emitting_points", "n_horizon", "n_escape", "n_nmax"):
+                        assert c[k] == c0[k], (form, cfg, k)
+                    assert c["n_overflow"] == 0 and c["ms_geodesic"] > 0 and c["ms_transfer"] > 0
+                    tl = polrt.rt_last_timeline(ctx)
+                    if frac == 1.0:
+                        assert c["shape"] == 2 and c["chunks"] == cfg[2] and c["geodesic_launches"] == 1
+                        assert check_timeline(tl, c["chunks"], 2) == 1
+                    elif frac > 0.1:
+                        assert c["shape"] == 2 and c["chunks"] == 3 * cfg[2] and c["geodesic_launches"] == 3
+                        assert check_timeline(tl, c["chunks"], 2) == 3
+                    else:
+                        assert c["shape"] == 1 and c["chunks"] >= 160 and c["geodesic_launches"] == c["chunks"]
+                        check_timeline(tl, c["chunks"], 1)
+                    assert 1 <= c["transfer_launches"] <= c["chunks"]
+                if frac < 1.0:
+                    polrt.rt_set_workspace(ctx, None)
         # automatic shape: one pass of each kernel for an image this small
         render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 0))
         assert polrt.rt_last_counters(ctx)["chunks"] == 1
+        assert polrt.rt_last_timeline(ctx) == []
     finally:
+        polrt.rt_set_workspace(ctx, None)
         polrt.rt_set_render_config(ctx, 0, 0, 0)
 
 
 def test_render_config_checks(rt):
     polrt, ctx = rt
-    for bad in ((0, 0, 257), (0, 0, -1), (99, 0, 0), (0, 99, 0), (-1, 0, 0)):
+    for bad in ((0, 0, 257), (0, 0, -1), (99, 0, 0), (0, 99, 0), (-1, 0, 0), (0, 0, 4, 17), (0, 0, 4, -1)):
         with pytest.raises(polrt.PolrtError):
             polrt.rt_set_render_config(ctx, *bad)
-    polrt.rt_set_render_config(ctx, 1, 2, 8)
-    assert polrt.rt_get_render_config(ctx) == {"geo_blocks_per_sm": 1, "xfer_blocks_per_sm": 2, "chunks": 8}
+    polrt.rt_set_render_config(ctx, 1, 2, 8, 4)
+    assert polrt.rt_get_render_config(ctx) == {"geo_blocks_per_sm": 1, "xfer_blocks_per_sm": 2, "chunks": 8,
+                                               "last_chunk_div": 4}
     polrt.rt_set_render_config(ctx, 0, 0, 0)
-    assert polrt.rt_get_render_config(ctx) == {"geo_blocks_per_sm": 0, "xfer_blocks_per_sm": 0, "chunks": 0}
+    assert polrt.rt_get_render_config(ctx) == {"geo_blocks_per_sm": 0, "xfer_blocks_per_sm": 0, "chunks": 0,
+                                               "last_chunk_div": 0}
 
 
 def test_overlapped_surrogate_is_identical(rt, synth, torus_grid):

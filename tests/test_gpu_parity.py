@@ -127,8 +127,8 @@ def test_grid_fp64_small_images(rt, ora, synth, torus_grid, nx, ny):
 
 def test_grid_fp64_1024_sampled(rt, ora, synth, torus_grid):
     """The benchmark workload (torus grid, 1024x1024, i = 20 deg) at full size, in the launch
-    shapes the benchmark times (automatic: one pass for the FP64 form, 8 overlapped chunks for
-    the mixed form, rays longest first from the second render on); the oracle checks 256
+    shapes the benchmark times (automatic: one pass for the FP64 form, the streamed overlapped
+    shape for the mixed form, rays longest first from the second render on); the oracle checks 256
     seeded pixels one by one. The FP64 form is held to 1e-9 outside the sensitivity mask; the mixed
     form (the benchmark's form) to 1e-3 on every sampled pixel and 1e-5 at the median (on the
     whole image it measures p99 9e-5, max 8e-4 against the FP64 form)."""
@@ -149,7 +149,9 @@ def test_grid_fp64_1024_sampled(rt, ora, synth, torus_grid):
     assert err[~mask].max() <= 1e-9, err[~mask].max()
     assert cnt["n_overflow"] == 0 and cnt["rays"] == 1024 * 1024 and cnt["chunks"] == 1
     rc, mix, st_m, cnt_m = gpu_render(rt, cam, polrt.grid_model(torch.from_numpy(prims).cuda(), g), polrt.RT_MIXED)
-    assert rc == 0 and cnt_m["chunks"] == 8 and np.array_equal(st_m, st)
+    tl = polrt.rt_last_timeline(rt[1])
+    streamed = len(tl) >= 2 and all(t[0] == 0.0 and t[1] == tl[0][1] for t in tl)  # one geodesic launch
+    assert rc == 0 and cnt_m["chunks"] == len(tl) and streamed and np.array_equal(st_m, st)
     err_m = np.abs(mix[iy, ix] - ref).max(axis=-1) / scale
     print(f"mixed 1024 sampled: median {np.median(err_m):.1e} max {err_m.max():.1e}")
     assert err_m.max() <= 1e-3 and np.median(err_m) <= 1e-5
