@@ -132,8 +132,9 @@ struct DK {
 // table of (theta_k, sin theta_k, cos theta_k) at spacing h = 1.5 pi / 1023 over
 // [-pi/4, 5 pi/4] (24 KB, small enough for shared memory), delta = theta - theta_k
 // (|delta| <= h/2 < 2.4e-3), then sin(theta_k + delta) = s_k cos(delta) + c_k sin(delta) with
-// the Taylor polynomials sin d = d - d^3/6 + d^5/120 and cos d = 1 - d^2/2 + d^4/24 - d^6/720
-// (remainders below 1e-22 absolute). Outside the table range it falls back to sincos().
+// the Taylor polynomials sin d = d - d^3/6 + d^5/120 (remainder below 1e-22) and
+// cos d = 1 - d^2/2 + d^4/24 (remainder d^6/720 below 2.1e-19, a thousandth of an ulp of 1).
+// Outside the table range it falls back to sincos().
 constexpr int kSinTab = 1024;
 constexpr double kSinLo = -0.25 * kPi;
 constexpr double kSinH = 1.5 * kPi / (kSinTab - 1);
@@ -153,22 +154,23 @@ __device__ __forceinline__ void sincos_tab(const double *__restrict__ tab, doubl
     double sk = e[1], ck = e[2];
     double d2 = d * d;
     double sd = fma(d * d2, fma(d2, 1.0 / 120.0, -1.0 / 6.0), d);       // sin d
-    double cm = d2 * fma(d2, fma(d2, -1.0 / 720.0, 1.0 / 24.0), -0.5);  // cos d - 1
+    double cm = d2 * fma(d2, 1.0 / 24.0, -0.5);                          // cos d - 1
     *s = fma(sk, cm, fma(ck, sd, sk));
     *c = fma(ck, cm, fma(-sk, sd, ck));
 }
 
 // 1/x for positive normal x: the approximate FP64 reciprocal of the PTX ISA
-// (rcp.approx.ftz.f64, relative error below 2^-22) refined by two Newton-Raphson steps
-// r <- r + r (1 - x r). Each step squares the relative error, so the result is within an ulp
-// of the correctly rounded quotient, in 5 FP64 instructions instead of a full division.
+// (rcp.approx.ftz.f64, relative error below 2^-22) refined by one third-order step: with
+// e = 1 - x r (exact to its rounding), 1/x = r / (1 - e) = r (1 + e + e^2 + ...), so
+// r (1 + e + e^2) leaves a relative error of e^3 < 2^-66 before the last rounding. The result
+// is the correctly rounded quotient except, about once in 5e4 arguments, one ulp from it (a
+// quotient within 2^-66 of a rounding boundary); two Newton-Raphson steps would round
+// correctly, at one FP64 instruction more per reciprocal (five per RK4 step).
 __device__ __forceinline__ double recip_nr(double x) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // Geodesic acceleration dK/dl = -Gamma K K (FP64 path), arranged for the FP64 pipe: every
