@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form (96-image library) leg")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the kappa/surrogate leg")
     ap.add_argument("--no-highres", action="store_true", help="skip the ADAF 4096^2 leg")
+    ap.add_argument("--batch-images", type=int, default=96,
+                    help="images of the library in the batched leg (the first ones of the 96)")
+    ap.add_argument("--batch-mode", default="auto", choices=["auto", "persistent"],
+                    help="persistent: mode 0 at a fixed balanced shape, no autotuner, no mode-1 or "
+                         "unpolarized batches (a small device footprint, for profiling the persistent kernel)")
     ap.add_argument("--fetch", default="auto", choices=["auto", "gather", "staged"],
                     help="grid fetch of the FP32 transfer (rt_set_grid_fetch)")
     return ap.parse_args()
@@ -202,18 +207,22 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
+def batch_leg(polrt, ctx, prims_dev, g, dev, torch, nimg=96, mode="auto"):
     """rt_render_batch of the image library: 96 images, N in {128, 256, 512}, inclination
-    10-170 deg, R_high 1-160, M_unit 1e17-1e20 g, mixed form; autotuned shape, graph replay."""
+    10-170 deg, R_high 1-160, M_unit 1e17-1e20 g, mixed form; autotuned shape, graph replay.
+    nimg < 96 takes the first nimg images; mode "persistent" runs mode 0 alone at a fixed shape."""
     from paper_2302_02733_gb300 import synth
 
-    table = synth.batch_jobs(7, 96)
+    table = synth.batch_jobs(7, nimg)
     cams = [synth.Camera(incl_deg=j.incl_deg, nx=j.n, ny=j.n) for j in table]
     outs = [torch.empty((j.n, j.n, 4), dtype=torch.float32, device=dev) for j in table]
     jobs = polrt.make_jobs((c, j.M_unit, j.R_high, o, None, None) for c, j, o in zip(cams, table, outs))
     polrt.rt_load_model(ctx, polrt.grid_model(prims_dev, g))
     npix = sum(j.n * j.n for j in table)
-    polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)  # autotune, capture
+    workload = f"image library: {nimg} images, N in {{128,256,512}}, torus grid, mixed form"
+    if mode == "persistent":  # 3 and 4 geodesic warps in alternate 8-warp blocks, 2 blocks per SM
+        polrt.rt_set_batch_config(ctx, polrt.RT_MIXED, 3, 1, 2, polrt.RT_BATCH_PERSISTENT, 4)
+    polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)  # autotune (mode auto), capture
     polrt.rt_render_batch(ctx, polrt.RT_MIXED, jobs)  # warm replay
     ms, steps = [], 0
     for _ in range(2):
@@ -226,10 +235,12 @@ def batch_leg(polrt, ctx, prims_dev, g, dev, torch):
     shape = polrt.rt_get_batch_config(ctx, polrt.RT_MIXED)
     launch = {polrt.RT_BATCH_PERSISTENT: "one persistent kernel per batch, replayed from a CUDA graph",
               polrt.RT_BATCH_CHUNKS: "the images' rays as one ray space, in the overlapped two-kernel shape of rt_render"}
-    res = {"workload": "image library: 96 images, N in {128,256,512}, torus grid, mixed form", "images": 96,
+    res = {"workload": workload, "images": nimg,
            "pixels": npix, "value": npix / (m / 1e3), "unit": "pixels/s", "ms_per_batch": m,
            "launch": launch[shape["mode"]], "shape": shape,
            "geodesic_fp64_tflops": fp64, "geodesic_fp64_frac": fp64 / FP64_PEAK_TFLOPS}
+    if mode == "persistent":
+        return res
     # the other mode at the autotuner's best shape for it, for comparison
     other = polrt.RT_BATCH_PERSISTENT if shape["mode"] == polrt.RT_BATCH_CHUNKS else polrt.RT_BATCH_CHUNKS
     g, t, b = (shape["geo_warps"] or 4), (shape["step_tile"] or 1), (shape["blocks_per_sm"] or 2)
@@ -537,7 +548,7 @@ def main():
 
     # batched form: the 96-image library in one persistent launch per batch (graph replay)
     if not args.no_batch and ws == 1:
-        extra["batched_form"] = batch_leg(polrt, ctx, prims_dev, g, dev, torch)
+        extra["batched_form"] = batch_leg(polrt, ctx, prims_dev, g, dev, torch, args.batch_images, args.batch_mode)
     # the high-resolution ADAF image
     if not args.no_highres and ws == 1:
         extra["highres_form"] = highres_leg(polrt, ctx, dev, torch)

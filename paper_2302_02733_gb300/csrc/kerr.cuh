@@ -175,8 +175,13 @@ __device__ __forceinline__ double recip_nr(double x) {
 
 // Geodesic acceleration dK/dl = -Gamma K K (FP64 path), arranged for the FP64 pipe: every
 // product that can be folded into a fused multiply-add is, and products shared by the
-// D, P and Q contractions are formed once. Same quantities as DK::eval / connection_T:
-//   A_nu = D_{nu b} K^b, B_r = K.P/2, B_th = K.Q/2, acc = -g^{-1} (A - B).
+// contractions are formed once. Same quantities as DK::eval / connection_T:
+//   A_nu = D_{nu b} K^b, B_r = K.P/2, B_th = K.Q/2, F = A - B, acc = -g^{-1} F,
+// with the two B terms summed in closed form. With V = l.K = K^t + K^r - a s^2 K^phi:
+//   K.P = dq/dr V^2 + 2 r (K^th^2 + s^2 K^phi^2),
+//   K.Q = dq/dth V^2 + 2 s c [P K^phi^2 - a^2 K^th^2 - 2 a K^phi (q (K^t + K^r) + K^r)],
+// P = Sigma + a^2 s^2 (1 + 2 q): the P and Q contractions of DK::eval summed against K and
+// simplified, which takes fewer FP64 operations than forming P_nu and Q_nu and summing them.
 __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, double a, double r, double th,
                                           const double K[4], double acc[4]) {
     const double a2 = a * a;
@@ -201,35 +206,25 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double V = fma(-as2, Kp, W);               // l_mu K^mu
     double d1 = fma(Kr, dqr, Kh * dqt);        // D_tt = D_tr = D_rr
     double scK = two_sc * Kh;
-    double aq = a * q;
-    double ndtp = fma(as2, d1, aq * scK);      // -D_tphi
-    double ndrp = fma(a, scK, ndtp);           // -D_rphi
-    double a2scK = a2 * scK;
-    double dhh = fma(tr, Kr, -a2scK);          // D_thth
+    double ndtp = a * fma(s2, d1, q * scK);    // -D_tphi
+    double ascK = a * scK;                     // -D_rphi = -D_tphi + a scK
     double a2s2 = a2 * s2;
-    double bigp = fma(a2s2, q + q, sig + a2s2);
+    double sa = sig + a2s2;                    // r^2 + a^2
+    double bigp = fma(q + q, a2s2, sa);
     double dpp = fma(s2, fma(tr, Kr, a2s2 * d1), bigp * scK);  // D_phiphi
-    double P0 = dqr * V;                       // P_t = P_r
-    double P2 = tr * Kh;
-    double P3 = fma(-as2, P0, (tr * s2) * Kp);
-    double sca = two_sc * a;
-    double scaK = sca * Kp;
-    double dqtV = dqt * V;
-    double Q0 = fma(-scaK, q, dqtV);
-    double Q1 = Q0 - scaK;
-    double Q3 = fma(two_sc * bigp, Kp, -fma(sca, fma(q, Kt, op * Kr), as2 * dqtV));
-    // A_nu, B_nu and F = A - B
+    // A_nu and F = A - B
     double d1W = d1 * W;
     double At = fma(-ndtp, Kp, d1W);
-    double Ar = fma(-ndrp, Kp, d1W);
-    double Ap = fma(dpp, Kp, -fma(ndtp, Kt, ndrp * Kr));
-    double sumP = fma(P3, Kp, fma(P2, Kh, P0 * W));
-    double sumQ = fma(Q3, Kp, fma(-a2scK, Kh, fma(Q1, Kr, Q0 * Kt)));
-    double Fr = fma(-0.5, sumP, Ar);
-    double Fh = fma(-0.5, sumQ, dhh * Kh);
+    double Ar = fma(-ascK, Kp, At);
+    double Ap = fma(dpp, Kp, -fma(ndtp, W, ascK * Kr));
+    double V2 = V * V, Kh2 = Kh * Kh, Kp2 = Kp * Kp;
+    double Fr = fma(-0.5 * dqr, V2, fma(-r, fma(s2, Kp2, Kh2), Ar));
+    double t = fma(bigp, Kp2, a2 * Kh2);
+    t = fma(-(a + a) * Kp, fma(q, W, Kr), t);
+    double Fh = fma(tr * Kr, Kh, fma(-0.5 * dqt, V2, -sc * t));
     // acc = -g^{-1} F with g^tt = -(1+q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
     // g^thth = 1/Sigma, g^phiphi = 1/(Sigma sin^2)
-    double del = (r2 - tr) + a2;
+    double del = sa - tr;
     acc[0] = fma(op, At, -q * Fr);
     acc[1] = -fma(isig, fma(del, Fr, a * Ap), q * At);
     acc[2] = -isig * Fh;
