@@ -54,8 +54,18 @@ __device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double 
 #pragma unroll
     for (int i = 0; i < 7; i++) t[i] = fma(h, k3[i], y[i]);
     rhs(t, k4);
+    // The position rates of a stage are the previous stage's K: k1 = y_K and k_j+1 = K of
+    // stage j+1. So a position and its K component share the sums: with T = k2 + k3 and
+    // S = k1 + T of the K component, the classic weights give
+    //   position' = position + h y_K + (h^2 / 6) S,  K' = y_K + (h / 6) (S + T + k4).
+    const double hh6 = h * h6;
 #pragma unroll
-    for (int i = 0; i < 7; i++) out[i] = fma(h6, k4[i], fma(h3, k3[i], fma(h3, k2[i], fma(h6, k1[i], y[i]))));
+    for (int i = 0; i < 3; i++) {
+        const double T = k2[4 + i] + k3[4 + i], S = k1[4 + i] + T;
+        out[i] = fma(hh6, S, fma(h, y[4 + i], y[i]));
+        out[4 + i] = fma(h6, (S + T) + k4[4 + i], y[4 + i]);
+    }
+    out[3] = fma(h6, k4[3], fma(h3, k3[3], fma(h3, k2[3], fma(h6, k1[3], y[3]))));
 }
 
 // Initial state of the backward ray through pixel (ix, iy): the camera frame's past-directed

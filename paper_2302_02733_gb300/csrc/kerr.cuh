@@ -190,13 +190,13 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     const double Kt = K[0], Kr = K[1], Kh = K[2], Kp = K[3];
     // metric pieces
     double s2 = s * s, sc = s * c;
-    double r2 = r * r;
-    double sig = fma(a2 * c, c, r2);
+    double a2s2 = a2 * s2;
+    double sa = fma(r, r, a2);                 // r^2 + a^2
+    double sig = sa - a2s2;                    // Sigma = r^2 + a^2 cos^2 (>= r^2: no cancellation)
     double iss = recip_nr(sig * s2);  // 1/(Sigma sin^2)
     double isig = iss * s2;         // 1/Sigma
     double tr = r + r;
     double q = tr * isig;           // 2r/Sigma
-    double op = 1.0 + q;
     double dqr = fma(-q, q, isig + isig);      // d q/dr
     double two_sc = sc + sc;
     double dqt = (a2 * two_sc) * (q * isig);   // d q/dtheta
@@ -208,8 +208,6 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double scK = two_sc * Kh;
     double ndtp = a * fma(s2, d1, q * scK);    // -D_tphi
     double ascK = a * scK;                     // -D_rphi = -D_tphi + a scK
-    double a2s2 = a2 * s2;
-    double sa = sig + a2s2;                    // r^2 + a^2
     double bigp = fma(q + q, a2s2, sa);
     double dpp = fma(s2, fma(tr, Kr, a2s2 * d1), bigp * scK);  // D_phiphi
     // A_nu and F = A - B
@@ -217,18 +215,18 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double At = fma(-ndtp, Kp, d1W);
     double Ar = fma(-ascK, Kp, At);
     double Ap = fma(dpp, Kp, -fma(ndtp, W, ascK * Kr));
-    double V2 = V * V, Kh2 = Kh * Kh, Kp2 = Kp * Kp;
-    double Fr = fma(-0.5 * dqr, V2, fma(-r, fma(s2, Kp2, Kh2), Ar));
+    double hV2 = (0.5 * V) * V, Kh2 = Kh * Kh, Kp2 = Kp * Kp;
+    double Fr = fma(-dqr, hV2, fma(-r, fma(s2, Kp2, Kh2), Ar));
     double t = fma(bigp, Kp2, a2 * Kh2);
     t = fma(-(a + a) * Kp, fma(q, W, Kr), t);
-    double Fh = fma(tr * Kr, Kh, fma(-0.5 * dqt, V2, -sc * t));
+    double Fh = fma(tr * Kr, Kh, fma(-dqt, hV2, -sc * t));
     // acc = -g^{-1} F with g^tt = -(1+q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
     // g^thth = 1/Sigma, g^phiphi = 1/(Sigma sin^2)
     double del = sa - tr;
-    acc[0] = fma(op, At, -q * Fr);
+    acc[0] = fma(q, At - Fr, At);              // (1 + q) At - q Fr
     acc[1] = -fma(isig, fma(del, Fr, a * Ap), q * At);
     acc[2] = -isig * Fh;
-    acc[3] = -fma(iss, Ap, (a * isig) * Fr);
+    acc[3] = -iss * fma(as2, Fr, Ap);          // a/Sigma = a s^2 / (Sigma s^2)
 }
 
 // T^mu_b = Gamma^mu_{a b} K^a = 1/2 g^{mu nu} (D_{nu b} + [b=r] P_nu + [b=th] Q_nu
