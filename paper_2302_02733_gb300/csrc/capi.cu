@@ -3,6 +3,7 @@
 // parameters (units, horizon radius, grid spacings).
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <thread>
 #include <cmath>
 #include <cstring>
@@ -316,11 +317,17 @@ int rt_set_workspace(rt_ctx *c, void *dev_ptr, size_t bytes) {
     return RT_OK;
 }
 
+// Bytes per arena block the surrogate form adds: per saved state, the network's input (float4)
+// and output (8 floats), and (streamed) the state's compact row.
+constexpr size_t kSurBlockBytes = (size_t)kBlockStates * (16 + 32 + 4);
+constexpr size_t kSurPerRayBytes = kPerRayBytes + (size_t)kBudgetBlocksPerRay * kSurBlockBytes;
+
 // Workspace bytes the streamed shape needs for nrays rays: counters, chunk counts, ray records
-// and the arena at the per-ray budget.
-static size_t streamed_bytes(long long nrays) {
-    return align_up(sizeof(Counters)) + align_up(sizeof(unsigned) * rt_ctx::kMaxChunks) + (size_t)nrays * kPerRayBytes +
-           4 * kAlign;
+// and the arena at the per-ray budget (per_ray: kPerRayBytes, or kSurPerRayBytes for the
+// surrogate form).
+static size_t streamed_bytes(long long nrays, size_t per_ray = kPerRayBytes) {
+    return align_up(sizeof(Counters)) + align_up(sizeof(unsigned) * rt_ctx::kMaxChunks) + (size_t)nrays * per_ray +
+           8 * kAlign;
 }
 
 int rt_workspace_hint(const rt_ctx *c, size_t *bytes) {
@@ -387,7 +394,22 @@ static void launch_network_pass(const rt_ctx *c, const XferArgs &xa, float *sur_
     long long rows = nblocks * kBlockStates;
     launch_mlp_forward(reinterpret_cast<const float *>(xa.feat), sur_y, rows, c->d_wpk,
                        reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
-                       (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), s, used_blocks);
+                       (int)std::min<long long>((rows + 127) / 128, (long long)c->nsm * 4), s, used_blocks,
+                       kBlockStates);
+}
+
+// The same for the rays of xa in the streamed shape: the features pass hands each ray
+// consecutive compact rows (xa.sur_row maps every saved state to its row), and the network runs
+// over the rows handed out, a count it reads on the device. max_rows bounds the rows.
+static int launch_network_pass_rows(const rt_ctx *c, const XferArgs &xa, float *sur_y, Counters *ctr,
+                                    long long max_rows, int xf_grid, cudaStream_t s) {
+    CK(cudaMemsetAsync(&ctr->feat_next, 0, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(&ctr->sur_rows, 0, sizeof(unsigned long long), s));
+    launch_sur_features(xa, xf_grid, s);
+    launch_mlp_forward(reinterpret_cast<const float *>(xa.feat), sur_y, max_rows, c->d_wpk,
+                       reinterpret_cast<unsigned *>(c->d_mlpaux) + 1,
+                       (int)std::min<long long>((max_rows + 127) / 128, (long long)c->nsm * 4), s, &ctr->sur_rows, 1);
+    return RT_OK;
 }
 
 // Streams, events and the second pinned counter block of the overlapped render, made on first use.
@@ -626,8 +648,8 @@ static int render_overlap(rt_ctx *c, int form, int coef, const Camera &cam, cons
 
 // Whether the workspace holds, or (when the library owns it) can grow to hold, the streamed
 // shape's nrays rays; grows it then.
-static bool prepare_streamed(rt_ctx *c, long long nrays) {
-    const size_t need = streamed_bytes(nrays);
+static bool prepare_streamed(rt_ctx *c, long long nrays, size_t per_ray = kPerRayBytes) {
+    const size_t need = streamed_bytes(nrays, per_ray);
     if (c->ws_bytes >= need) return true;
     if (c->ws && !c->ws_owned) return false;
     size_t freeb = 0, total = 0;
@@ -636,19 +658,19 @@ static bool prepare_streamed(rt_ctx *c, long long nrays) {
         return false;
     }
     if (need > c->ws_bytes + (size_t)(0.6 * (double)freeb)) return false;
-    return ensure_workspace(c, nrays + 1) == RT_OK && c->ws_bytes >= need;
+    return ensure_workspace(c, nrays + 1, per_ray) == RT_OK && c->ws_bytes >= need;
 }
 
 // Pieces of a streamed render of nrays rays: 1 when the workspace holds (or can grow to hold)
 // every path; otherwise as many as the workspace needs, after growing a library-owned one as
 // far as ensure_workspace allows; 0 (no streamed render) beyond kMaxStreamPieces.
 constexpr int kMaxStreamPieces = 64;
-static int plan_pieces(rt_ctx *c, long long nrays) {
-    if (prepare_streamed(c, nrays)) return 1;
-    if (!c->ws || c->ws_owned) ensure_workspace(c, nrays + 1);
-    const size_t fixed = streamed_bytes(0);
+static int plan_pieces(rt_ctx *c, long long nrays, size_t per_ray = kPerRayBytes) {
+    if (prepare_streamed(c, nrays, per_ray)) return 1;
+    if (!c->ws || c->ws_owned) ensure_workspace(c, nrays + 1, per_ray);
+    const size_t fixed = streamed_bytes(0, per_ray);
     if (c->ws_bytes <= fixed) return 0;
-    const long long cap = (long long)((c->ws_bytes - fixed) / kPerRayBytes);
+    const long long cap = (long long)((c->ws_bytes - fixed) / per_ray);
     if (cap < 1) return 0;
     for (long long P = (nrays + cap - 1) / cap; P <= kMaxStreamPieces; P++)
         if (ChunkLayout{nrays, (int)P, 1}.max_size() <= cap) return (int)P;
@@ -683,8 +705,12 @@ static int render_streamed(rt_ctx *c, int form, int coef, const Camera &cam, con
                            int njobs = 0) {
     int rv = ensure_overlap(c);
     if (rv) return rv;
+    // the surrogate form: per run of chunks, its features pass, the network over the run's
+    // compact rows, then its transfer
+    const bool sur = form == RT_SURROGATE;
+    const size_t per_ray = sur ? kSurPerRayBytes : kPerRayBytes;
     const ChunkLayout Lp{nrays, P, 1};
-    if (P < 1 || K < 1 || (long long)P * K > rt_ctx::kMaxChunks || c->ws_bytes < streamed_bytes(Lp.max_size()))
+    if (P < 1 || K < 1 || (long long)P * K > rt_ctx::kMaxChunks || c->ws_bytes < streamed_bytes(Lp.max_size(), per_ray))
         return RT_ERR_NOMEM;
     char *base = (char *)c->ws;
     Counters *ctr = (Counters *)base;
@@ -694,9 +720,23 @@ static int render_streamed(rt_ctx *c, int form, int coef, const Camera &cam, con
     RayRecord *rec = (RayRecord *)(base + off);
     off = align_up(off + sizeof(RayRecord) * Lp.max_size());
     Arena ar;
-    ar.nblocks = (long long)((c->ws_bytes - off - 3 * kAlign) / kBlockBytes);
+    ar.nblocks = (long long)((c->ws_bytes - off - 6 * kAlign) / (kBlockBytes + (sur ? kSurBlockBytes : 0)));
     ar.states = (PathState *)(base + off);
     ar.prev = (int *)(base + off + (size_t)ar.nblocks * sizeof(PathState) * kBlockStates);
+    float4 *feat = nullptr;
+    float *sur_y = nullptr;
+    int *sur_row = nullptr;
+    if (sur) {
+        ar.nblocks = std::min<long long>(ar.nblocks, INT_MAX / kBlockStates);  // rows are int
+        ar.prev = (int *)(base + off + (size_t)ar.nblocks * sizeof(PathState) * kBlockStates);
+        const size_t rows = (size_t)ar.nblocks * kBlockStates;
+        off = align_up(off + (size_t)ar.nblocks * kBlockBytes);
+        feat = (float4 *)(base + off);
+        off = align_up(off + rows * sizeof(float4));
+        sur_y = (float *)(base + off);
+        off = align_up(off + rows * 8 * sizeof(float));
+        sur_row = (int *)(base + off);
+    }
     cudaStream_t sg = c->ostream[0], st = c->ostream[1];
     cudaEvent_t *gs = c->oev, *ge = c->oev + rt_ctx::kMaxChunks, *ts = c->oev + 2 * rt_ctx::kMaxChunks,
                 *te = c->oev + 3 * rt_ctx::kMaxChunks;
@@ -779,6 +819,12 @@ static int render_streamed(rt_ctx *c, int form, int coef, const Camera &cam, con
                 const int grid = q == cudaSuccess ? xf_grid_alone : xf_grid;
                 CK(cudaMemsetAsync(&ctr->xfer_next, 0, sizeof(unsigned long long), st));
                 for (int k = a; k < b; k++) CK(cudaEventRecord(ts[base_k + k], st));
+                if (sur) {
+                    set_surrogate_args(c, xa, feat, sur_y);
+                    xa.sur_row = sur_row;
+                    rv = launch_network_pass_rows(c, xa, sur_y, ctr, (long long)ar.nblocks * kBlockStates, grid, st);
+                    if (rv) return rv;
+                }
                 if (form == RT_FP64)
                     launch_transfer_fp64(xa, coef, grid, st);
                 else if (form == RT_UNPOL)
@@ -939,6 +985,7 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     if (form == RT_UNPOL && mod.edf != RT_EDF_THERMAL) return RT_ERR_INVALID;
     const size_t ncomp = form == RT_UNPOL ? 1 : 4;  // values per pixel
     const int coef = mod.edf != RT_EDF_KAPPA ? 0 : (sur ? 2 : 1);
+    if (sur) CK(cudaMemsetAsync(reinterpret_cast<unsigned *>(c->d_mlpaux) + 1, 0, sizeof(unsigned), c->stream));
 
     // workspace carving; the surrogate form adds, per saved state, the network's inputs and
     // outputs (16 + 32 bytes)
@@ -956,10 +1003,10 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
                      ? (int)std::min<long long>(kAutoChunksMax, std::max<long long>(4, nrays >> kAutoChunkShift))
                      : 1;
     bool ovl = chunks >= 2 && nrays >= 2;
-    // the streamed shape when the workspace can hold every ray's path (not for the surrogate
-    // form, whose network pass runs over one chunk's arena); else two halves of the workspace
+    // the streamed shape, in pieces that the workspace holds (the surrogate form's network then
+    // runs over compact rows of each transfer launch's rays); else two halves of the workspace
     // that hold a chunk each, with their own counters
-    int rv = RT_OK, P = ovl && !sur ? plan_pieces(c, nrays) : 0, Kp = 0;
+    int rv = RT_OK, P = ovl ? plan_pieces(c, nrays, sur ? kSurPerRayBytes : kPerRayBytes) : 0, Kp = 0;
     const bool streamed = P > 0;
     ChunkLayout L{nrays, 1, 1};
     if (streamed) {
@@ -1126,6 +1173,11 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     CK(cudaStreamSynchronize(c->stream));
     c->last_rays = nrays;
     c->last_was_batch = false;
+    if (sur) {  // a bounded wait of the network pass that ran out
+        unsigned err = 0;
+        CK(cudaMemcpy(&err, reinterpret_cast<unsigned *>(c->d_mlpaux) + 1, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (err) return RT_ERR_STALL;
+    }
     if (c->h_ctr->n_status[kStageStatus] > 0) return RT_ERR_STALL;
     if (c->h_ctr->n_status[kOverflow] > 0) return RT_ERR_WORKSPACE;
     if (steps_out) {  // every ray of this camera recorded its steps

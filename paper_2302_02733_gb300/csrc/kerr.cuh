@@ -209,7 +209,8 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double ndtp = a * fma(s2, d1, q * scK);    // -D_tphi
     double ascK = a * scK;                     // -D_rphi = -D_tphi + a scK
     double bigp = fma(q + q, a2s2, sa);
-    double dpp = fma(s2, fma(tr, Kr, a2s2 * d1), bigp * scK);  // D_phiphi
+    double trKr = tr * Kr;
+    double dpp = fma(s2, fma(a2s2, d1, trKr), bigp * scK);  // D_phiphi
     // A_nu and F = A - B
     double d1W = d1 * W;
     double At = fma(-ndtp, Kp, d1W);
@@ -219,7 +220,7 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double Fr = fma(-dqr, hV2, fma(-r, fma(s2, Kp2, Kh2), Ar));
     double t = fma(bigp, Kp2, a2 * Kh2);
     t = fma(-(a + a) * Kp, fma(q, W, Kr), t);
-    double Fh = fma(tr * Kr, Kh, fma(-dqt, hV2, -sc * t));
+    double Fh = fma(trKr, Kh, fma(-dqt, hV2, -sc * t));
     // acc = -g^{-1} F with g^tt = -(1+q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
     // g^thth = 1/Sigma, g^phiphi = 1/(Sigma sin^2)
     double del = sa - tr;

@@ -87,14 +87,14 @@ constexpr int kFwdA0 = kPkWBytes, kFwdA = kFwdA0 + 128 * 16 * 2, kFwdBar = kFwdA
 constexpr int kFwdSmem = kFwdBar + 16;
 
 // y[n][8] = MLP(x[n][4]) (x already normalised), tiles of 128 rows, one row per thread. With
-// used_blocks, n is capped at 32 rows per arena block in use, a count an earlier kernel on the
-// stream wrote (so the host need not wait for it).
+// used, n is capped at used[0] * used_scale rows (32 per arena block in use, or a row count), a
+// count an earlier kernel on the stream wrote (so the host need not wait for it).
 __global__ void __launch_bounds__(128, 1) mlp_forward_kernel(const float4 *__restrict__ x, float *__restrict__ y,
                                                              long long n, const uint4 *__restrict__ wpk,
-                                                             unsigned *err,
-                                                             const unsigned long long *used_blocks) {
+                                                             unsigned *err, const unsigned long long *used,
+                                                             int used_scale) {
     extern __shared__ __align__(128) unsigned char sm[];
-    if (used_blocks) n = min(n, (long long)(*used_blocks * kBlockStates));
+    if (used) n = min(n, (long long)(*used * (unsigned long long)used_scale));
     const int r = threadIdx.x, warp = r >> 5;
     for (int i = r; i < kPkWBytes / 16; i += 128) reinterpret_cast<uint4 *>(sm)[i] = wpk[i];
     uint32_t *slot = reinterpret_cast<uint32_t *>(sm + kFwdBar + 8);
@@ -352,9 +352,9 @@ void launch_mlp_pack(const float *th, void *wpk, void *tpk, cudaStream_t s) {
 }
 
 void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s,
-                        const unsigned long long *used_blocks) {
+                        const unsigned long long *used, int used_scale) {
     mlp_forward_kernel<<<grid, 128, kFwdSmem, s>>>(reinterpret_cast<const float4 *>(x), y, n,
-                                                   reinterpret_cast<const uint4 *>(wpk), err, used_blocks);
+                                                   reinterpret_cast<const uint4 *>(wpk), err, used, used_scale);
 }
 
 void launch_mlp_grad(const float *x, const float *t, long long n, long long ntot, const void *wpk, const void *tpk,

@@ -114,6 +114,7 @@ struct Counters {
     unsigned long long feat_count;            // emitting points written by rt_render_features
     unsigned long long steps, points, emitting;
     unsigned int n_status[8];
+    unsigned long long sur_rows;              // rows of the surrogate's compact features (streamed)
 };
 
 struct RayRecord {

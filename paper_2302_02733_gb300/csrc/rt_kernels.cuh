@@ -91,7 +91,9 @@ struct XferArgs {
     const float *sur_y;
     const float *sur_norm;
     float sur_lo[4], sur_hi[4];
-    float4 *feat;         // features pass: network inputs per saved state
+    float4 *feat;         // features pass: network inputs per saved state, or (sur_row) per compact row
+    int *sur_row;         // optional: per saved state, its row of feat and sur_y; the features pass
+                          // hands each ray consecutive rows (ctr->sur_rows counts them)
     float4 *feat_raw;     // or (rt_render_features) raw inputs of the emitting points, compacted
     long long feat_cap;
     const int *pix_list;  // optional: the pixel of each global ray id (adaptive rendering)
@@ -198,8 +200,10 @@ void launch_transfer_mixed(const XferArgs &a, int coef, int grid, cudaStream_t s
 void launch_transfer_staged(const XferArgs &a, const CUtensorMap &map, int grid, cudaStream_t s);
 void launch_sur_features(const XferArgs &a, int grid, cudaStream_t s);
 void launch_unpol(const XferArgs &a, int grid, cudaStream_t s);  // Stokes I only, FP32
+// n rows, capped (when used is given) at used[0] * used_scale, a count an earlier kernel on the
+// stream wrote
 void launch_mlp_forward(const float *x, float *y, long long n, const void *wpk, unsigned *err, int grid, cudaStream_t s,
-                        const unsigned long long *used_blocks = nullptr);
+                        const unsigned long long *used = nullptr, int used_scale = 1);
 void launch_x2_table(const GridModel &g, double *table, float *table_f, cudaStream_t s);
 // out[7]: sum I, Q, U, V, flux [Jy], net LP, net CP; out holds 8 + 4 kStatBlocks doubles
 constexpr int kStatBlocks = 608;

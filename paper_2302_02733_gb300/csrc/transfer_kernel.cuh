@@ -210,7 +210,8 @@ __device__ __forceinline__ void kappa_point_coeffs(const XferArgs *pa, long long
         if (in) {
             float phi[kSurBasis], y[8];
             sur_basis(xn, phi);
-            const float *nm = pa->sur_norm, *yh = pa->sur_y + 8 * st;
+            const long long row = pa->sur_row ? (long long)pa->sur_row[st] : st;
+            const float *nm = pa->sur_norm, *yh = pa->sur_y + 8 * row;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
                 float b = 0.f;
@@ -685,7 +686,7 @@ template <typename R>
 __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
     const Camera &c = p.cam;
     const R a = pick<R>(c.a, c.f_a), nu_obs = pick<R>(c.nu_obs, c.f_nu_obs);
-    long long ray = -1;
+    long long ray = -1, row = 0;
     int blk = -1, slot = 0, n = 0;
     bool live = false, drained = false;
     for (;;) {
@@ -700,6 +701,8 @@ __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
                     slot = (rec.nstates - 1) % kBlockStates;
                     n = rec.nstates - 1;
                     live = true;
+                    // compact rows: the ray's n states take n consecutive rows
+                    if (p.sur_row) row = (long long)atomicAdd(&p.ctr->sur_rows, (unsigned long long)n);
                 }
             } else {
                 drained = true;
@@ -737,7 +740,12 @@ __global__ void __launch_bounds__(kXferThreads) sur_features_pass(XferArgs p) {
             for (int j = 0; j < 4; j++) xn[j] = 2.0f * (f[j] - p.sur_lo[j]) / (p.sur_hi[j] - p.sur_lo[j]) - 1.0f;
             o = make_float4(xn[0], xn[1], xn[2], xn[3]);
         }
-        if (p.feat) p.feat[(long long)blk * kBlockStates + slot] = o;
+        if (p.sur_row) {
+            p.feat[row + n] = o;
+            p.sur_row[(long long)blk * kBlockStates + slot] = (int)(row + n);
+        } else if (p.feat) {
+            p.feat[(long long)blk * kBlockStates + slot] = o;
+        }
         if (n == 0) live = false;
     }
 }

@@ -144,10 +144,12 @@ def test_render_config_checks(rt):
 
 
 def test_overlapped_surrogate_is_identical(rt, synth, torus_grid):
-    """The surrogate form through the overlapped shape: per chunk the features pass, the
-    tensor-core network pass (its row count read on the device) and the transfer, in each
-    workspace half. A fixed random network is enough: the check is that the shape does not
-    change the image."""
+    """The surrogate form through the overlapped shapes: streamed, where each transfer launch's
+    rays get compact rows for the features pass and the tensor-core network pass (its row count
+    read on the device); and in two halves, per chunk over the half's arena (a caller's
+    workspace of 1/50 of the thermal image's: a streamed piece would hold under 1/64 of the
+    rays, a half about 1/175). A fixed random network is enough: the check is that the shape
+    does not change the image."""
     polrt, ctx = rt
     prims, g = torus_grid
     cam = synth.Camera(incl_deg=20.0, nx=160, ny=128)
@@ -163,12 +165,22 @@ def test_overlapped_surrogate_is_identical(rt, synth, torus_grid):
     try:
         ref, st0, _, c0 = render(polrt, ctx, polrt.RT_SURROGATE, cam, (0, 0, 1))
         assert c0["chunks"] == 1 and torch.isfinite(ref).all() and ref[..., 0].max() > 0
-        for cfg in ((1, 0, 4), (0, 0, 3)):
-            out, st, _, c = render(polrt, ctx, polrt.RT_SURROGATE, cam, cfg)
-            assert c["chunks"] == cfg[2]
-            assert torch.equal(out, ref) and torch.equal(st, st0), cfg
-            assert c["points"] == c0["points"] and c["steps"] == c0["steps"]
+        # streamed (the network over each transfer launch's compact rows), then in two halves
+        for frac, cfgs, shape in ((1.0, ((1, 0, 4), (0, 0, 3)), 2), (1 / 50, ((1, 0, 4),), 1)):
+            if frac < 1.0:
+                ws = torch.empty(int(frac * polrt.rt_workspace_hint(ctx)), dtype=torch.uint8, device="cuda")
+                polrt.rt_set_workspace(ctx, ws)
+            for cfg in cfgs:
+                out, st, _, c = render(polrt, ctx, polrt.RT_SURROGATE, cam, cfg)
+                assert c["shape"] == shape, (frac, cfg)
+                if shape == 2:
+                    assert c["chunks"] == cfg[2]
+                assert torch.equal(out, ref) and torch.equal(st, st0), (frac, cfg)
+                assert c["points"] == c0["points"] and c["steps"] == c0["steps"]
+            if frac < 1.0:
+                polrt.rt_set_workspace(ctx, None)
     finally:
+        polrt.rt_set_workspace(ctx, None)
         polrt.rt_set_render_config(ctx, 0, 0, 0)
 
 
