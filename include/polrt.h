@@ -319,8 +319,8 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
  *     geodesic still running (after the geodesic has ended, at the transfer's full occupancy);
  *     a piece starts when the previous one has ended. The call occupies its host thread until
  *     the render ends.
- *   - in two halves of the workspace, when a piece would hold under 1/64 of the rays (and for
- *     RT_SURROGATE): the rays are dealt to the chunks, each chunk uses one half in turn, and
+ *   - in two halves of the workspace, when a piece would hold under 1/64 of the rays: the
+ *     rays are dealt to the chunks, each chunk uses one half in turn, and
  *     the geodesic kernel of chunk i + 1 runs on one internal stream beside the transfer
  *     kernel of chunk i on another. last_chunk_div >= 2 shrinks the last chunk to
  *     1/last_chunk_div of a regular one (1 to 16; 0 = 1).
@@ -330,8 +330,9 @@ int rt_image_visibilities(rt_ctx *ctx, const void *img, int form, int stokes, vo
  * rays or more are overlapped, streamed in chunks of about 2^15 rays (at least 16 per piece)
  * with the geodesic at 2 blocks per SM, or in halves of 4 to 16 chunks of about 2^17 rays with
  * the geodesic at 1 block per SM; smaller images, and the RT_FP64 and RT_SURROGATE forms, run
- * one pass of each kernel (RT_SURROGATE overlaps its features, network and transfer passes, in
- * halves, when chunks >= 2 is set).
+ * one pass of each kernel. RT_SURROGATE overlaps when chunks >= 2 is set: streamed, each
+ * transfer launch's rays go through the features pass, the network (over compact rows) and
+ * the transfer in turn; in halves, per chunk (both measured slower than one pass on GB300).
  * Independently of the shape, a full render records each pixel's step count, and the next
  * render of the same camera and integrator takes its rays longest first, so that no launch ends
  * waiting for a few long photon-ring rays. The first render of a new camera of 2^18 rays or more
