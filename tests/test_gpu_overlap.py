@@ -220,3 +220,26 @@ def test_probe_order_for_a_new_camera(rt, synth, torus_grid):
     second, st2, _, c2 = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 0))
     assert torch.isfinite(first).all() and torch.equal(first, second) and torch.equal(st1, st2)
     assert c1["steps"] == c2["steps"] and c1["rays"] == 512 * 512 and c1["n_overflow"] == 0
+
+
+def test_streamed_image_with_probed_then_recorded_order(rt, synth, torus_grid):
+    """The automatic shape of a new 1024^2 camera: streamed, its first render in the order the
+    probe predicts, the next in the order the first recorded (a different cut of the rays into
+    chunks and transfer launches); the images and counts agree with one pass of each kernel."""
+    polrt, ctx = rt
+    prims, g = torus_grid
+    cam = synth.Camera(incl_deg=27.0, nx=1024, ny=1024)  # a camera no other test renders
+    polrt.rt_set_integrator(ctx, 0.05, 20000)
+    polrt.rt_set_camera(ctx, cam)
+    polrt.rt_load_model(ctx, polrt.grid_model(torch.from_numpy(prims).cuda(), g))
+    try:
+        first, st1, _, c1 = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 0))
+        assert c1["shape"] == 2 and c1["geodesic_launches"] == 1
+        second, st2, _, c2 = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 0))
+        ref, st0, _, c0 = render(polrt, ctx, polrt.RT_MIXED, cam, (0, 0, 1))
+        assert c0["shape"] == 0 and torch.isfinite(ref).all()
+        for img, st, c in ((first, st1, c1), (second, st2, c2)):
+            assert torch.equal(img, ref) and torch.equal(st, st0)
+            assert c["steps"] == c0["steps"] and c["points"] == c0["points"] and c["n_overflow"] == 0
+    finally:
+        polrt.rt_set_render_config(ctx, 0, 0, 0)
