@@ -46,7 +46,8 @@ enum {
     RT_ERR_NOT_READY = -4,  /* no model or no camera set */
     RT_ERR_WORKSPACE = -5,  /* the path arena ran out; rays carry RT_RAY_OVERFLOW */
     RT_ERR_SIZE = -6,       /* a size beyond a fixed limit of the call */
-    RT_ERR_STALL = -7       /* a bounded wait inside a kernel ran out; results invalid */
+    RT_ERR_STALL = -7       /* a bounded wait ran out (inside a kernel, or rt_render's host wait of
+                               600 s for a streamed render's chunks); results invalid */
 };
 
 enum { RT_MODEL_ADAF = 1, RT_MODEL_GRID = 2 };

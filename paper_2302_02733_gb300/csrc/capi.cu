@@ -303,10 +303,19 @@ int rt_load_model(rt_ctx *c, const rt_model_params *p) {
     return RT_OK;
 }
 
+// Wait for the overlapped shapes' internal streams: a render that returned an error part way
+// may have left launches on them that still use the workspace. Idle streams return at once.
+static int quiesce_overlap(rt_ctx *c) {
+    for (int i = 0; i < 2; i++)
+        if (c->ostream[i]) CK(cudaStreamSynchronize(c->ostream[i]));
+    return RT_OK;
+}
+
 int rt_set_workspace(rt_ctx *c, void *dev_ptr, size_t bytes) {
     if (!c) return RT_ERR_INVALID;
     if (dev_ptr && bytes < rt_workspace_min_bytes()) return RT_ERR_INVALID;
     if (dev_ptr && ((uintptr_t)dev_ptr % kAlign) != 0) return RT_ERR_INVALID;
+    quiesce_overlap(c);  // no launch of an earlier render may still use the old workspace
     if (c->ws_owned) {
         cudaStreamSynchronize(c->stream);
         cudaFree(c->ws);
@@ -972,6 +981,8 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     if (form == RT_UNPOL && depth) return RT_ERR_INVALID;
     if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
     CK(cudaSetDevice(c->device));
+    int qv = quiesce_overlap(c);
+    if (qv) return qv;
     const rt_camera &rc = c->cam;
     long long nrays = list ? nlist : (long long)rc.nx * rc.ny;
     if (nrays == 0) return RT_OK;
@@ -1195,6 +1206,8 @@ int rt_render_features(rt_ctx *c, float *feat, long long cap, long long *count) 
     if (!c->have_cam || !c->have_model) return RT_ERR_NOT_READY;
     if (!is_device_ptr(feat)) return RT_ERR_INVALID;
     CK(cudaSetDevice(c->device));
+    int qv = quiesce_overlap(c);
+    if (qv) return qv;
     const rt_camera &rc = c->cam;
     long long nrays = (long long)rc.nx * rc.ny;
     int rv = ensure_workspace(c, nrays);
