@@ -30,6 +30,17 @@ __device__ __forceinline__ float d2f_int(double d) {
     return __uint_as_float(f);
 }
 
+// float -> double, exact, with integer operations only (a conversion instruction would take the
+// FP64 pipe). Zero and subnormal floats become signed zero; infinity and NaN keep their class.
+__device__ __forceinline__ double f2d_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    const unsigned long long de = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+    return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 // The nearest integer of |x| < 2^22, and the float of an integer |i| < 2^22: adding
 // 1.5 * 2^23 moves x into the binade whose unit in the last place is 1, where the mantissa
 // bits hold round(x) in two's complement.

@@ -19,12 +19,13 @@ __device__ __forceinline__ double pos_max(double x, double y) { return dbits(x) 
 // so min and max compare bit patterns. The 1e-40 only keeps the denominator from zero: it is
 // below half an ulp of |K^ph| >= 1e-24 and of any denominator above 1e-24 r tt, so it changes
 // no rounded result there; a floor on the bit pattern stands in for it, without an FP64
-// addition.
+// addition. The floor is 1e-30, inside the reciprocal's range; it differs from the 1e-40 term
+// only for denominators below 1e-30, where the step already exceeds 1e27 r tt.
 __device__ __forceinline__ double step_size(double eps, const double y[7]) {
     double tt = pos_max(pos_min(y[1], kPi - y[1]), 1e-2);
     double rt = y[0] * tt;
     double den = fma(fabs(y[6]), rt, fma(fabs(y[4]), tt, fabs(y[5]) * y[0]));
-    den = pos_max(den, 1e-40 * 1e-2 * 1.05);  // below every 1e-40 r tt (r > 1.05, tt >= 0.01)
+    den = pos_max(den, 1e-30);
     return (eps * rt) * recip_nr(den);
 }
 

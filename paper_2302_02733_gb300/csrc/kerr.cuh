@@ -159,16 +159,17 @@ __device__ __forceinline__ void sincos_tab(const double *__restrict__ tab, doubl
     *c = fma(ck, cm, fma(-sk, sd, ck));
 }
 
-// 1/x for positive normal x: the approximate FP64 reciprocal of the PTX ISA
-// (rcp.approx.ftz.f64, relative error below 2^-22) refined by one third-order step: with
-// e = 1 - x r (exact to its rounding), 1/x = r / (1 - e) = r (1 + e + e^2 + ...), so
-// r (1 + e + e^2) leaves a relative error of e^3 < 2^-66 before the last rounding. The result
-// is the correctly rounded quotient except, about once in 5e4 arguments, one ulp from it (a
-// quotient within 2^-66 of a rounding boundary); two Newton-Raphson steps would round
-// correctly, at one FP64 instruction more per reciprocal (five per RK4 step).
+// 1/x for positive x between 2^-120 and 2^120: a seed from FP32, x rounded to FP32 and
+// rcp.approx.ftz.f32 (relative error of the seed below 2^-22; both conversions on the integer
+// pipe, the reciprocal on the special-function unit, so the seed takes no FP64 instruction),
+// refined by one third-order step: with e = 1 - x r (exact to its rounding),
+// 1/x = r / (1 - e) = r (1 + e + e^2 + ...), so r (1 + e + e^2) leaves a relative error of
+// e^3 < 2^-66 before the last rounding. The result is the correctly rounded quotient except,
+// rarely, one ulp from it (a quotient within 2^-66 of a rounding boundary).
 __device__ __forceinline__ double recip_nr(double x) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(d2f_int(x)));
+    const double r = f2d_int(rf);
     const double e = fma(-x, r, 1.0);
     return fma(r, fma(e, e, e), r);
 }
