@@ -41,6 +41,42 @@ __device__ __forceinline__ double f2d_int(float f) {
     return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
 
+// 2x and x/2 of a double, exactly as the FP64 sum x + x and product 0.5 x round them, with
+// integer operations only (the FP64 pipe bounds the geodesic; the integer pipe is idle there).
+// twice: a normal x below 2^1023 gets one more in its exponent field; a zero or subnormal x
+// doubles its significand (carrying into the exponent field when it becomes normal); a larger x
+// overflows to infinity; infinity and NaN pass through.
+__device__ __forceinline__ double twice(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long e = b & 0x7ff0000000000000ull, sign = b & 0x8000000000000000ull;
+    unsigned long long r;
+    if (e == 0ull)
+        r = sign | ((b & 0x000fffffffffffffull) << 1);
+    else if (e >= 0x7fe0000000000000ull)
+        r = e == 0x7ff0000000000000ull ? b : (sign | 0x7ff0000000000000ull);
+    else
+        r = b + (1ull << 52);
+    return __longlong_as_double((long long)r);
+}
+// halve: a normal x with exponent field above 1 gets one less; otherwise the significand
+// (with its implicit bit) is halved, rounded to nearest even; infinity and NaN pass through.
+__device__ __forceinline__ double halve(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long e = b & 0x7ff0000000000000ull, sign = b & 0x8000000000000000ull;
+    unsigned long long r;
+    if (e >= (2ull << 52) && e != 0x7ff0000000000000ull) {
+        r = b - (1ull << 52);
+    } else if (e == 0x7ff0000000000000ull) {
+        r = b;
+    } else {
+        const unsigned long long m = (b & 0x000fffffffffffffull) | (e ? (1ull << 52) : 0ull);
+        unsigned long long q = m >> 1;
+        q += (m & 1ull) & (q & 1ull);
+        r = sign | q;
+    }
+    return __longlong_as_double((long long)r);
+}
+
 // The nearest integer of |x| < 2^22, and the float of an integer |i| < 2^22: adding
 // 1.5 * 2^23 moves x into the binade whose unit in the last place is 1, where the mantissa
 // bits hold round(x) in two's complement.

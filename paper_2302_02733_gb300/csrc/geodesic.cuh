@@ -44,7 +44,8 @@ __device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double 
         dz[5] = acc[2];
         dz[6] = acc[3];
     };
-    const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
+    // h/6 as half of h/3: 1/6 in FP64 is half of 1/3, so the product rounds to the same bits
+    const double h2 = halve(h), h3 = h * (1.0 / 3.0), h6 = halve(h3);
     rhs(y, k1);
 #pragma unroll
     for (int i = 0; i < 7; i++) t[i] = fma(h2, k1[i], y[i]);

@@ -196,10 +196,10 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double sig = sa - a2s2;                    // Sigma = r^2 + a^2 cos^2 (>= r^2: no cancellation)
     double iss = recip_nr(sig * s2);  // 1/(Sigma sin^2)
     double isig = iss * s2;         // 1/Sigma
-    double tr = r + r;
+    double tr = twice(r);           // 2r (twice, halve: exact, on the integer pipe)
     double q = tr * isig;           // 2r/Sigma
-    double dqr = fma(-q, q, isig + isig);      // d q/dr
-    double two_sc = sc + sc;
+    double dqr = fma(-q, q, twice(isig));      // d q/dr
+    double two_sc = twice(sc);
     double dqt = (a2 * two_sc) * (q * isig);   // d q/dtheta
     // contractions with K
     double W = Kt + Kr;
@@ -209,7 +209,7 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double scK = two_sc * Kh;
     double ndtp = a * fma(s2, d1, q * scK);    // -D_tphi
     double ascK = a * scK;                     // -D_rphi = -D_tphi + a scK
-    double bigp = fma(q + q, a2s2, sa);
+    double bigp = fma(twice(q), a2s2, sa);
     double trKr = tr * Kr;
     double dpp = fma(s2, fma(a2s2, d1, trKr), bigp * scK);  // D_phiphi
     // A_nu and F = A - B
@@ -217,7 +217,7 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double At = fma(-ndtp, Kp, d1W);
     double Ar = fma(-ascK, Kp, At);
     double Ap = fma(dpp, Kp, -fma(ndtp, W, ascK * Kr));
-    double hV2 = (0.5 * V) * V, Kh2 = Kh * Kh, Kp2 = Kp * Kp;
+    double hV2 = halve(V) * V, Kh2 = Kh * Kh, Kp2 = Kp * Kp;
     double Fr = fma(-dqr, hV2, fma(-r, fma(s2, Kp2, Kh2), Ar));
     double t = fma(bigp, Kp2, a2 * Kh2);
     t = fma(-(a + a) * Kp, fma(q, W, Kr), t);
