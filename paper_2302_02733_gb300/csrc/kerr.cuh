@@ -207,20 +207,20 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double V = fma(-as2, Kp, W);               // l_mu K^mu
     double d1 = fma(Kr, dqr, Kh * dqt);        // D_tt = D_tr = D_rr
     double scK = two_sc * Kh;
-    double ndtp = a * fma(s2, d1, q * scK);    // -D_tphi
-    double ascK = a * scK;                     // -D_rphi = -D_tphi + a scK
+    double m = fma(s2, d1, q * scK);           // -D_tphi / a
     double bigp = fma(twice(q), a2s2, sa);
     double trKr = tr * Kr;
     double dpp = fma(s2, fma(a2s2, d1, trKr), bigp * scK);  // D_phiphi
     // A_nu and F = A - B
     double d1W = d1 * W;
-    double At = fma(-ndtp, Kp, d1W);
-    double Ar = fma(-ascK, Kp, At);
-    double Ap = fma(dpp, Kp, -fma(ndtp, W, ascK * Kr));
+    double aKp = a * Kp;
+    double At = fma(-m, aKp, d1W);
+    double Ar = fma(-scK, aKp, At);            // -D_rphi = -D_tphi + a scK
+    double Ap = fma(dpp, Kp, -a * fma(m, W, scK * Kr));
     double hV2 = halve(V) * V, Kh2 = Kh * Kh, Kp2 = Kp * Kp;
     double Fr = fma(-dqr, hV2, fma(-r, fma(s2, Kp2, Kh2), Ar));
     double t = fma(bigp, Kp2, a2 * Kh2);
-    t = fma(-(a + a) * Kp, fma(q, W, Kr), t);
+    t = fma(-twice(aKp), fma(q, W, Kr), t);
     double Fh = fma(trKr, Kh, fma(-dqt, hV2, -sc * t));
     // acc = -g^{-1} F with g^tt = -(1+q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
     // g^thth = 1/Sigma, g^phiphi = 1/(Sigma sin^2)
