@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kGeoThreads, 4) geodesic_kernel(GeoArgs p) {
                 blk = (int)b;
                 slot = 0;
             }
-            PathState ps = {z[0], z[1], z[2], z[3], z[4], z[5], z[6], hz};
+            PathState ps = {z[0], z[1], z[2], z[3] - z[4], z[4], z[5], z[6], hz};  // K^t = W - K^r
             reinterpret_cast<double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot)[0] =
                 make_double4_32a(ps.r, ps.th, ps.ph, ps.kt);
             reinterpret_cast<double4_32a *>(p.arena.states + (long long)blk * kBlockStates + slot)[1] =

@@ -29,7 +29,8 @@ __device__ __forceinline__ double step_size(double eps, const double y[7]) {
     return (eps * rt) * recip_nr(den);
 }
 
-// y = (r, theta, phi, K^t, K^r, K^theta, K^phi); t is never needed (stationary metric).
+// y = (r, theta, phi, W, K^r, K^theta, K^phi) with W = K^t + K^r (geo_accel); t is never
+// needed (stationary metric). Saved states hold K^t = W - K^r.
 __device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double a, double h, const double y[7],
                                          double out[7]) {
     double k1[7], k2[7], k3[7], k4[7], t[7];
@@ -81,6 +82,7 @@ __device__ __forceinline__ void ray_start(const Camera &c, int ix, int iy, doubl
     y[2] = 0.0;
 #pragma unroll
     for (int k = 0; k < 4; k++) y[3 + k] = -e[0][k] + s[0] * e[1][k] + s[1] * e[2][k] + s[2] * e[3][k];
+    y[3] += y[4];  // W = K^t + K^r
 }
 
 // The camera constants a geodesic step and its stop test read. The batched kernel, whose

@@ -183,12 +183,15 @@ __device__ __forceinline__ double recip_nr(double x) {
 //   K.Q = dq/dth V^2 + 2 s c [P K^phi^2 - a^2 K^th^2 - 2 a K^phi (q (K^t + K^r) + K^r)],
 // P = Sigma + a^2 s^2 (1 + 2 q): the P and Q contractions of DK::eval summed against K and
 // simplified, which takes fewer FP64 operations than forming P_nu and Q_nu and summing them.
+//
+// The geodesic carries W = K^t + K^r in place of K^t (the stationary metric's K^t enters the
+// acceleration only through W): K = (W, K^r, K^theta, K^phi) on input, and acc[0] = dW/dl.
 __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, double a, double r, double th,
                                           const double K[4], double acc[4]) {
     const double a2 = a * a;
     double s, c;
     sincos_tab(sctab, th, &s, &c);
-    const double Kt = K[0], Kr = K[1], Kh = K[2], Kp = K[3];
+    const double W = K[0], Kr = K[1], Kh = K[2], Kp = K[3];
     // metric pieces
     double s2 = s * s, sc = s * c;
     double a2s2 = a2 * s2;
@@ -202,7 +205,6 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     double two_sc = twice(sc);
     double dqt = (a2 * two_sc) * (q * isig);   // d q/dtheta
     // contractions with K
-    double W = Kt + Kr;
     double as2 = a * s2;
     double V = fma(-as2, Kp, W);               // l_mu K^mu
     double d1 = fma(Kr, dqr, Kh * dqt);        // D_tt = D_tr = D_rr
@@ -225,8 +227,11 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     // acc = -g^{-1} F with g^tt = -(1+q), g^tr = q, g^rr = Delta/Sigma, g^rphi = a/Sigma,
     // g^thth = 1/Sigma, g^phiphi = 1/(Sigma sin^2)
     double del = sa - tr;
-    acc[0] = fma(q, At - Fr, At);              // (1 + q) At - q Fr
-    acc[1] = -fma(isig, fma(del, Fr, a * Ap), q * At);
+    // dK^t = (1 + q) At - q Fr and dK^r = -(isig (del Fr + a Ap) + q At), so
+    // dW = At - q Fr - isig (del Fr + a Ap)
+    const double X = fma(del, Fr, a * Ap);
+    acc[0] = fma(-isig, X, fma(-q, Fr, At));
+    acc[1] = -fma(isig, X, q * At);
     acc[2] = -isig * Fh;
     acc[3] = -iss * fma(as2, Fr, Ap);          // a/Sigma = a s^2 / (Sigma s^2)
 }

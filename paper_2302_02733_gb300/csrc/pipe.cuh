@@ -65,7 +65,7 @@ __device__ __forceinline__ int pool_free_chain(const Pool &P, PipeCounters *c, i
 
 __device__ __forceinline__ void save_state(const Pool &P, int blk, int slot, const double y[7], double h) {
     double4_32a *d = reinterpret_cast<double4_32a *>(P.states + (long long)blk * kBlockStates + slot);
-    d[0] = make_double4_32a(y[0], y[1], y[2], y[3]);
+    d[0] = make_double4_32a(y[0], y[1], y[2], y[3] - y[4]);  // K^t = W - K^r
     d[1] = make_double4_32a(y[4], y[5], y[6], h);
 }
 
