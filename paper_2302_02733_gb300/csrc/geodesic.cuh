@@ -31,44 +31,96 @@ __device__ __forceinline__ double step_size(double eps, const double y[7]) {
 
 // y = (r, theta, phi, W, K^r, K^theta, K^phi) with W = K^t + K^r (geo_accel); t is never
 // needed (stationary metric). Saved states hold K^t = W - K^r.
+//
+// The position rates of a stage are the previous stage's K: k1 = y_K and k_j+1 = K of stage
+// j+1. So a position and its K component share the sums: with T = k2 + k3 and S = k1 + T of
+// the K component, the classic weights give
+//   position' = position + h y_K + (h^2 / 6) S,  K' = y_K + (h / 6) (S + T + k4),
+// and W' = y_W + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4, summed in that order.
+// h/6 is taken as half of h/3: 1/6 in FP64 is half of 1/3, so the product rounds to the same
+// bits.
+//
+// Two forms with the same arithmetic, hence bit-identical states. LOOP = false writes the four
+// right-hand sides out (the faster form in a kernel of its own); LOOP = true runs the stages as
+// one loop over a single copy of the right-hand side, a quarter of the instruction footprint,
+// for the persistent kernel, whose geodesic and transfer loops compete for the instruction
+// cache. No sum is left for the compiler to contract: every addend is an fma, a negated fma or
+// a rate rounded by mul.rn (geo_accel), and the last stage's theta and phi rates enter their
+// sums through an explicit fma of their factors. (Left to the compiler, the written-out form
+// fused rate products into the sums that the loop form keeps in other basic blocks, and the two
+// forms' states differed by rounding.)
+template <bool LOOP>
 __device__ __forceinline__ void rk4_step(const double *__restrict__ tab, double a, double h, const double y[7],
                                          double out[7]) {
-    double k1[7], k2[7], k3[7], k4[7], t[7];
-    auto rhs = [&](const double *z, double *dz) {
-        dz[0] = z[4];
-        dz[1] = z[5];
-        dz[2] = z[6];
-        double acc[4];
-        geo_accel(tab, a, z[0], z[1], z + 3, acc);
-        dz[3] = acc[0];
-        dz[4] = acc[1];
-        dz[5] = acc[2];
-        dz[6] = acc[3];
-    };
-    // h/6 as half of h/3: 1/6 in FP64 is half of 1/3, so the product rounds to the same bits
-    const double h2 = halve(h), h3 = h * (1.0 / 3.0), h6 = halve(h3);
-    rhs(y, k1);
+    const double h2 = halve(h), h3 = h * (1.0 / 3.0), h6 = halve(h3), hh6 = h * h6;
+    double S[3], T[3];
+    if (!LOOP) {
+        double k1[4], k2[4], k3[4], k4[4], f[4], z[2], zk[4];
+        geo_accel(tab, a, y[0], y[1], y + 3, k1, f);  // k = d(W, K^r, K^theta, K^phi)
+        z[0] = fma(h2, y[4], y[0]);
+        z[1] = fma(h2, y[5], y[1]);
 #pragma unroll
-    for (int i = 0; i < 7; i++) t[i] = fma(h2, k1[i], y[i]);
-    rhs(t, k2);
+        for (int i = 0; i < 4; i++) zk[i] = fma(h2, k1[i], y[3 + i]);
+        geo_accel(tab, a, z[0], z[1], zk, k2, f);
+        z[0] = fma(h2, zk[1], y[0]);
+        z[1] = fma(h2, zk[2], y[1]);
 #pragma unroll
-    for (int i = 0; i < 7; i++) t[i] = fma(h2, k2[i], y[i]);
-    rhs(t, k3);
+        for (int i = 0; i < 4; i++) zk[i] = fma(h2, k2[i], y[3 + i]);
+        geo_accel(tab, a, z[0], z[1], zk, k3, f);
+        z[0] = fma(h, zk[1], y[0]);
+        z[1] = fma(h, zk[2], y[1]);
 #pragma unroll
-    for (int i = 0; i < 7; i++) t[i] = fma(h, k3[i], y[i]);
-    rhs(t, k4);
-    // The position rates of a stage are the previous stage's K: k1 = y_K and k_j+1 = K of
-    // stage j+1. So a position and its K component share the sums: with T = k2 + k3 and
-    // S = k1 + T of the K component, the classic weights give
-    //   position' = position + h y_K + (h^2 / 6) S,  K' = y_K + (h / 6) (S + T + k4).
-    const double hh6 = h * h6;
+        for (int i = 0; i < 4; i++) zk[i] = fma(h, k3[i], y[3 + i]);
+        geo_accel(tab, a, z[0], z[1], zk, k4, f);
 #pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const double T = k2[4 + i] + k3[4 + i], S = k1[4 + i] + T;
-        out[i] = fma(hh6, S, fma(h, y[4 + i], y[i]));
-        out[4 + i] = fma(h6, (S + T) + k4[4 + i], y[4 + i]);
+        for (int i = 0; i < 3; i++) {
+            T[i] = k2[1 + i] + k3[1 + i];
+            S[i] = k1[1 + i] + T[i];
+        }
+        out[3] = fma(h6, k4[0], fma(h3, k3[0], fma(h3, k2[0], fma(h6, k1[0], y[3]))));
+        out[4] = fma(h6, (S[0] + T[0]) + k4[1], y[4]);
+        out[5] = fma(h6, fma(f[0], f[1], S[1] + T[1]), y[5]);
+        out[6] = fma(h6, fma(f[2], f[3], S[2] + T[2]), y[6]);
+    } else {
+        double z[7], k[4], f[4], k1[3], k2[3], w;
+#pragma unroll
+        for (int i = 0; i < 7; i++) z[i] = y[i];
+#pragma unroll 1
+        for (int st = 0; st < 4; st++) {
+            geo_accel(tab, a, z[0], z[1], z + 3, k, f);
+            if (st == 0) {
+                w = fma(h6, k[0], y[3]);
+#pragma unroll
+                for (int i = 0; i < 3; i++) k1[i] = k[1 + i];
+            } else if (st == 1) {
+                w = fma(h3, k[0], w);
+#pragma unroll
+                for (int i = 0; i < 3; i++) k2[i] = k[1 + i];
+            } else if (st == 2) {
+                w = fma(h3, k[0], w);
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    T[i] = k2[i] + k[1 + i];
+                    S[i] = k1[i] + T[i];
+                }
+            } else {
+                out[3] = fma(h6, k[0], w);
+                out[4] = fma(h6, (S[0] + T[0]) + k[1], y[4]);
+                out[5] = fma(h6, fma(f[0], f[1], S[1] + T[1]), y[5]);
+                out[6] = fma(h6, fma(f[2], f[3], S[2] + T[2]), y[6]);
+                break;
+            }
+            // the next stage's state from y: positions advance with this stage's K (z[4], z[5])
+            const double c = st == 2 ? h : h2;
+            const double r = fma(c, z[4], y[0]), th = fma(c, z[5], y[1]);
+            z[0] = r;
+            z[1] = th;
+#pragma unroll
+            for (int i = 0; i < 4; i++) z[3 + i] = fma(c, k[i], y[3 + i]);
+        }
     }
-    out[3] = fma(h6, k4[3], fma(h3, k3[3], fma(h3, k2[3], fma(h6, k1[3], y[3]))));
+#pragma unroll
+    for (int i = 0; i < 3; i++) out[i] = fma(hh6, S[i], fma(h, y[4 + i], y[i]));
 }
 
 // Initial state of the backward ray through pixel (ix, iy): the camera frame's past-directed
@@ -94,12 +146,13 @@ struct StepCam {
 __device__ __forceinline__ StepCam step_cam(const Camera &c) { return StepCam{c.a, c.eps, c.r_stop, c.r_cam, c.nmax}; }
 
 // One step from y: yn, the step h, and whether it crossed the polar axis (then theta is
-// reflected, phi advanced by pi and K^theta reversed). C is Camera or StepCam.
-template <class C>
+// reflected, phi advanced by pi and K^theta reversed). C is Camera or StepCam; LOOP selects
+// the form of rk4_step.
+template <bool LOOP = false, class C>
 __device__ __forceinline__ bool geo_step(const double *__restrict__ tab, const C &c, const double y[7],
                                          double yn[7], double &h) {
     h = step_size(c.eps, y);
-    rk4_step(tab, c.a, h, y, yn);
+    rk4_step<LOOP>(tab, c.a, h, y, yn);
     bool refl = false;
     long long tb = dbits(yn[1]);
     if (tb < 0 && (tb << 1) != 0) {  // theta < 0 (not -0)

@@ -187,7 +187,7 @@ __device__ __forceinline__ double recip_nr(double x) {
 // The geodesic carries W = K^t + K^r in place of K^t (the stationary metric's K^t enters the
 // acceleration only through W): K = (W, K^r, K^theta, K^phi) on input, and acc[0] = dW/dl.
 __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, double a, double r, double th,
-                                          const double K[4], double acc[4]) {
+                                          const double K[4], double acc[4], double fac[4]) {
     const double a2 = a * a;
     double s, c;
     sincos_tab(sctab, th, &s, &c);
@@ -232,8 +232,16 @@ __device__ __forceinline__ void geo_accel(const double *__restrict__ sctab, doub
     const double X = fma(del, Fr, a * Ap);
     acc[0] = fma(-isig, X, fma(-q, Fr, At));
     acc[1] = -fma(isig, X, q * At);
-    acc[2] = -isig * Fh;
-    acc[3] = -iss * fma(as2, Fr, Ap);          // a/Sigma = a s^2 / (Sigma s^2)
+    // The theta and phi rates are products, acc[2] = fac[0] fac[1] and acc[3] = fac[2] fac[3],
+    // rounded here with mul.rn, which the compiler never contracts into a later addition: a
+    // caller's sums of these rates then round alike wherever they are compiled. A caller that
+    // wants a rate fused into a sum takes its factors (fac) and writes the fma itself.
+    fac[0] = -isig;
+    fac[1] = Fh;
+    fac[2] = -iss;
+    fac[3] = fma(as2, Fr, Ap);  // a/Sigma = a s^2 / (Sigma s^2)
+    acc[2] = __dmul_rn(fac[0], fac[1]);
+    acc[3] = __dmul_rn(fac[2], fac[3]);
 }
 
 // T^mu_b = Gamma^mu_{a b} K^a = 1/2 g^{mu nu} (D_{nu b} + [b=r] P_nu + [b=th] Q_nu

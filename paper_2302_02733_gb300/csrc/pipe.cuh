@@ -172,7 +172,7 @@ __device__ __forceinline__ void pipe_geodesic(const PipeArgs &p, const double *t
         uint8_t status = 0;
         for (int k = 0; k < p.step_tile; k++) {
             double h, yn[7];
-            bool refl = geo_step(tab, sc, y, yn, h);
+            bool refl = geo_step<true>(tab, sc, y, yn, h);
             save_state(p.pool, blk, slot, y, refl ? -h : h);
             slot++;
             n++;
