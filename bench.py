@@ -34,10 +34,10 @@ GEO_FLOP_PER_STEP = 612
 XFER_FLOP_PER_POINT = {"fp64": 1450, "mixed": 1450}
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 # DRAM bytes (read + write) per RK4 step of geodesic_kernel: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum = 0.004385 + 1.424782 GB over 22,982,083 steps (torus, 256^2, one launch,
+# dram__bytes_write.sum = 0.003515 + 1.424256 GB over 22,982,083 steps (torus, 256^2, one launch,
 # the kernel as built now). The kernel's traffic is the path arena it writes (64 B per state), so
 # it scales with the steps.
-GEO_DRAM_BYTES_PER_STEP = (0.004385e9 + 1.424782e9) / 22982083
+GEO_DRAM_BYTES_PER_STEP = (0.003515e9 + 1.424256e9) / 22982083
 
 
 def parse():
