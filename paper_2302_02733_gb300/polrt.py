@@ -103,6 +103,7 @@ def lib():
         L.rt_get_camera.argtypes = [_VP, C.POINTER(rt_camera)]
         L.rt_set_integrator.argtypes = [_VP, C.c_double, C.c_int]
         L.rt_set_workspace.argtypes = [_VP, _VP, C.c_size_t]
+        L.rt_workspace_min_bytes.argtypes = []
         L.rt_workspace_min_bytes.restype = C.c_size_t
         L.rt_workspace_hint.argtypes = [_VP, C.POINTER(C.c_size_t)]
         L.rt_render.argtypes = [_VP, C.c_int, _VP, _VP]
@@ -134,6 +135,7 @@ def lib():
         L.rt_fp64_fma_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
         L.rt_get_batch_stats.argtypes = [_VP, C.c_void_p]
         L.rt_get_grid_fetch.argtypes = [_VP, C.POINTER(C.c_int)]
+        L.rt_render_static_max_pixels.argtypes = []
         L.rt_render_static_max_pixels.restype = C.c_longlong
         L.rt_error_string.argtypes = [C.c_int]
         L.rt_error_string.restype = C.c_char_p

@@ -70,3 +70,54 @@ def test_constants_match_the_header():
     assert len(consts) >= 25
     for name, v in consts.items():
         assert v == got[("const", name)], name
+
+
+def _c_kind(decl):
+    """Kind of a C parameter or return type: ptr, f64, f32, or i/u with its width in bits."""
+    d = " ".join(decl.split())
+    if "*" in d or "[" in d:
+        return "ptr"
+    for words, kind in (("double", "f64"), ("float", "f32"), ("unsigned long long", "u64"), ("uint64_t", "u64"),
+                        ("size_t", "u64"), ("long long", "i64"), ("int64_t", "i64"), ("uint32_t", "u32"),
+                        ("unsigned", "u32"), ("int", "i32")):
+        if re.search(r"\b" + words + r"\b", d):
+            return kind
+    raise AssertionError(f"unknown C type in {decl!r}")
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+        return "ptr"
+    if t is C.c_double:
+        return "f64"
+    if t is C.c_float:
+        return "f32"
+    signed = t(-1).value < 0
+    return ("i" if signed else "u") + str(8 * C.sizeof(t))
+
+
+def _prototypes():
+    text = open(os.path.join(__graft_entry__.ROOT, "include", "polrt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^\s*(int|size_t|long long|const char \*)\s*(rt_\w+)\s*\(([^;]*?)\)\s*;", text, re.M | re.S)
+
+
+def test_binding_argument_types_match_the_prototypes():
+    from paper_2302_02733_gb300 import build
+
+    build.build()
+    L = polrt.lib()
+    protos = _prototypes()
+    assert len(protos) >= 40
+    for ret, name, args in protos:
+        fn = getattr(L, name)
+        params = [] if args.strip() == "void" else [a for a in args.split(",")]
+        want = [_c_kind(a) for a in params]
+        assert fn.argtypes is not None, f"{name}: no argtypes"
+        assert [_ctypes_kind(t) for t in fn.argtypes] == want, name
+        if ret == "const char *":
+            assert _ctypes_kind(fn.restype) == "ptr", name
+        else:
+            assert _ctypes_kind(fn.restype) == _c_kind(ret), name
