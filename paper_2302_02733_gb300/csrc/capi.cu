@@ -1003,10 +1003,12 @@ static int render_impl(rt_ctx *c, int form, void *out_iquv, uint8_t *status, voi
     const size_t per_ray = kPerRayBytes + (sur ? (size_t)kBudgetBlocksPerRay * kBlockStates * 48 : 0);
 
     // launch shape: the configured one, or automatic. RT_MIXED and RT_UNPOL overlap images of
-    // 2^19 rays or more in chunks of about 2^17 rays, the geodesic at 1 block per SM beside the
-    // transfer at its occupancy. Smaller images run one pass of each kernel, and so do RT_FP64
-    // (its FP64 transfer competes with the geodesic for the same pipe) and RT_SURROGATE (the
-    // network pass beside the geodesic measured slower than one pass: 859 against 536 ms).
+    // 2^19 rays or more: streamed (chunks of about 2^15 rays, the geodesic at 2 blocks per SM)
+    // when the workspace holds a piece of at least 1/64 of the rays, else in two workspace
+    // halves (4 to 16 chunks of about 2^17 rays, the geodesic at 1 block per SM beside the
+    // transfer). Smaller images run one pass of each kernel, and so do RT_FP64 (its FP64
+    // transfer competes with the geodesic for the same pipe) and RT_SURROGATE (the network pass
+    // beside the geodesic measured slower than one pass: 859 against 536 ms).
     int chunks = c->rcfg.chunks, geo_b = c->rcfg.geo_blocks_per_sm, W = c->rcfg.last_chunk_div;
     const bool auto_shape = chunks == 0;
     if (auto_shape)
