@@ -897,7 +897,8 @@ static int render_streamed(rt_ctx *c, int form, int coef, const Camera &cam, con
 int render_jobs_overlap(rt_ctx *c, int form, const JobDev *d_jobs, const JobDev *h_jobs, int njobs, long long nrays) {
     const size_t per_ray = kPerRayBytes;
     const int chunks = (int)std::min<long long>(64, std::max<long long>(2, nrays >> kAutoChunkShift));
-    // streamed when the workspace can hold every ray's path, else in two halves
+    // streamed, in pieces of the ray space that the workspace holds (up to kMaxStreamPieces),
+    // else in two halves
     const int P = plan_pieces(c, nrays), Kp = P > 0 ? stream_chunks(nrays, P, 0, true) : 0;
     const bool streamed = P > 0;
     ChunkLayout L{nrays, (int)std::min<long long>(chunks, nrays), kAutoLastDiv};
