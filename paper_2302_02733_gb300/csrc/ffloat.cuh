@@ -90,7 +90,7 @@ __device__ __forceinline__ int floor_small(float x) {
 
 // d = hi + lo: hi is d rounded to FP32 (as d2f_int), lo the remainder d - hi to about 2^-24
 // of itself (the 29 bits below hi's last, as two exact 13- and 16-bit halves). For |d| in the
-// FP32 normal range; lo becomes 0 for |d| below 2^-75 and hi for |d| outside the range.
+// FP32 normal range; lo becomes 0 for |d| below 2^-74 and hi for |d| outside the range.
 __device__ __forceinline__ void split_ff(double d, float &hi, float &lo) {
     unsigned long long x = (unsigned long long)__double_as_longlong(d);
     unsigned hw = (unsigned)(x >> 32), lw = (unsigned)x;
