@@ -6,7 +6,7 @@ and <= 1e-10 on the total flux. The mask holds pixels whose oracle output moves 
 1e-10 (same measure) when the pixel position is nudged by one ulp, or whose step count moves
 (the photon ring, where the path is chaotic); it must cover under 0.1% of the pixels.
 Mixed form (FP32 transfer, compensated Stokes sums): ADAF per-pixel p99 <= 5e-6, max <= 2e-5,
-total flux and net LP/CP within 1e-6; torus per-pixel p99 <= 1e-4, flux <= 1e-4, LP/CP within 1e-5.
+total flux and net LP/CP within 1e-6; torus per-pixel p99 <= 1e-4, flux and LP/CP within 1e-5.
 """
 import numpy as np
 import pytest
