@@ -1,6 +1,6 @@
 """The unpolarized fast path (RT_UNPOL: Stokes I with j_I and a_I only, FP32 scalar transfer
 with a compensated sum) against the oracle's scalar transfer: ADAF 64^2 per-pixel p99 <= 1e-5
-and flux <= 1e-6; torus 32^2 p99 <= 1e-4 and flux <= 1e-4; the image statistics (flux) from
+and flux <= 1e-6; torus 32^2 p99 <= 1e-4 and flux <= 1e-5 (measured 6.2e-5 and 7.7e-7); the image statistics (flux) from
 the I-only layout; and its speed against the polarized mixed form."""
 import numpy as np
 import pytest
@@ -31,7 +31,7 @@ def test_unpolarized_images_match_oracle(rt, ora, synth, torus_grid):
     cases = [("adaf64", synth.Camera(incl_deg=60.0, nx=64, ny=64), polrt.adaf_model(synth.adaf_params(1)),
               ora.adaf_model(synth.adaf_params(1)), 1e-5, 1e-6),
              ("grid32", synth.Camera(incl_deg=20.0, nx=32, ny=32), polrt.grid_model(prims, g),
-              ora.grid_model(prims, g), 1e-4, 1e-4)]
+              ora.grid_model(prims, g), 1e-4, 1e-5)]
     for name, cam, model, omodel, tp, tf in cases:
         polrt.rt_set_camera(ctx, cam)
         polrt.rt_load_model(ctx, model)
