@@ -1,7 +1,8 @@
 """The unpolarized fast path (RT_UNPOL: Stokes I with j_I and a_I only, FP32 scalar transfer
 with a compensated sum) against the oracle's scalar transfer: ADAF 64^2 per-pixel p99 <= 1e-5
-and flux <= 1e-6; torus 32^2 p99 <= 1e-4 and flux <= 1e-5 (measured 6.2e-5 and 7.7e-7); the image statistics (flux) from
-the I-only layout; and its speed against the polarized mixed form."""
+and flux <= 1e-6; torus 32^2 p99 <= 1e-4 and flux <= 1e-5 (measured 6.2e-5 and 7.7e-7); the
+image statistics (flux) from the I-only layout; and its speed against the polarized mixed
+form."""
 import numpy as np
 import pytest
 
