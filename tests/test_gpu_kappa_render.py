@@ -6,7 +6,7 @@ the surrogate form against the quadrature path (its reference) and against the o
   sensitivity mask, total flux within 1e-10, on a 32x32 image and on 545 pixels of the 1024x1024
   image (the lattice of every 64th pixel and the centres between, traced by rt_render_adaptive
   with an unreachable tolerance, so through the same kernels in a full-size camera); the mixed form (the
-  tabulated quadrature, FP32 transfer) p99 within 3e-4 and flux within 1e-4 at 32x32.
+  tabulated quadrature, FP32 transfer) p99 within 3e-4 and flux within 1e-5 at 32x32.
 - Surrogate: trained on 2^20 quadrature points drawn in the box that covers the 0.1-99.9
   percentiles of the image's emitting points; the 128^2 surrogate image against the
   quadrature image: flux within 1%, net LP and CP within 0.5 percentage points; a 32x32
@@ -87,7 +87,7 @@ def test_kappa_image_matches_oracle(rt, ora, synth, torus_grid):
     assert e64[~mask].max() <= 1e-9 and f64 <= 1e-10
     if mask.any():
         assert e64[mask].max() <= 1e-6
-    assert np.percentile(e32, 99) <= 3e-4 and f32 <= 1e-4
+    assert np.percentile(e32, 99) <= 3e-4 and f32 <= 1e-5  # measured 4.6e-5 and 4.5e-7
 
 
 def test_kappa_fp64_sampled_at_full_size(rt, ora, synth, torus_grid):
